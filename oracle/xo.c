@@ -1,0 +1,543 @@
+/*
+ * xo.c -- plain, slow FP64 CPU oracle for the line-list -> cross-section path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library; the only thing
+ * both sides share is the seeded input generator (xcsynth), which holds none
+ * of the method's arithmetic.
+ *
+ * Everything here is written from the ExoCross paper (Yurchenko, Al-Refaie &
+ * Tennyson 2018, arXiv:1801.09803), in its notation, in the order it gives:
+ *   Q(T)          Eq. (e:pf)   direct state sum
+ *   I_fi          Eq. (e:int)  LTE absorption intensity, upper degeneracy
+ *   alpha_D       Eq. (e:alphaD)
+ *   gamma_L       Eq. (e:gamma_L)
+ *   Gauss         Eq. (e:Gauss)        Lorentz  Eq. (e:lor)
+ *   Voigt         Eq. (e:Voigt), read as the unit-area convolution
+ *                 V = sqrt(ln2/pi)/alpha * Re w(x+iy), x = sqrt(ln2) D/alpha,
+ *                 y = sqrt(ln2) gamma/alpha  (the printed prefactor is garbled)
+ *   w(z)          Humlicek's four-region rational approximation "w4"
+ *                 (J. Humlicek, JQSRT 27 (1982) 437), restated below
+ *   GH sampled    Eq. (e:V-quad) with the node shift alpha*x_j/sqrt(ln2)
+ *   GH binned     Eq. (e:sigma:quad), y^+- = (nu_k +- dnu/2 - nu_fi - alpha x_j/sqrt(ln2))/gamma
+ *   sampling      sigma(nu_k) = sum_fi I_fi f(nu_k)  (Sec. 3.1), lines outer,
+ *                 grid points inner, within the cutoff ("Off-set", Sec. 3.10)
+ *   grid          nu_k = nu_A + k * dnu, N points including both ends, Eq. (e:Ngrid)
+ *
+ * Readings where the paper is silent: the cutoff test is inclusive,
+ * |nu_k - nu_fi| <= cut; accumulation is FP64 with Neumaier compensation;
+ * OpenMP threads (the paper's own design, Sec. 5.3) each own a private grid
+ * over a contiguous block of lines and are combined in thread order.
+ *
+ * The adjoint (vector-Jacobian product) is not in the paper; it is the
+ * analytic chain rule of the same expressions (see xo_cross_section_vjp).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC xo.c -lm
+ * (-ffp-contract=off keeps a*b+c as two roundings on every host.)
+ */
+#include <complex.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 exact SI values */
+static const double XO_H = 6.62607015e-34;      /* J s */
+static const double XO_C_SI = 2.99792458e8;     /* m/s */
+static const double XO_KB = 1.380649e-23;       /* J/K */
+static const double XO_DALTON = 1.66053906660e-27; /* kg */
+
+static const double XO_PI = 3.14159265358979323846;
+static const double XO_LN2 = 0.69314718055994530942;
+
+double xo_c2(void) { return XO_H * (XO_C_SI * 100.0) / XO_KB; } /* cm K */
+
+enum { XO_DOPPLER = 0, XO_LORENTZ = 1, XO_VOIGT_W4 = 2, XO_GH_BINNED = 3, XO_GH_SAMPLED = 4 };
+
+/* ---------------------------------------------------------------------- */
+/* Partition function, Eq. (e:pf), and its temperature derivative          */
+/* ---------------------------------------------------------------------- */
+void xo_partition_function(const double *E, const int32_t *g, size_t n, double T,
+                           double *Q, double *dQdT)
+{
+    const double c2 = xo_c2();
+    double q = 0.0, dq = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        double b = exp(-c2 * E[i] / T);
+        q += (double)g[i] * b;
+        dq += (double)g[i] * (c2 * E[i] / (T * T)) * b;
+    }
+    *Q = q;
+    if (dQdT) *dQdT = dq;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Per-line parameters for one condition                                  */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    double T, P, Q, dQdT;       /* K, units of P_ref, -, 1/K */
+    double mass_da, T_ref, P_ref;
+    double gamma_scale, n_shift;
+    double abundance;
+} xo_condition;
+
+typedef struct {
+    int profile;                 /* XO_* */
+    double cutoff;               /* cm^-1 */
+    double width_mult;           /* > 0: cut_l = min(cutoff, width_mult*max(alpha, gamma)) */
+    int n_gh;
+} xo_opts;
+
+/* Eq. (e:int): I = g' A / (8 pi c nu^2) * exp(-c2 E''/T) * (1 - exp(-c2 nu/T)) / Q(T) */
+double xo_intensity(double nu, double elower, double A, double g_up, const xo_condition *c)
+{
+    const double c2 = xo_c2();
+    const double c_cm = XO_C_SI * 100.0;
+    double boltz = exp(-c2 * elower / c->T);
+    double stim = -expm1(-c2 * nu / c->T);
+    return c->abundance * g_up * A / (8.0 * XO_PI * c_cm * nu * nu) * boltz * stim / c->Q;
+}
+
+/* Eq. (e:alphaD): Doppler HWHM */
+double xo_alpha_doppler(double nu, const xo_condition *c)
+{
+    double m = c->mass_da * XO_DALTON;
+    return sqrt(2.0 * XO_KB * c->T * XO_LN2 / m) * nu / XO_C_SI;
+}
+
+/* Eq. (e:gamma_L): Lorentz HWHM, with a global scale and exponent shift */
+double xo_gamma_lorentz(double gamma_ref, double n_T, const xo_condition *c)
+{
+    return c->gamma_scale * gamma_ref * pow(c->T_ref / c->T, n_T + c->n_shift) * (c->P / c->P_ref);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Humlicek w4: w(z) ~ F(t), t = y - i x, four regions by s = |x| + y      */
+/* F'(t) is the exact derivative of the same rational (and exp) forms.     */
+/* ---------------------------------------------------------------------- */
+static int w4_region(double x, double y)
+{
+    double s = fabs(x) + y;
+    if (s >= 15.0) return 1;
+    if (s >= 5.5) return 2;
+    if (y >= 0.195 * fabs(x) - 0.176) return 3;
+    return 4;
+}
+
+/* region III numerator / denominator polynomials in t (Horner form) */
+static const double R3P[5] = {16.4955, 20.20933, 11.96482, 3.778987, 0.5642236};
+static const double R3Q[6] = {16.4955, 38.82363, 39.27121, 21.69274, 6.699398, 1.0};
+/* region IV: w = exp(u) - t*N(u)/D(u), u = t^2; N and D alternate in sign */
+static const double R4N[7] = {36183.31, 3321.9905, 1540.787, 219.0313, 35.76683, 1.320522, 0.56419};
+static const double R4D[8] = {32066.6, 24322.84, 9022.228, 2186.181, 364.2191, 61.57037, 1.841439, 1.0};
+
+static double complex poly(const double *a, int n, double complex t)
+{   /* a[0] + a[1] t + ... + a[n-1] t^(n-1) */
+    double complex r = a[n - 1];
+    for (int i = n - 2; i >= 0; --i) r = r * t + a[i];
+    return r;
+}
+static double complex dpoly(const double *a, int n, double complex t)
+{
+    double complex r = (n - 1) * a[n - 1];
+    for (int i = n - 2; i >= 1; --i) r = r * t + i * a[i];
+    return r;
+}
+static double complex altpoly(const double *a, int n, double complex u)
+{   /* a[0] - u (a[1] - u (a[2] - ...)) = sum_i (-1)^i a[i] u^i */
+    double complex r = a[n - 1];
+    for (int i = n - 2; i >= 0; --i) r = a[i] - u * r;
+    return r;
+}
+static double complex daltpoly(const double *a, int n, double complex u)
+{
+    double complex r = 0.0;
+    for (int i = n - 1; i >= 1; --i) r = r * u + ((i & 1) ? -1.0 : 1.0) * i * a[i];
+    return r;
+}
+
+void xo_w4_deriv(double x, double y, double *wre, double *wim, double *dre, double *dim)
+{
+    double complex t = y - I * x;
+    double complex w, d;
+    switch (w4_region(x, y)) {
+    case 1: {
+        double complex den = 0.5 + t * t;
+        w = t * 0.5641896 / den;
+        d = 0.5641896 * (0.5 - t * t) / (den * den);
+        break;
+    }
+    case 2: {
+        double complex u = t * t;
+        double complex N = t * (1.410474 + u * 0.5641896);
+        double complex Np = 1.410474 + 3.0 * 0.5641896 * u;
+        double complex D = 0.75 + u * (3.0 + u);
+        double complex Dp = 6.0 * t + 4.0 * t * u;
+        w = N / D;
+        d = (Np * D - N * Dp) / (D * D);
+        break;
+    }
+    case 3: {
+        double complex N = poly(R3P, 5, t), D = poly(R3Q, 6, t);
+        w = N / D;
+        d = (dpoly(R3P, 5, t) * D - N * dpoly(R3Q, 6, t)) / (D * D);
+        break;
+    }
+    default: {
+        double complex u = t * t;
+        double complex N = altpoly(R4N, 7, u), D = altpoly(R4D, 8, u);
+        double complex Nu = daltpoly(R4N, 7, u), Du = daltpoly(R4D, 8, u);
+        double complex e = cexp(u);
+        double complex r = N / D;
+        double complex ru = (Nu * D - N * Du) / (D * D);
+        w = e - t * r;
+        d = 2.0 * t * e - (r + t * ru * 2.0 * t);
+        break;
+    }
+    }
+    *wre = creal(w); *wim = cimag(w);
+    if (dre) *dre = creal(d);
+    if (dim) *dim = cimag(d);
+}
+
+void xo_w4(double x, double y, double *wre, double *wim)
+{
+    xo_w4_deriv(x, y, wre, wim, NULL, NULL);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Gauss-Hermite nodes and weights for weight exp(-x^2)                   */
+/* Roots of H_N bracketed by sign changes on a fine mesh, refined by       */
+/* bisection; weights are Christoffel numbers 1 / sum_k p_k(x)^2 with the  */
+/* orthonormal Hermite polynomials p_k (three-term recurrence).            */
+/* ---------------------------------------------------------------------- */
+static void orthonormal_hermite(int N, double x, double *pN, double *sumsq)
+{
+    double pm1 = 0.0, p = pow(XO_PI, -0.25), s = p * p;
+    for (int k = 0; k < N; ++k) {
+        double pn = x * sqrt(2.0 / (k + 1)) * p - sqrt((double)k / (k + 1)) * pm1;
+        pm1 = p; p = pn;
+        if (k + 1 < N) s += p * p;
+    }
+    *pN = p;
+    if (sumsq) *sumsq = s;
+}
+
+int xo_gauss_hermite(int N, double *x, double *w)
+{
+    if (N < 1 || N > 200) return -1;
+    double L = sqrt(2.0 * N + 1.0) + 1.0;
+    int M = 200 * N + 1, found = 0;
+    double a = -L, fa; orthonormal_hermite(N, a, &fa, NULL);
+    for (int i = 1; i < M && found < N; ++i) {
+        double b = -L + 2.0 * L * i / (M - 1), fb;
+        orthonormal_hermite(N, b, &fb, NULL);
+        if (fa == 0.0) { x[found++] = a; }
+        else if (fa * fb < 0.0) {
+            double lo = a, hi = b, flo = fa;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi), fm;
+                if (mid == lo || mid == hi) break;
+                orthonormal_hermite(N, mid, &fm, NULL);
+                if (flo * fm <= 0.0) hi = mid; else { lo = mid; flo = fm; }
+            }
+            x[found++] = 0.5 * (lo + hi);
+        }
+        a = b; fa = fb;
+    }
+    if (found != N) return -2;
+    for (int j = 0; j < N; ++j) {
+        double pN, s;
+        orthonormal_hermite(N, x[j], &pN, &s);
+        w[j] = 1.0 / s;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Line profiles (unit area), D = nu - nu_fi                              */
+/* ---------------------------------------------------------------------- */
+double xo_gauss(double D, double alpha)        /* Eq. (e:Gauss) */
+{
+    return sqrt(XO_LN2 / XO_PI) / alpha * exp(-D * D * XO_LN2 / (alpha * alpha));
+}
+
+double xo_lorentz(double D, double gamma)      /* Eq. (e:lor) */
+{
+    return gamma / (XO_PI * (D * D + gamma * gamma));
+}
+
+double xo_voigt_w4(double D, double alpha, double gamma)
+{
+    double sl = sqrt(XO_LN2);
+    double wr, wi;
+    xo_w4(sl * D / alpha, sl * gamma / alpha, &wr, &wi);
+    return sqrt(XO_LN2 / XO_PI) / alpha * wr;
+}
+
+double xo_voigt_gh(double D, double alpha, double gamma, int n, const double *xg, const double *wg)
+{
+    double s = 0.0, sl = sqrt(XO_LN2);
+    for (int j = 0; j < n; ++j) {
+        double d = D - alpha * xg[j] / sl;
+        s += wg[j] * gamma / (d * d + gamma * gamma);
+    }
+    return s / pow(XO_PI, 1.5);
+}
+
+/* bin average over [D - h/2, D + h/2], Eq. (e:sigma:quad) without I */
+double xo_voigt_gh_binned(double D, double h, double alpha, double gamma,
+                          int n, const double *xg, const double *wg)
+{
+    double s = 0.0, sl = sqrt(XO_LN2);
+    for (int j = 0; j < n; ++j) {
+        double yp = (D + 0.5 * h - alpha * xg[j] / sl) / gamma;
+        double ym = (D - 0.5 * h - alpha * xg[j] / sl) / gamma;
+        s += wg[j] * (atan(yp) - atan(ym));
+    }
+    return s / (pow(XO_PI, 1.5) * h);
+}
+
+/* profile value and its partial derivatives w.r.t. alpha and gamma */
+static double profile_eval(int prof, double D, double h, double alpha, double gamma,
+                           int ngh, const double *xg, const double *wg,
+                           double *dVda, double *dVdg)
+{
+    double sl = sqrt(XO_LN2);
+    double V, da = 0.0, dg = 0.0;
+    switch (prof) {
+    case XO_DOPPLER:
+        V = xo_gauss(D, alpha);
+        da = V * (-1.0 / alpha + 2.0 * XO_LN2 * D * D / (alpha * alpha * alpha));
+        break;
+    case XO_LORENTZ: {
+        double q = D * D + gamma * gamma;
+        V = gamma / (XO_PI * q);
+        dg = (D * D - gamma * gamma) / (XO_PI * q * q);
+        break;
+    }
+    case XO_VOIGT_W4: {
+        double wr, wi, dr, di;
+        xo_w4_deriv(sl * D / alpha, sl * gamma / alpha, &wr, &wi, &dr, &di);
+        V = sqrt(XO_LN2 / XO_PI) / alpha * wr;
+        double dVdD = XO_LN2 / (sqrt(XO_PI) * alpha * alpha) * di;   /* Re(-i F') = Im F' */
+        dg = XO_LN2 / (sqrt(XO_PI) * alpha * alpha) * dr;
+        da = -(V + D * dVdD + gamma * dg) / alpha;
+        break;
+    }
+    case XO_GH_SAMPLED: {
+        double s = 0.0;
+        for (int j = 0; j < ngh; ++j) {
+            double d = D - alpha * xg[j] / sl, q = d * d + gamma * gamma;
+            s += wg[j] * gamma / q;
+            dg += wg[j] * (d * d - gamma * gamma) / (q * q);
+            da += wg[j] * gamma * 2.0 * d * (xg[j] / sl) / (q * q);
+        }
+        double k = pow(XO_PI, -1.5);
+        V = s * k; dg *= k; da *= k;
+        break;
+    }
+    case XO_GH_BINNED:
+    default: {
+        double s = 0.0;
+        for (int j = 0; j < ngh; ++j) {
+            double sp = D + 0.5 * h - alpha * xg[j] / sl, sm = D - 0.5 * h - alpha * xg[j] / sl;
+            s += wg[j] * (atan(sp / gamma) - atan(sm / gamma));
+            dg += wg[j] * (-sp / (sp * sp + gamma * gamma) + sm / (sm * sm + gamma * gamma));
+            da += wg[j] * (xg[j] / sl) * (-gamma / (sp * sp + gamma * gamma) + gamma / (sm * sm + gamma * gamma));
+        }
+        double k = 1.0 / (pow(XO_PI, 1.5) * h);
+        V = s * k; dg *= k; da *= k;
+        break;
+    }
+    }
+    if (dVda) *dVda = da;
+    if (dVdg) *dVdg = dg;
+    return V;
+}
+
+double xo_profile(int prof, double D, double h, double alpha, double gamma, int ngh,
+                  const double *xg, const double *wg, double *dVda, double *dVdg)
+{
+    return profile_eval(prof, D, h, alpha, gamma, ngh, xg, wg, dVda, dVdg);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Cross section by sampling (Sec. 3.1): lines outer, grid points inner    */
+/* ---------------------------------------------------------------------- */
+static double line_cut(const xo_opts *o, double alpha, double gamma)
+{
+    if (o->width_mult > 0.0) {
+        double w = o->width_mult * (alpha > gamma ? alpha : gamma);
+        return w < o->cutoff ? w : o->cutoff;
+    }
+    return o->cutoff;
+}
+
+static void neumaier_add(double *s, double *c, double v)
+{
+    double t = *s + v;
+    if (fabs(*s) >= fabs(v)) *c += (*s - t) + v;
+    else *c += (v - t) + *s;
+    *s = t;
+}
+
+/* first grid index k with nu_A + k*h >= x  (a window start; exact test done per point) */
+static long long grid_floor_index(double x, double nu_A, double h)
+{
+    return (long long)floor((x - nu_A) / h);
+}
+
+int xo_cross_section(const double *nu, const float *elower, const float *A, const float *gamma_ref,
+                     const float *n_T, const int16_t *g_up, size_t n_lines,
+                     const xo_condition *cond, double nu_A, double h, long long n_pts,
+                     const xo_opts *o, double *sigma, int nthreads)
+{
+    if (n_pts <= 0) return 0;
+    double xg[200], wg[200];
+    int ngh = 0;
+    if (o->profile == XO_GH_BINNED || o->profile == XO_GH_SAMPLED) {
+        ngh = o->n_gh;
+        if (xo_gauss_hermite(ngh, xg, wg) != 0) return -1;
+    }
+    if (nthreads < 1) nthreads = 1;
+    double *acc = (double *)calloc((size_t)nthreads * 2 * (size_t)n_pts, sizeof(double));
+    if (!acc) return -2;
+
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static, 1)
+#endif
+    for (int t = 0; t < nthreads; ++t) {
+        double *s = acc + (size_t)t * 2 * (size_t)n_pts, *c = s + n_pts;
+        size_t l0 = n_lines * (size_t)t / (size_t)nthreads;
+        size_t l1 = n_lines * (size_t)(t + 1) / (size_t)nthreads;
+        for (size_t l = l0; l < l1; ++l) {
+            double nul = nu[l];
+            double Ifi = xo_intensity(nul, elower[l], A[l], g_up[l], cond);
+            double al = xo_alpha_doppler(nul, cond);
+            double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cond);
+            double cut = line_cut(o, al, ga);
+            long long k0 = grid_floor_index(nul - cut, nu_A, h) - 1;
+            long long k1 = grid_floor_index(nul + cut, nu_A, h) + 1;
+            if (k0 < 0) k0 = 0;
+            if (k1 > n_pts - 1) k1 = n_pts - 1;
+            for (long long k = k0; k <= k1; ++k) {
+                double xk = nu_A + (double)k * h;
+                double D = xk - nul;
+                if (fabs(D) > cut) continue;
+                double v = profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, NULL, NULL);
+                neumaier_add(&s[k], &c[k], Ifi * v);
+            }
+        }
+    }
+    for (long long k = 0; k < n_pts; ++k) {
+        double s = 0.0, c = 0.0;
+        for (int t = 0; t < nthreads; ++t) {
+            double *st = acc + (size_t)t * 2 * (size_t)n_pts;
+            neumaier_add(&s, &c, st[k]);
+            neumaier_add(&s, &c, st[n_pts + k]);
+        }
+        sigma[k] = s + c;
+    }
+    free(acc);
+    return 0;
+}
+
+/* number of (line, grid point) pairs inside the cutoff: the algorithmic work */
+long long xo_count_evals(const double *nu, const float *gamma_ref, const float *n_T, size_t n_lines,
+                         const xo_condition *cond, double nu_A, double h, long long n_pts,
+                         const xo_opts *o)
+{
+    long long cnt = 0;
+    for (size_t l = 0; l < n_lines; ++l) {
+        double al = xo_alpha_doppler(nu[l], cond);
+        double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cond);
+        double cut = line_cut(o, al, ga);
+        long long k0 = grid_floor_index(nu[l] - cut, nu_A, h) - 1;
+        long long k1 = grid_floor_index(nu[l] + cut, nu_A, h) + 1;
+        if (k0 < 0) k0 = 0;
+        if (k1 > n_pts - 1) k1 = n_pts - 1;
+        for (long long k = k0; k <= k1; ++k) {
+            double D = (nu_A + (double)k * h) - nu[l];
+            if (fabs(D) <= cut) ++cnt;
+        }
+    }
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint: given g_k = dL/dsigma_k for each condition, the chain rule     */
+/*   dL/dT_c, dL/dP_c                         per condition               */
+/*   dL/d(gamma_scale), dL/d(n_shift)         global                      */
+/*   dL/d(gamma_ref_l), dL/d(n_l)             per line (summed over c)    */
+/* The cutoff is held fixed (its boundary terms are measure-zero).         */
+/* ---------------------------------------------------------------------- */
+int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, const float *gamma_ref,
+                         const float *n_T, const int16_t *g_up, size_t n_lines,
+                         const xo_condition *conds, int n_cond, double nu_A, double h, long long n_pts,
+                         const xo_opts *o, const double *grad_sigma,
+                         double *dT, double *dP, double *d_gscale, double *d_nshift,
+                         double *d_gref_line, double *d_n_line)
+{
+    const double c2 = xo_c2();
+    double xg[200], wg[200];
+    int ngh = 0;
+    if (o->profile == XO_GH_BINNED || o->profile == XO_GH_SAMPLED) {
+        ngh = o->n_gh;
+        if (xo_gauss_hermite(ngh, xg, wg) != 0) return -1;
+    }
+    double gs = 0.0, gn = 0.0;
+    if (d_gref_line) memset(d_gref_line, 0, n_lines * sizeof(double));
+    if (d_n_line) memset(d_n_line, 0, n_lines * sizeof(double));
+    for (int c = 0; c < n_cond; ++c) {
+        const xo_condition *cd = &conds[c];
+        const double *g = grad_sigma + (size_t)c * (size_t)n_pts;
+        double T = cd->T;
+        double sT = 0.0, sP = 0.0;
+        for (size_t l = 0; l < n_lines; ++l) {
+            double nul = nu[l];
+            double Ifi = xo_intensity(nul, elower[l], A[l], g_up[l], cd);
+            double al = xo_alpha_doppler(nul, cd);
+            double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cd);
+            double cut = line_cut(o, al, ga);
+            long long k0 = grid_floor_index(nul - cut, nu_A, h) - 1;
+            long long k1 = grid_floor_index(nul + cut, nu_A, h) + 1;
+            if (k0 < 0) k0 = 0;
+            if (k1 > n_pts - 1) k1 = n_pts - 1;
+            double SI = 0.0, Sa = 0.0, Sg = 0.0;
+            for (long long k = k0; k <= k1; ++k) {
+                double D = (nu_A + (double)k * h) - nul;
+                if (fabs(D) > cut) continue;
+                double dVa, dVg;
+                double V = profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, &dVa, &dVg);
+                SI += g[k] * V;
+                Sa += g[k] * Ifi * dVa;
+                Sg += g[k] * Ifi * dVg;
+            }
+            /* d ln I / dT = c2 E''/T^2 - (c2 nu/T^2)/(exp(c2 nu/T) - 1) - Q'/Q */
+            double dlnI = c2 * elower[l] / (T * T) - (c2 * nul / (T * T)) / expm1(c2 * nul / T)
+                          - cd->dQdT / cd->Q;
+            double dIdT = Ifi * dlnI;
+            double dadT = al / (2.0 * T);
+            double ntot = n_T[l] + cd->n_shift;
+            double dgdT = -ntot * ga / T;
+            sT += SI * dIdT + Sa * dadT + Sg * dgdT;
+            sP += Sg * ga / cd->P;
+            gs += Sg * ga / cd->gamma_scale;
+            double dgdn = ga * log(cd->T_ref / T);
+            gn += Sg * dgdn;
+            if (d_gref_line) d_gref_line[l] += Sg * ga / gamma_ref[l];
+            if (d_n_line) d_n_line[l] += Sg * dgdn;
+        }
+        dT[c] = sT;
+        dP[c] = sP;
+    }
+    if (d_gscale) *d_gscale = gs;
+    if (d_nshift) *d_nshift = gn;
+    return 0;
+}

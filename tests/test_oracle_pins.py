@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against facts outside itself.
+
+Each test checks one part of the oracle against a closed form, a textbook
+relation, a library routine computed by a different method, a limit, an
+invariant or brute force, so that a dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.special as sp
+import scipy.stats as st
+
+import xcsynth as xs
+
+LN2 = math.log(2.0)
+
+
+# ---------------------------------------------------------------- constants
+def test_second_radiation_constant(oracle_lib):
+    # CODATA 2018: c2 = hc/k = 1.438776877... cm K
+    assert abs(oracle_lib.c2() - 1.438776877) < 1e-9
+
+
+# ------------------------------------------------------ Q(T), Eq. (e:pf)
+def test_partition_two_level_and_limits(oracle_lib):
+    c2 = 1.438776877503933802
+    E = np.array([0.0, 1234.5])
+    g = np.array([3, 7], np.int32)
+    for T in (50.0, 296.0, 3000.0):
+        Q, dQ = oracle_lib.partition_function(E, g, T)
+        x = c2 * 1234.5 / T
+        assert Q == pytest.approx(3 + 7 * math.exp(-x), rel=1e-14)
+        assert dQ == pytest.approx(7 * math.exp(-x) * x / T, rel=1e-13)
+    # T -> infinity: every state counts fully
+    Es, gs = xs.gen_states(5, 5000)
+    Q, _ = oracle_lib.partition_function(Es, gs, 1e14)
+    assert Q == pytest.approx(gs.sum(), rel=1e-8)
+    # T -> 0: only the ground level (E = 0) survives
+    Q0, _ = oracle_lib.partition_function(E, g, 1.0)
+    assert Q0 == pytest.approx(3.0, rel=1e-14)
+
+
+def test_partition_derivative_matches_finite_difference(oracle_lib):
+    E, g = xs.gen_states(9, 5000)
+    for T in (300.0, 1500.0):
+        h = T * 1e-5
+        Qp, _ = oracle_lib.partition_function(E, g, T + h)
+        Qm, _ = oracle_lib.partition_function(E, g, T - h)
+        _, dQ = oracle_lib.partition_function(E, g, T)
+        assert dQ == pytest.approx((Qp - Qm) / (2 * h), rel=1e-7)
+
+
+# --------------------------------------------- intensity, Eq. (e:int)
+def test_intensity_equals_einstein_population_difference(oracle_lib):
+    """Two-level system: integrated absorption = A g_u/(8 pi c nu^2 g_l) (n_l - g_l/g_u n_u)
+    with Boltzmann fractions n = g e^{-c2 E/T}/Q (the Einstein-coefficient relation of
+    Hilborn, Am. J. Phys. 50 (1982) 982, written in wavenumber units)."""
+    c2 = 1.438776877503933802
+    c_cm = 2.99792458e10
+    El, nu = 250.0, 1800.0
+    gl, gu, A = 5.0, 7.0, 12.5
+    for T in (296.0, 1000.0, 3000.0):
+        Eu = El + nu
+        Q = 2.0 + gl * math.exp(-c2 * El / T) + gu * math.exp(-c2 * Eu / T)  # plus a ground level g=2
+        nl = gl * math.exp(-c2 * El / T) / Q
+        nu_pop = gu * math.exp(-c2 * Eu / T) / Q
+        expect = A * gu / (8 * math.pi * c_cm * nu ** 2 * gl) * (nl - gl / gu * nu_pop)
+        cond = oracle_lib.make_condition(T, 1.0, Q)
+        assert oracle_lib.intensity(nu, El, A, gu, cond) == pytest.approx(expect, rel=1e-12)
+
+
+def test_intensity_structure(oracle_lib):
+    cond = oracle_lib.make_condition(1000.0, 1.0, 345.0)
+    base = oracle_lib.intensity(2000.0, 1000.0, 1.0, 3.0, cond)
+    assert oracle_lib.intensity(2000.0, 1000.0, 2.0, 3.0, cond) == pytest.approx(2 * base, rel=1e-15)
+    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 6.0, cond) == pytest.approx(2 * base, rel=1e-15)
+    # Boltzmann ratio between lower levels
+    r = oracle_lib.intensity(2000.0, 3000.0, 1.0, 3.0, cond) / base
+    assert r == pytest.approx(math.exp(-1.438776877503934 * 2000.0 / 1000.0), rel=1e-13)
+    # abundance scales I linearly (Sec. 2.1 remark) and Q divides it
+    c2 = oracle_lib.make_condition(1000.0, 1.0, 690.0, abundance=0.25)
+    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 3.0, c2) == pytest.approx(base / 8, rel=1e-15)
+    # small c2 nu/T: (1 - e^{-x}) -> x, so I -> g A c2 /(8 pi c nu T Q) ; tests the expm1 branch
+    hot = oracle_lib.make_condition(1e6, 1.0, 1.0)
+    nu = 1e-3
+    expect = 1.0 * 1.438776877503934 / (8 * math.pi * 2.99792458e10 * nu * 1e6)
+    assert oracle_lib.intensity(nu, 0.0, 1.0, 1.0, hot) == pytest.approx(expect, rel=1e-8)
+
+
+# --------------------------------------------- widths, Eqs. (e:alphaD), (e:gamma_L)
+def test_doppler_hwhm_textbook_constant(oracle_lib):
+    # alpha_D = 3.581e-7 * nu * sqrt(T / M[g/mol])  (the usual practical form)
+    for T, nu in ((296.0, 1000.0), (3000.0, 10000.0)):
+        cond = oracle_lib.make_condition(T, 1.0, 1.0, mass_da=18.0)
+        assert oracle_lib.alpha_doppler(nu, cond) == pytest.approx(3.5812e-7 * nu * math.sqrt(T / 18.0), rel=2e-4)
+    c1 = oracle_lib.make_condition(400.0, 1.0, 1.0)
+    c4 = oracle_lib.make_condition(1600.0, 1.0, 1.0)
+    assert oracle_lib.alpha_doppler(2000.0, c4) == pytest.approx(2 * oracle_lib.alpha_doppler(2000.0, c1), rel=1e-15)
+
+
+def test_lorentz_hwhm_scaling(oracle_lib):
+    ref = oracle_lib.make_condition(296.0, 1.0, 1.0)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, ref) == pytest.approx(0.07, rel=1e-15)
+    hot = oracle_lib.make_condition(592.0, 3.0, 1.0)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, hot) == pytest.approx(0.07 * 3.0 / math.sqrt(2.0), rel=1e-14)
+    sc = oracle_lib.make_condition(592.0, 1.0, 1.0, gamma_scale=1.05, n_shift=0.25)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, sc) == pytest.approx(1.05 * 0.07 * 0.5 ** 0.75, rel=1e-14)
+
+
+# --------------------------------------------- profiles
+def test_gauss_is_normal_pdf_with_hwhm(oracle_lib):
+    a = 0.037
+    sig = a / math.sqrt(2 * LN2)
+    for D in (0.0, 0.01, -0.05, 0.2):
+        assert oracle_lib.gauss(D, a) == pytest.approx(st.norm.pdf(D, scale=sig), rel=1e-13)
+    assert oracle_lib.gauss(a, a) == pytest.approx(0.5 * oracle_lib.gauss(0.0, a), rel=1e-14)
+
+
+def test_lorentz_is_cauchy_pdf(oracle_lib):
+    g = 0.061
+    for D in (0.0, 0.03, -1.0, 24.9):
+        assert oracle_lib.lorentz(D, g) == pytest.approx(st.cauchy.pdf(D, scale=g), rel=1e-13)
+
+
+def test_w4_against_faddeeva(oracle_lib):
+    """w4's relative accuracy is about 1e-4 (Humlicek 1982); compare with scipy's wofz
+    and with mpmath's erfc at 30 digits."""
+    xs_ = np.concatenate([np.linspace(-30, 30, 121), [0.0, 0.7071, 3.3, 5.49, 5.51, 14.99, 15.01]])
+    ys_ = np.concatenate([np.logspace(-8, 2.3, 40), [0.176, 0.195]])
+    worst_abs, worst_re = 0.0, 0.0
+    for x in xs_:
+        for y in ys_:
+            w = oracle_lib.w4(x, y)
+            e = sp.wofz(complex(x, y))
+            worst_abs = max(worst_abs, abs(w - e) / abs(e))
+            worst_re = max(worst_re, abs(w.real - e.real) / abs(e.real))
+    # w4 is accurate to ~1e-4 in |w|; Re w alone loses relative accuracy where it is
+    # tiny next to Im w (y -> 0 just above s = 5.5, where region II misses exp(-x^2)):
+    # measured 3.95e-4 at x = 5.5, y = 1e-8.
+    assert worst_abs < 1.2e-4
+    assert worst_re < 4.5e-4
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    for x, y in ((0.3, 0.05), (4.0, 1e-3), (7.0, 0.5), (20.0, 2.0), (2.5, 3.0)):
+        z = mp.mpc(x, y)
+        e = mp.exp(-z * z) * mp.erfc(-1j * z)
+        w = oracle_lib.w4(x, y)
+        assert abs(w.real - float(e.real)) / abs(float(e.real)) < 1.2e-4
+        assert abs(w.imag - float(e.imag)) / abs(float(e.imag)) < 2e-4
+
+
+def test_w4_region_boundaries_are_small_jumps(oracle_lib):
+    # the four rational forms meet within the approximation's own accuracy
+    for x, y in ((15.0 - 0.5 - 1e-9, 0.5), (5.5 - 0.3 - 1e-9, 0.3), (3.0, 0.195 * 3.0 - 0.176 - 1e-9)):
+        a = oracle_lib.w4(x, y)
+        b = oracle_lib.w4(x + 2e-9, y + (2e-9 if x == 3.0 else 0.0))
+        assert abs(a - b) / abs(b) < 2e-4
+        assert abs(a.real - b.real) / abs(b.real) < 2e-4
+
+
+def test_w4_derivative(oracle_lib):
+    """F'(t) is the derivative of the same piecewise form (complex finite difference
+    inside one region), and approximates the exact w'(z) = -2 z w + 2i/sqrt(pi)."""
+    for x, y in ((20.0, 0.5), (7.0, 0.3), (2.0, 1.0), (3.0, 0.05), (0.5, 0.01)):
+        w, d = oracle_lib.w4(x, y, deriv=True)
+        eps = 1e-6
+        fx = (oracle_lib.w4(x + eps, y) - oracle_lib.w4(x - eps, y)) / (2 * eps)
+        fy = (oracle_lib.w4(x, y + eps) - oracle_lib.w4(x, y - eps)) / (2 * eps)
+        # t = y - i x: dF/dx = -i F'(t), dF/dy = F'(t)
+        assert abs(fx - (-1j) * d) < 1e-6 * max(1.0, abs(d))
+        assert abs(fy - d) < 1e-6 * max(1.0, abs(d))
+        z = complex(x, y)
+        exact = -2 * z * sp.wofz(z) + 2j / math.sqrt(math.pi)
+        assert abs((-1j) * d - exact) < 5e-3 * abs(exact) + 1e-6
+
+
+def test_voigt_is_library_voigt_and_limits(oracle_lib):
+    a, g = 0.02, 0.03
+    sig = a / math.sqrt(2 * LN2)
+    for D in (0.0, 0.01, 0.05, -0.3, 5.0, 24.0):
+        assert oracle_lib.voigt_w4(D, a, g) == pytest.approx(sp.voigt_profile(D, sig, g), rel=1.2e-4)
+    # gamma -> 0: Gaussian ; alpha -> 0: Lorentzian (Eqs. e:Gauss, e:lor)
+    for D in (0.0, 0.01, 0.03):
+        assert oracle_lib.voigt_w4(D, a, 1e-9) == pytest.approx(oracle_lib.gauss(D, a), rel=1.2e-4)
+    for D in (0.0, 0.01, 0.3):
+        assert oracle_lib.voigt_w4(D, 1e-7, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1.2e-4)
+    assert oracle_lib.voigt_w4(0.037, a, g) == oracle_lib.voigt_w4(-0.037, a, g)
+
+
+def test_voigt_unit_area_bruteforce(oracle_lib):
+    a, g = 0.02, 0.01
+    val, _ = si.quad(lambda D: oracle_lib.voigt_w4(D, a, g), -200, 200, points=[0.0], limit=400)
+    assert val == pytest.approx(1.0, abs=2e-4)
+
+
+def test_gauss_hermite_nodes(oracle_lib):
+    for n in (1, 2, 5, 20, 30):
+        x, w = oracle_lib.gauss_hermite(n)
+        xr, wr = np.polynomial.hermite.hermgauss(n)
+        assert np.allclose(x, xr, atol=1e-13, rtol=0)
+        assert np.allclose(w, wr, rtol=1e-11, atol=1e-300)
+        assert w.sum() == pytest.approx(math.sqrt(math.pi), rel=1e-14)
+        for k in range(0, 2 * n, 2):  # exact for polynomials of degree <= 2n-1
+            assert np.dot(w, x ** k) == pytest.approx(math.gamma(k / 2 + 0.5), rel=1e-10)
+
+
+def test_gh_sampled_voigt_converges_to_voigt(oracle_lib):
+    # smooth case (gamma comparable to alpha): 30 nodes match the exact Voigt closely
+    a, g = 0.02, 0.03
+    sig = a / math.sqrt(2 * LN2)
+    for D in (0.0, 0.02, 0.1, 1.0):
+        assert oracle_lib.voigt_gh(D, a, g, 30) == pytest.approx(sp.voigt_profile(D, sig, g), rel=2e-3)
+    val, _ = si.quad(lambda D: oracle_lib.voigt_gh(D, a, g, 20), -np.inf, np.inf, limit=400)
+    assert val == pytest.approx(1.0, rel=1e-8)
+
+
+def test_gh_binned_telescopes_and_matches_bin_average(oracle_lib):
+    a, g, h = 0.02, 0.015, 0.01
+    x, w = oracle_lib.gauss_hermite(20)
+    # telescoping over bins k = -K..K: h * sum = pi^-3/2 sum_j w_j [atan(top) - atan(bot)]
+    K = 400
+    tot = sum(oracle_lib.voigt_gh_binned(k * h, h, a, g, 20) for k in range(-K, K + 1)) * h
+    top, bot = (K + 0.5) * h, -(K + 0.5) * h
+    expect = sum(w[j] * (math.atan((top - a * x[j] / math.sqrt(LN2)) / g)
+                         - math.atan((bot - a * x[j] / math.sqrt(LN2)) / g)) for j in range(20)) / math.pi ** 1.5
+    assert tot == pytest.approx(expect, rel=1e-12)
+    # bin average of the exact Voigt, within the quadrature error of 20 nodes
+    sig = a / math.sqrt(2 * LN2)
+    for D in (0.0, 0.01, 0.05, 0.5):
+        ex, _ = si.quad(lambda u: sp.voigt_profile(u, sig, g), D - h / 2, D + h / 2)
+        assert oracle_lib.voigt_gh_binned(D, h, a, g, 20) == pytest.approx(ex / h, rel=5e-3)
+
+
+# --------------------------------------------- full cross sections
+def _tiny_lines(n, seed=3, lo=1000.0, hi=1001.0):
+    return xs.gen_lines(seed, 0, n, lo, hi)
+
+
+@pytest.mark.parametrize("profile", ["doppler", "lorentz", "voigt_w4"])
+def test_cross_section_bruteforce(oracle_lib, profile):
+    L = _tiny_lines(7)
+    E, gst = xs.gen_states(3, 500)
+    T, P = 1200.0, 0.7
+    Q, _ = oracle_lib.partition_function(E, gst, T)
+    cond = oracle_lib.make_condition(T, P, Q)
+    nu_A, h, N, cut = 999.5, 0.02, 101, 0.6
+    sig = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts(profile, cut))
+    # independent brute force with library pdfs (scipy), direct per point
+    c2, c_cm = 1.438776877503933802, 2.99792458e10
+    out = np.zeros(N)
+    for k in range(N):
+        xk = nu_A + k * h
+        for l in range(7):
+            nu = float(L["nu"][l]); D = xk - nu
+            if abs(D) > cut:
+                continue
+            I = (float(L["g_up"][l]) * float(L["A"][l]) / (8 * math.pi * c_cm * nu * nu)
+                 * math.exp(-c2 * float(L["elower"][l]) / T) * (1 - math.exp(-c2 * nu / T)) / Q)
+            al = nu / 2.99792458e8 * math.sqrt(2 * 1.380649e-23 * T * LN2 / (18 * 1.66053906660e-27))
+            ga = float(L["gamma_ref"][l]) * (296.0 / T) ** float(L["n_T"][l]) * P
+            if profile == "doppler":
+                v = st.norm.pdf(D, scale=al / math.sqrt(2 * LN2))
+            elif profile == "lorentz":
+                v = st.cauchy.pdf(D, scale=ga)
+            else:
+                v = sp.voigt_profile(D, al / math.sqrt(2 * LN2), ga)
+            out[k] += I * v
+    tol = 1e-11 if profile != "voigt_w4" else 1.2e-4
+    mask = out > 0
+    assert np.array_equal(mask, sig > 0)
+    assert np.max(np.abs(sig[mask] - out[mask]) / out[mask]) < tol
+
+
+def test_cutoff_is_inclusive_and_ragged_edges(oracle_lib):
+    # a line whose cut lands exactly on grid points (all values exact in binary)
+    L = {"nu": np.array([1000.5]), "elower": np.array([0.0], np.float32), "A": np.array([1.0], np.float32),
+         "gamma_ref": np.array([0.0625], np.float32), "n_T": np.array([0.5], np.float32),
+         "g_up": np.array([1], np.int16), "j_lo": np.array([0], np.int16)}
+    cond = oracle_lib.make_condition(296.0, 1.0, 1.0)
+    sig = oracle_lib.cross_section(L, cond, 1000.0, 0.125, 9, oracle_lib.make_opts("lorentz", 0.25))
+    # points 1000.25 .. 1000.75 (k = 2..6) are within |D| <= 0.25
+    assert np.array_equal(np.nonzero(sig)[0], np.arange(2, 7))
+    # a line outside the grid still feeds the points within its cut
+    L2 = dict(L); L2["nu"] = np.array([999.9])
+    sig2 = oracle_lib.cross_section(L2, cond, 1000.0, 0.125, 9, oracle_lib.make_opts("lorentz", 0.25))
+    assert np.array_equal(np.nonzero(sig2)[0], np.array([0, 1]))
+    # empty line list and an empty grid
+    L0 = {k: v[:0] for k, v in L.items()}
+    assert np.all(oracle_lib.cross_section(L0, cond, 1000.0, 0.125, 9, oracle_lib.make_opts()) == 0)
+    assert oracle_lib.cross_section(L, cond, 1000.0, 0.125, 0, oracle_lib.make_opts()).shape == (0,)
+
+
+def test_sampled_area_equals_intensity(oracle_lib):
+    """Eq. (e:integr): a finely sampled line with a wide cut integrates to I; the truncated
+    Lorentzian integrates to I (2/pi) atan(cut/gamma)."""
+    L = {"nu": np.array([2000.003]), "elower": np.array([100.0], np.float32), "A": np.array([3.0], np.float32),
+         "gamma_ref": np.array([0.05], np.float32), "n_T": np.array([0.6], np.float32),
+         "g_up": np.array([5], np.int16), "j_lo": np.array([2], np.int16)}
+    cond = oracle_lib.make_condition(1000.0, 1.0, 100.0)
+    I = oracle_lib.intensity(2000.003, 100.0, 3.0, 5.0, cond)
+    ga = oracle_lib.gamma_lorentz(0.05, 0.6, cond)
+    h = 0.001
+    nu_A, N = 1990.0, 20001
+    s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("doppler", 5.0))
+    assert s.sum() * h == pytest.approx(I, rel=1e-9)
+    s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("lorentz", 5.0))
+    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=1e-6)
+    s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("voigt_gh_binned", 5.0))
+    # binned GH conserves the area of the truncated profile exactly (telescoping), ~ I atan-limited
+    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=2e-5)
+
+
+def test_threads_are_deterministic_and_agree(oracle_lib):
+    L = xs.gen_lines(21, 0, 3000, 1000.0, 1010.0)
+    cond = oracle_lib.make_condition(800.0, 1.0, 500.0)
+    a = oracle_lib.cross_section(L, cond, 995.0, 0.01, 2001, oracle_lib.make_opts("voigt_w4", 3.0), nthreads=1)
+    b = oracle_lib.cross_section(L, cond, 995.0, 0.01, 2001, oracle_lib.make_opts("voigt_w4", 3.0), nthreads=4)
+    c = oracle_lib.cross_section(L, cond, 995.0, 0.01, 2001, oracle_lib.make_opts("voigt_w4", 3.0), nthreads=4)
+    assert np.array_equal(b, c)
+    assert np.allclose(a, b, rtol=1e-14, atol=0)
+
+
+def test_width_limited_cut(oracle_lib):
+    L = xs.gen_lines(22, 0, 50, 1000.0, 1002.0)
+    cond = oracle_lib.make_condition(1500.0, 1.0, 500.0)
+    o = oracle_lib.make_opts("voigt_w4", 25.0, width_mult=10.0)
+    n = oracle_lib.count_evals(L, cond, 990.0, 0.01, 2201, o)
+    exp_n = 0
+    for l in range(50):
+        al = oracle_lib.alpha_doppler(L["nu"][l], cond)
+        ga = oracle_lib.gamma_lorentz(L["gamma_ref"][l], L["n_T"][l], cond)
+        cut = min(25.0, 10.0 * max(al, ga))
+        k = np.arange(2201)
+        exp_n += int(np.sum(np.abs((990.0 + k * 0.01) - L["nu"][l]) <= cut))
+    assert n == exp_n
+
+
+# --------------------------------------------- adjoint
+@pytest.mark.parametrize("profile", ["voigt_w4", "doppler", "lorentz", "voigt_gh_binned"])
+def test_vjp_matches_central_differences(oracle_lib, profile):
+    L = xs.gen_lines(31, 0, 6, 1000.0, 1000.5)
+    E, gst = xs.gen_states(31, 400)
+    nu_A, h, N, cut = 999.0, 0.01, 251, 1.0
+    o = oracle_lib.make_opts(profile, cut, n_gh=10)
+    rng = np.random.default_rng(0)
+    gs = rng.standard_normal(N)
+
+    def loss(T, P, s=1.0, dn=0.0, gref=None, nl=None):
+        Q, dQ = oracle_lib.partition_function(E, gst, T)
+        c = oracle_lib.make_condition(T, P, Q, dQ, gamma_scale=s, n_shift=dn)
+        LL = dict(L)
+        if gref is not None:
+            LL["gamma_ref"] = gref
+        if nl is not None:
+            LL["n_T"] = nl
+        return float(np.dot(gs, oracle_lib.cross_section(LL, c, nu_A, h, N, o)))
+
+    T, P = 900.0, 0.5
+    Q, dQ = oracle_lib.partition_function(E, gst, T)
+    c = oracle_lib.make_condition(T, P, Q, dQ)
+    g = oracle_lib.cross_section_vjp(L, [c], nu_A, h, N, o, gs)
+    rel = 1e-5
+
+    def fd(f, x):
+        d = x * rel
+        return (f(x + d) - f(x - d)) / (2 * d)
+
+    tol = dict(rel=2e-5, abs=1e-30)
+    assert g["dT"][0] == pytest.approx(fd(lambda t: loss(t, P), T), **tol)
+    assert g["dP"][0] == pytest.approx(fd(lambda p: loss(T, p), P), **tol)
+    assert g["d_gamma_scale"] == pytest.approx(fd(lambda s: loss(T, P, s=s), 1.0), **tol)
+    d = 1e-5
+    fdn = (loss(T, P, dn=d) - loss(T, P, dn=-d)) / (2 * d)
+    assert g["d_n_shift"] == pytest.approx(fdn, **tol)
+    # per-line gradients: perturb one line's gamma_ref (float64 copy so the step is exact)
+    # (line records are float32: use perturbed values that are exact float32 numbers)
+    l = 2
+    gref = L["gamma_ref"].copy()
+    vp = np.float32(gref[l] * (1 + 1e-4)); vm = np.float32(gref[l] * (1 - 1e-4))
+    def lg(v):
+        a = gref.copy(); a[l] = v
+        return loss(T, P, gref=a)
+    fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
+    assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4)
+    assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12)
