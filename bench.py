@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the line-list -> cross-section hot path on GB300.
+
+Workload (default): 1e8 synthetic lines, 8 temperatures x 4 pressures = 32
+(T, P) conditions, Voigt (Humlicek w4), grid 0..10000 cm^-1 step 0.01
+(1 000 001 points), cut 25 cm^-1, FP32 batched kernel.  One step = load the
+unsorted line list into the engine (device radix sort + gather), Q(T) for the
+8 temperatures, and the batched cross sections of all 32 conditions.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import xcsynth as xs  # noqa: E402
+
+METRIC = "line x gridpoint Voigt evals/s (FP32 batched, 32 conditions)"
+UNIT = "evals/s"
+ALG_FLOPS_PER_EVAL = 11  # w4 region-I rational with hoisted line constants (FMA = 2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="xc", choices=["xc", "reference"])
+    ap.add_argument("--workload", default="C3")
+    ap.add_argument("--lines", type=int, default=0, help="override the line count (smaller test runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 form on a subset")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    if args.gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        backend = "nccl" if args.impl == "xc" else "gloo"
+        dist.init_process_group(backend, rank=rank, world_size=world)
+        return dist, rank, world, local
+    return None, 0, 1, 0
+
+
+def make_workload(args, rank):
+    W = xs.WORKLOADS[args.workload]
+    n = args.lines or W.n_lines
+    seed = W.seed + 1000 * rank  # each rank its own independent problem (weak scaling)
+    t0 = time.time()
+    lines = xs.gen_lines(seed, 0, n, W.nu_lo, W.nu_hi)
+    E, g = xs.gen_states(seed, W.n_states)
+    return W, n, seed, lines, E, g, time.time() - t0
+
+
+# ---------------------------------------------------------------------------- reference arm
+def cpu_oracle_rate(W, lines, E, g, conds, budget_s=12.0, threads=None):
+    """Time the FP64 oracle (as it stands) on a bounded sample: the first lines of the
+    list, doubling until the run takes a few seconds; return evals/s."""
+    import oracle
+    oracle.build()
+    threads = threads or (os.cpu_count() or 1)
+    n_try = 500
+    total = len(lines["nu"])
+    best = None
+    while True:
+        sub = {k: v[:n_try] for k, v in lines.items()}
+        c = conds[len(conds) // 2]
+        Q, dQ = oracle.partition_function(E, g, c["T"])
+        oc = oracle.make_condition(c["T"], c["P"], Q, dQ, mass_da=W.mass_da)
+        op = oracle.make_opts(W.profile, W.cutoff, W.cutoff_width_mult, W.n_gh)
+        ev = oracle.count_evals(sub, oc, W.grid_lo, W.step, W.n_points, op)
+        t0 = time.perf_counter()
+        oracle.cross_section(sub, oc, W.grid_lo, W.step, W.n_points, op, nthreads=threads)
+        dt = time.perf_counter() - t0
+        best = (ev / dt, n_try, ev, dt)
+        if dt > budget_s / 4 or n_try >= total:
+            break
+        n_try = min(total, n_try * 4 if dt < budget_s / 40 else n_try * 2)
+    return {"value": best[0], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {best[1]} lines of the {W.name} list, 1 of {len(conds)} conditions, "
+                      f"full grid ({best[2]:.3g} evals in {best[3]:.1f} s)"}
+
+
+def run_reference(args, dist, rank, world):
+    if rank != 0:
+        return
+    W, n, seed, lines, E, g, _ = make_workload(args, rank)
+    conds = xs.conditions_for(W)
+    threads = os.cpu_count() or 1
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(W, lines, E, g, conds, budget_s=8.0, threads=threads)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    # evals of one full step of the workload, at the oracle's rate
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{W.name}: {n} lines, {len(conds)} (T,P) conditions, grid {W.n_points} pts, "
+                               f"cut {W.cutoff} cm-1, {W.profile}"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------- GB300 arm
+def run_xc(args, dist, rank, world, local):
+    import torch
+    import paper_1801_09803_gb300 as xc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    xc.build.build()
+    W, n, seed, lines, E, g, t_gen = make_workload(args, rank)
+    conds_py = xs.conditions_for(W)
+    conds = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da) for c in conds_py]
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    opts = xc.make_opts(W.profile, "fp32", W.cutoff, W.cutoff_width_mult, W.n_gh)
+    nc = len(conds)
+
+    # inputs resident in HBM (unsorted, as generated) and pinned host copies for e2e
+    dlines = {k: torch.from_numpy(v).to(dev) for k, v in lines.items()}
+    sigma = torch.empty((nc, W.n_points), dtype=torch.float64, device=dev)
+    eng = xc.Engine(local)
+    eng.set_states(E, g)
+    eng.set_timing(True)
+
+    def step_device():
+        eng.load_lines(dlines)
+        eng.cross_section_batched(conds, grid, opts, sigma)
+
+    # algorithmic work: pairs (line, grid point) inside the cut, summed over conditions
+    eng.load_lines(dlines)
+    evals = eng.count_evals(conds, grid, opts)
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prof_ms, sort_ms, launches = [], [], 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+            t = eng.timings()
+            prof_ms.append(t["profile"])
+            launches += eng.last_launch_count()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # load_lines' own launch count is reset by the batched call; count it separately
+    eng.load_lines(dlines)
+    load_launches = eng.last_launch_count()
+    sort_t = eng.timings()
+    launches += load_launches * args.steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = evals * args.steps * world / (ms / 1e3)
+
+    # end-to-end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hl = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in lines.items()}
+        hout = torch.empty((nc, W.n_points), dtype=torch.float64).pin_memory().numpy()
+        h2d = sum(v.nbytes for v in hl.values())
+        d2h = hout.nbytes
+        eng.load_lines(hl)
+        eng.cross_section_batched(conds, grid, opts, hout)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            eng.load_lines(hl)
+            eng.cross_section_batched(conds, grid, opts, hout)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": evals * args.steps * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3 / args.steps}
+
+    # FP64 plain form on the same GPU (subset of conditions) for the FP32 vs FP64 ratio
+    fp64 = None
+    if args.fp64_compare:
+        o64 = xc.make_opts(W.profile, "fp64", W.cutoff, W.cutoff_width_mult, W.n_gh)
+        eng.load_lines(dlines)
+        c1 = conds[:1]
+        s1 = torch.empty((1, W.n_points), dtype=torch.float64, device=dev)
+        eng.cross_section_batched(c1, grid, o64, s1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng.cross_section_batched(c1, grid, o64, s1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ev1 = eng.count_evals(c1, grid, o64)
+        fp64 = {"value": ev1 / dt, "unit": UNIT, "conditions": 1}
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    prof = statistics.mean(prof_ms) if prof_ms else None
+    peak_max = nsm * 128 * 2 * 2070e6 / 1e12
+    rl = None
+    if prof:
+        ach = evals * ALG_FLOPS_PER_EVAL / (prof / 1e3) / 1e12
+        rl = {"bound": "alu", "achieved": ach, "peak": peak_max, "unit": "TFLOP/s", "frac": ach / peak_max,
+              "traffic": None, "kernel": "k_gather_f32 (graph replay incl. setup kernels)",
+              "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+              "frac_at_sampled_clock": (ach / (nsm * 128 * 2 * sm_mhz * 1e6 / 1e12)) if sm_mhz else None,
+              "flops_per_eval": ALG_FLOPS_PER_EVAL, "kernel_ms": prof}
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_oracle_rate(W, lines, E, g, conds_py)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{W.name}: {n} lines (nu uniform in ({W.nu_lo:g},{W.nu_hi:g}]), {nc} (T,P) "
+                               f"conditions, grid {W.grid_lo:g}..{W.grid_hi:g} step {W.step:g} "
+                               f"({W.n_points} pts), cut {W.cutoff:g} cm-1, {W.profile}, FP32 batched",
+                   "evals_per_step": evals, "l2": "inputs larger than L2 (2.8 GB line list, 256 MB output)",
+                   "step": "device radix sort + gather of the unsorted list, Q(T), batched cross sections",
+                   "generation_s": round(t_gen, 1)},
+        "e2e": e2e, "roofline": rl, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "stage_ms": {"sort": sort_t["sort"], "gather": sort_t["gather"], "profile_mean": prof},
+    }
+    if fp64:
+        out["fp64_plain"] = fp64
+        out["fp32_over_fp64"] = (evals / (prof / 1e3)) / fp64["value"] if prof else None
+    print(json.dumps(out), flush=True)
+    eng.close()
+
+
+def main():
+    args = parse()
+    dist, rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, dist, rank, world)
+    else:
+        run_xc(args, dist, rank, world, local)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

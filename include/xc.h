@@ -1,0 +1,225 @@
+/*
+ * xc.h -- C ABI of libxc, a GB300 (sm_103a) engine that turns a molecular
+ * line list into absorption cross sections on a wavenumber grid, following
+ * the ExoCross method (Yurchenko, Al-Refaie & Tennyson 2018, arXiv:1801.09803).
+ *
+ * Conventions for every entry point
+ *   - All functions return xc_status (XC_OK = 0).  They never throw, abort or
+ *     exit; on failure xc_last_error() gives a message (thread-local, valid
+ *     until the next call on the same thread).
+ *   - Pointers passed in are borrowed for the duration of the call.  Outputs
+ *     are allocated by the caller.  A `mem` argument says whether the arrays
+ *     it covers are host (XC_MEM_HOST) or device (XC_MEM_DEVICE) memory; host
+ *     outputs are complete when the call returns, device outputs are complete
+ *     in stream order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls with host inputs or outputs
+ *     synchronise that stream before returning.
+ *   - Units (paper Table t:units): wavenumber cm^-1, temperature K, pressure
+ *     in units of P_ref, intensity cm/molecule, cross section
+ *     cm^2/molecule = cm/(molecule cm^-1).
+ *   - Per-line arrays that the library returns are in the library's sorted
+ *     order (ascending wavenumber, ties by input position);
+ *     xc_get_permutation() maps sorted position -> input position.
+ */
+#ifndef XC_H
+#define XC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int xc_status;
+enum {
+    XC_OK = 0,
+    XC_EINVAL = 1,        /* bad argument or invalid input values */
+    XC_ENOMEM = 2,        /* device or pinned host allocation failed */
+    XC_ECUDA = 3,         /* a CUDA runtime call failed */
+    XC_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    XC_EUNSUPPORTED = 5   /* valid request this build does not implement */
+};
+
+enum { XC_MEM_HOST = 0, XC_MEM_DEVICE = 1 };
+
+/* line profiles (paper Sec. 3) */
+enum {
+    XC_DOPPLER = 0,          /* Eq. (e:Gauss) with alpha_D of Eq. (e:alphaD) */
+    XC_LORENTZ = 1,          /* Eq. (e:lor) with gamma_L of Eq. (e:gamma_L) */
+    XC_VOIGT_W4 = 2,         /* Eq. (e:Voigt), w(z) by Humlicek's w4 */
+    XC_VOIGT_GH_BINNED = 3,  /* Eq. (e:sigma:quad): bin-averaged Gauss-Hermite (area-conserving) */
+    XC_VOIGT_GH_SAMPLED = 4  /* Eq. (e:V-quad): Gauss-Hermite sum sampled at the grid point */
+};
+
+/* arithmetic of the profile evaluation */
+enum {
+    XC_FP64_PLAIN = 0,  /* every step in FP64 */
+    XC_FP32 = 1         /* FP32 profile math and window accumulators; FP64 grid offsets,
+                           Q(T) and final accumulation */
+};
+
+/* xc_load_lines flags */
+enum { XC_ASSUME_SORTED = 1u };
+
+typedef struct xc_handle xc_handle;
+
+/* Line list, structure of arrays, n entries each (28 bytes per line).
+ * nu: transition wavenumber (float64, > 0, finite); elower: lower-state term
+ * value E'' (float32, finite, >= 0); A: Einstein coefficient (float32, >= 0);
+ * gamma_ref: Lorentz HWHM at T_ref, P_ref (float32, >= 0); n_T: temperature
+ * exponent (float32, finite); g_up: upper total degeneracy g_ns(2J'+1)
+ * (int16, >= 0); j_lo: lower J'' (int16, may be NULL: stored as 0).
+ * Paper: Eq. (e:int), Eq. (e:gamma_L), ExoMol .trans/.states fields (Sec. 5.1). */
+typedef struct {
+    const double *nu;
+    const float *elower;
+    const float *A;
+    const float *gamma_ref;
+    const float *n_T;
+    const int16_t *g_up;
+    const int16_t *j_lo;
+    int mem;  /* XC_MEM_HOST or XC_MEM_DEVICE, for all seven arrays */
+} xc_lines;
+
+/* One (T, P) condition.  gamma = gamma_scale * gamma_ref * (T_ref/T)^(n_T + n_shift)
+ * * P/P_ref (Eq. e:gamma_L); alpha from Eq. (e:alphaD) with m = mass_da daltons;
+ * I from Eq. (e:int) times `abundance`.  Q <= 0 means "compute Q(T) and dQ/dT
+ * from the states given to xc_set_states" (Eq. e:pf); otherwise Q and dQdT are
+ * used as given (dQdT only matters for the adjoint). */
+typedef struct {
+    double T, P, Q, dQdT;
+    double mass_da, T_ref, P_ref;
+    double gamma_scale, n_shift;
+    double abundance;
+} xc_condition;
+
+/* Equidistant grid nu_k = nu_A + k*step, k = 0..n-1 (Eq. e:Ngrid: n counts both ends). */
+typedef struct {
+    double nu_A;
+    double step;
+    int64_t n;
+} xc_grid;
+
+/* Profile options.  Each line contributes to grid points with |nu_k - nu_l| <= cut_l
+ * (inclusive), cut_l = cutoff, or min(cutoff, width_mult * max(alpha_l, gamma_l))
+ * when width_mult > 0 (Sec. 3.10 "Off-set").  n_gh: Gauss-Hermite nodes (1..64). */
+typedef struct {
+    int profile;        /* XC_DOPPLER .. XC_VOIGT_GH_SAMPLED */
+    int precision;      /* XC_FP64_PLAIN or XC_FP32 */
+    double cutoff;      /* cm^-1, > 0 */
+    double width_mult;  /* 0 = fixed cut */
+    int n_gh;
+    int flags;          /* reserved, 0 */
+} xc_opts;
+
+/* Library version string (static storage). */
+const char *xc_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *xc_last_error(void);
+
+/* Create a handle bound to CUDA device `device`; it owns the sorted line
+ * arrays, the states, scratch buffers, the autotune cache and CUDA graphs.
+ * EINVAL: bad device or NULL out pointer.  ENOMEM / ECUDA on failure. */
+xc_status xc_create(xc_handle **out, int device);
+
+/* Release everything the handle owns (NULL is accepted).  Synchronises the device. */
+xc_status xc_destroy(xc_handle *h);
+
+/* Copy n lines into the handle and sort them by wavenumber on the device
+ * (LSD radix sort on the float64 bit pattern; stable, so equal wavenumbers keep
+ * input order), then gather every field into sorted order.  Replaces any lines
+ * loaded before.  flags & XC_ASSUME_SORTED skips the sort but still checks the
+ * order (EINVAL if unsorted).  EINVAL: n >= 2^32, NULL arrays (except j_lo),
+ * nu <= 0 or non-finite, A < 0, gamma_ref < 0, non-finite elower/n_T.
+ * Paper: chunked reading of .trans lines (Sec. 5.3); ExoMol transitions are
+ * stored in wavenumber order (Table tab:trans). */
+xc_status xc_load_lines(xc_handle *h, const xc_lines *lines, size_t n, unsigned flags, void *stream);
+
+/* Number of lines held by the handle. */
+xc_status xc_num_lines(const xc_handle *h, size_t *n_out);
+
+/* Copy the sorted line arrays out (any pointer may be NULL to skip that field). */
+xc_status xc_get_lines(xc_handle *h, double *nu, float *elower, float *A, float *gamma_ref,
+                       float *n_T, int16_t *g_up, int16_t *j_lo, int mem, void *stream);
+
+/* Sorted position -> input position (uint32, n entries). */
+xc_status xc_get_permutation(xc_handle *h, uint32_t *perm_out, int mem, void *stream);
+
+/* Give the handle a state list (E term values cm^-1 float64, total degeneracy
+ * g int32 >= 0) for conditions with Q <= 0.  Paper Eq. (e:pf). */
+xc_status xc_set_states(xc_handle *h, const double *E, const int32_t *g, size_t n_states,
+                        int mem, void *stream);
+
+/* Partition function Q(T) = sum_n g_n exp(-c2 E_n / T) and dQ/dT for nT
+ * temperatures, in FP64 on the device (Eq. e:pf; Sec. 2.6).  E, g, T, Q_out,
+ * dQdT_out (nullable) all live in `mem`.  EINVAL: T <= 0, NULL E/g with
+ * n_states > 0.  No handle needed; uses the current device. */
+xc_status xc_partition_function(const double *E, const int32_t *g, size_t n_states,
+                                const double *T, size_t nT, double *Q_out, double *dQdT_out,
+                                int mem, void *stream);
+
+/* Per-line parameters for one condition, in FP64, in sorted order:
+ * I (Eq. e:int), alpha_D (Eq. e:alphaD), gamma_L (Eq. e:gamma_L).
+ * Any output may be NULL. */
+xc_status xc_line_params(xc_handle *h, const xc_condition *cond, double *I_out,
+                         double *alpha_out, double *gamma_out, int mem, void *stream);
+
+/* Number of (line, grid point) pairs inside the cutoff for these conditions:
+ * the algorithmic work of a cross section (host int64 output). */
+xc_status xc_count_evals(xc_handle *h, const xc_condition *conds, size_t n_cond,
+                         const xc_grid *grid, const xc_opts *opts, int64_t *count_out, void *stream);
+
+/* Cross section of one condition on the grid: sigma_k = sum_l I_l f_l(nu_k)
+ * over |nu_k - nu_l| <= cut_l (paper Sec. 3.1 "sampling method", Eq. e:cross;
+ * XC_VOIGT_GH_BINNED gives the bin average of Eq. e:sigma:quad).  Gather form:
+ * each CTA owns a window of grid points and visits only the lines whose cut
+ * reaches it; no global atomics, so results are bitwise reproducible.
+ * sigma_out: float64[grid->n] in `mem`.  EINVAL on bad grid/opts/condition,
+ * EUNSUPPORTED for an unknown profile/precision. */
+xc_status xc_cross_section(xc_handle *h, const xc_condition *cond, const xc_grid *grid,
+                           const xc_opts *opts, double *sigma_out, int mem, void *stream);
+
+/* n_cond conditions in one persistent launch that shares every staged line
+ * across conditions (sigma_out: float64[n_cond][grid->n], condition-major).
+ * opts->precision XC_FP32 uses the batched FP32 kernel (window size picked by
+ * the autotuner and cached per shape; the sweep is captured once into a CUDA
+ * graph and replayed); XC_FP64_PLAIN runs the FP64 kernel per condition. */
+xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size_t n_cond,
+                                   const xc_grid *grid, const xc_opts *opts, double *sigma_out,
+                                   int mem, void *stream);
+
+/* Vector-Jacobian product of the batched cross section.  Given
+ * grad_sigma = dL/dsigma (float64[n_cond][grid->n], in `mem`), returns
+ *   dT[c], dP[c]                      dL/dT_c, dL/dP_c          (n_cond each)
+ *   d_gamma_scale, d_n_shift          dL/d(gamma_scale), dL/d(n_shift), summed over conditions
+ *   d_gamma_ref_line, d_n_line        dL/d(gamma_ref_l), dL/d(n_l), sorted order (nullable)
+ * all float64 in `mem`.  dT includes dQ/dT through Q (from the states, or the
+ * condition's dQdT).  Profiles are recomputed, not stored; the cut is held
+ * fixed.  opts->precision selects FP32 (default) or FP64 recomputation; the
+ * reductions are FP64 and deterministic.  XC_DOPPLER, XC_LORENTZ, XC_VOIGT_W4
+ * only (EUNSUPPORTED otherwise).  Not in the paper: the chain rule of
+ * Eqs. (e:int), (e:alphaD), (e:gamma_L) and the profile. */
+xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n_cond,
+                               const xc_grid *grid, const xc_opts *opts, const double *grad_sigma,
+                               double *dT, double *dP, double *d_gamma_scale, double *d_n_shift,
+                               double *d_gamma_ref_line, double *d_n_line, int mem, void *stream);
+
+/* Stage timing: when enabled, the library records CUDA events on the launch
+ * stream around its kernels; xc_last_timings returns the milliseconds of the
+ * most recent call per stage: [0] sort, [1] gather/load, [2] Q(T), [3] line
+ * parameters, [4] window ranges, [5] profile kernel (or graph replay),
+ * [6] VJP kernel, [7] reduce/finish.  Stages not run read 0. */
+xc_status xc_set_timing(xc_handle *h, int enable);
+xc_status xc_last_timings(xc_handle *h, float *ms_out8);
+
+/* Kernel launches issued by the last call (for launch accounting). */
+xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XC_H */

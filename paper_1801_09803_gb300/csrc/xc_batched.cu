@@ -1,0 +1,884 @@
+// xc_batched.cu -- FP32 gather-form profile kernel over many (T, P) conditions.
+//
+// Work unit ("tile") = (window of W consecutive grid points, group of CG
+// conditions).  A persistent grid pulls tiles from an atomic work counter in
+// descending order of cost (lines in range x conditions; ranked on the device).
+// For its window a CTA walks the lines whose cut can reach the window (binary
+// search on the sorted wavenumbers), staging SCH lines at a time in shared
+// memory together with their per-condition constants, which are computed while
+// staging (the fused intensity / half-width step: Eq. e:int, e:alphaD, e:gamma_L).
+//
+// Thread layout: warp w owns the 32*R consecutive points [w*32R, (w+1)*32R) of
+// the window, lane j the points j + 32 r; every thread keeps R x CG FP32
+// accumulators in registers.  Offsets from line centre to grid point are
+// formed exactly: delta = (k - n_l) - f_l with n_l the integer and f_l the
+// fractional grid position of the line computed in FP64.
+//
+// Voigt (w4): Humlicek's region I (|x| + y >= 15), written in grid units as
+//     V = P (u + C) / (u (u + E) + F),   u = delta^2,
+// covers all but a few points next to each line centre.  Two lines that cover
+// the whole warp span with no region II-IV point are summed over one shared
+// reciprocal:  q1/D1 + q2/D2 = (q1 D2 + q2 D1) / (D1 D2).  Lines that straddle
+// the span edge of their cut, or whose centre zone (region II-IV for some
+// condition) reaches the span, take a masked single-line path that evaluates
+// the full w4 in FP32 at those points.
+//
+// Accumulation: FP32 in registers over FOLD_CHUNKS chunks of lines, then folded
+// into the FP64 output, which each thread owns exclusively (no atomics, fixed
+// order: bitwise reproducible).  Intensities are carried in FP32 multiplied by
+// a per-condition power of two that keeps the strongest possible line near
+// 1e10 (bound from max g A / nu^2 and max g A / nu over the list).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "xc_batched.cuh"
+
+namespace xc {
+
+constexpr int GT = 256;          // threads per CTA
+constexpr int NWARP = GT / 32;
+constexpr int SCH = 64;          // lines per staged chunk
+constexpr int FOLD_CHUNKS = 8;   // FP32 -> FP64 fold period, in chunks (512 lines)
+constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 region-I constant / sqrt(pi)
+constexpr float kSqrtLn2f = 0.8325546111576977f;
+constexpr float kSqrtLn2OverPi = 0.46971863934982566f;  // sqrt(ln2/pi)
+constexpr float kPiM32 = 0.17958712212516656f;          // pi^(-3/2)
+
+struct CParam {
+    double inv_scale;   // 1 / scale (power of two)
+    float kT_hi, kT_lo; // c2 log2(e) / T as a float pair
+    float c2T;          // c2 / T
+    float pref;         // abundance / (8 pi c Q) * scale
+    float acoef;        // alpha / nu
+    float log2Tr;       // log2(T_ref / T)
+    float pscale;       // gamma_scale * P / P_ref
+    float nshift;
+    float pad[2];
+};
+
+struct GeomStats {
+    unsigned int gA_nu2_bits;  // max g A / nu^2 (float bits; values >= 0)
+    unsigned int gA_nu_bits;   // max g A / nu
+};
+
+struct GatherParams {
+    LinesDev L;
+    const int *n_abs;          // per line: integer grid position (clamped)
+    const float *f_frac;       // per line: fractional grid position
+    const int *ka_abs, *kb_abs;// per line: inclusive grid-index range inside the cut
+    const CParam *cp;          // per condition
+    const unsigned *win_lo, *win_hi;
+    const int *tile_order;
+    int *counter;
+    int n_tiles, n_groups, n_cond;
+    int W;
+    int64_t n_pts;
+    float h, inv_h;
+    int max_lines_per_tile;    // autotune probe: stop early (0 = all)
+    const float *ghx, *ghw;    // Gauss-Hermite nodes (float), device
+    int ngh;
+    double *sigma;
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 2^(-z) for z >= 0 with the argument split into integer and fraction
+__device__ __forceinline__ float exp2_neg(float z) {
+    float zi = rintf(z);
+    float zf = z - zi;
+    if (zi > 125.f) return 0.f;
+    float b = ex2_approx(-zf);
+    return b * __int_as_float((127 - (int)zi) << 23);
+}
+
+// ---------------------------------------------------------------------------
+// per-condition constants
+// ---------------------------------------------------------------------------
+__global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cond) return;
+    const CondDev d = conds[c];
+    const double log2e = 1.4426950408889634;
+    double kT = kC2 * log2e / d.T;
+    float hi = (float)kT;
+    float lo = (float)(kT - (double)hi);
+    double pref = d.abundance / (8.0 * kPi * kLightCm * d.Q);
+    double s1 = (double)__uint_as_float(gs->gA_nu2_bits);
+    double s2 = (double)__uint_as_float(gs->gA_nu_bits);
+    double ib = pref * fmin(s1, kC2 / d.T * s2);  // bound on the largest intensity
+    int e2 = 0;
+    if (ib > 0.0 && isfinite(ib)) {
+        e2 = (int)floor(log2(1e10 / ib));
+        e2 = max(-120, min(120, e2));
+    }
+    double scale = ldexp(1.0, e2);
+    CParam p;
+    p.inv_scale = ldexp(1.0, -e2);
+    p.kT_hi = hi;
+    p.kT_lo = lo;
+    p.c2T = (float)(kC2 / d.T);
+    p.pref = (float)(pref * scale);
+    p.acoef = (float)alpha_coef(d.T, d.mass_da);
+    p.log2Tr = (float)log2(d.T_ref / d.T);
+    p.pscale = (float)(d.gamma_scale * d.P / d.P_ref);
+    p.nshift = (float)d.n_shift;
+    p.pad[0] = p.pad[1] = 0.f;
+    cp[c] = p;
+}
+
+// ---------------------------------------------------------------------------
+// per-line grid geometry (and the intensity bound statistics)
+// cond >= 0: per-line cut min(cutoff, width_mult * max(alpha, gamma)) of that condition
+// ---------------------------------------------------------------------------
+__global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int64_t n_pts, double cutoff,
+                            double width_mult, const CondDev *cond, int *n_abs, float *f_frac, int *ka_abs,
+                            int *kb_abs, GeomStats *gs) {
+    const double inv_h = 1.0 / step;
+    float m1 = 0.f, m2 = 0.f;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+        double nu = L.nu[l];
+        double cut = cutoff;
+        if (width_mult > 0.0 && cond) {
+            const CondDev c = *cond;
+            double al = alpha_coef(c.T, c.mass_da) * nu;
+            double ga = c.gamma_scale * (double)L.gamma_ref[l] *
+                        exp(((double)L.n_T[l] + c.n_shift) * log(c.T_ref / c.T)) * (c.P / c.P_ref);
+            cut = fmin(width_mult * fmax(al, ga), cutoff);
+        }
+        double d = (nu - nu_A) * inv_h;
+        double fl = floor(d);
+        double flc = fmin(fmax(fl, -1073741824.0), 1073741824.0);
+        n_abs[l] = (int)flc;
+        f_frac[l] = (float)(d - fl);
+        int64_t ka, kb;
+        line_k_range(nu, cut, nu_A, step, n_pts, &ka, &kb);
+        if (kb < ka) { ka = 1; kb = 0; }
+        ka_abs[l] = (int)i64min(i64max(ka, -1), (int64_t)0x7fffffff);
+        kb_abs[l] = (int)i64min(i64max(kb, -1), (int64_t)0x7fffffff);
+        float gA = (float)L.g_up[l] * L.A[l];
+        float nuf = (float)nu;
+        m1 = fmaxf(m1, gA / (nuf * nuf));
+        m2 = fmaxf(m2, gA / nuf);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (isfinite(m1)) atomicMax(&gs->gA_nu2_bits, __float_as_uint(m1));
+        if (isfinite(m2)) atomicMax(&gs->gA_nu_bits, __float_as_uint(m2));
+    }
+}
+
+// window -> line range for a fixed maximum cut
+__global__ void k_win_ranges32(const double *__restrict__ nu, int64_t n, double nu_A, double step, int64_t n_pts,
+                               int W, double cutmax, int n_win, unsigned *lo, unsigned *hi) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_win) return;
+    int64_t k0 = (int64_t)w * W;
+    int64_t k1 = i64min(k0 + W, n_pts) - 1;
+    double x0 = grid_x(nu_A, step, k0), x1 = grid_x(nu_A, step, k1);
+    double margin = cutmax * (1.0 + 1e-12) + 1e-12 * (fabs(x0) + fabs(x1)) + 1e-300;
+    int64_t a = 0, b = n;
+    double t = x0 - margin;
+    while (a < b) { int64_t m = a + ((b - a) >> 1); if (nu[m] < t) a = m + 1; else b = m; }
+    lo[w] = (unsigned)a;
+    int64_t a2 = a, b2 = n;
+    t = x1 + margin;
+    while (a2 < b2) { int64_t m = a2 + ((b2 - a2) >> 1); if (nu[m] <= t) a2 = m + 1; else b2 = m; }
+    hi[w] = (unsigned)a2;
+}
+
+// rank tiles by decreasing cost (ties by index): order[rank] = tile
+__global__ void k_rank_tiles(const unsigned *lo, const unsigned *hi, int n_win, int n_groups, int n_tiles,
+                             int *order, bool do_rank) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    if (!do_rank) {  // very many tiles: keep index order
+        order[t] = t;
+        return;
+    }
+    unsigned ct = hi[t / n_groups] - lo[t / n_groups];
+    int rank = 0;
+    for (int u = 0; u < n_tiles; ++u) {
+        unsigned cu = hi[u / n_groups] - lo[u / n_groups];
+        rank += (cu > ct) || (cu == ct && u < t);
+    }
+    order[rank] = t;
+}
+
+__global__ void k_nodes_to_float(const double *x, const double *w, int n, float *xf, float *wf) {
+    int j = threadIdx.x;
+    if (j < n) {
+        xf[j] = (float)x[j];
+        wf[j] = (float)w[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-(line, condition) constants, by profile
+//   W4 : A = {E', F', P', P'C'}   B = {a, y, Pv, thr^2}   (grid units)
+//   LOR: A = {G', P', 0, 0}
+//   DOP: A = {qd, Pd, 0, 0}
+//   GHS: A = {sh, G', P, 0}
+//   GHB: A = {sh, g', G' - 1/4, P}
+// ---------------------------------------------------------------------------
+template <int PROF>
+__device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
+                                            float4 *A, float4 *B, float *thr2) {
+    const float nu = (float)L.nu[l];
+    const float E = L.elower[l];
+    // Boltzmann factor exp(-c2 E/T) = 2^-(E c2 log2e / T), product kept to ~1 ulp
+    float z = fmaf(E, c.kT_hi, E * c.kT_lo);
+    float boltz = exp2_neg(z);
+    float stim = -expm1f(-c.c2T * nu);
+    float I = c.pref * ((float)L.g_up[l] * L.A[l]) / (nu * nu) * boltz * stim;
+    float al = c.acoef * nu;                                                   // Eq. e:alphaD
+    float ga = c.pscale * L.gamma_ref[l] * ex2_approx((L.n_T[l] + c.nshift) * c.log2Tr);  // Eq. e:gamma_L
+    float ah = al * inv_h, gh = ga * inv_h;   // widths in grid steps
+    *thr2 = -1.f;
+    if (PROF == XC_VOIGT_W4) {
+        float b = ah * ah * (float)(0.5 / 0.6931471805599453);
+        float g2 = gh * gh;
+        float C = b + g2;
+        float P = I * kKappa * gh * inv_h;
+        *A = make_float4(2.f * (g2 - b), C * C, P, P * C);
+        float a = kSqrtLn2f / ah;  // x = a |delta|
+        float y = a * gh;
+        float Pv = I * kSqrtLn2OverPi / al;
+        float thr = (15.f - y) / a;
+        float t2 = y < 15.f ? thr * thr : -1.f;
+        *B = make_float4(a, y, Pv, t2);
+        *thr2 = t2;
+    } else if (PROF == XC_LORENTZ) {
+        *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
+    } else if (PROF == XC_DOPPLER) {
+        float qd = 1.f / (ah * ah);
+        *A = make_float4(qd, I * kSqrtLn2OverPi / al, 0.f, 0.f);
+    } else if (PROF == XC_VOIGT_GH_SAMPLED) {
+        *A = make_float4(ah / kSqrtLn2f, fmaxf(gh * gh, 1e-30f), I * kPiM32 * gh * inv_h, 0.f);
+    } else {
+        *A = make_float4(ah / kSqrtLn2f, gh, gh * gh - 0.25f, I * kPiM32 * inv_h);
+    }
+}
+
+// full FP32 w4 Voigt value (all regions) times Pv, at grid offset delta
+__device__ __noinline__ float w4_value_f32(float delta, const float4 &B) {
+    float x = B.x * fabsf(delta);
+    Cx<float> w = w4_eval<float>(x, B.y, nullptr);
+    return B.z * w.re;
+}
+
+template <int PROF>
+__device__ __forceinline__ float contrib_single(float u, float delta, const float4 &A, const float4 &B,
+                                                const float *s_x, const float *s_w, int ngh) {
+    if (PROF == XC_VOIGT_W4) {
+        if (u < B.w) return w4_value_f32(delta, B);
+        float D = fmaf(u, u + A.x, A.y);
+        float q = fmaf(A.z, u, A.w);
+        return q * rcp_approx(D);
+    } else if (PROF == XC_LORENTZ) {
+        return A.y * rcp_approx(u + A.x);
+    } else if (PROF == XC_DOPPLER) {
+        return A.y * ex2_approx(-A.x * u);
+    } else if (PROF == XC_VOIGT_GH_SAMPLED) {
+        float s = 0.f;
+        for (int j = 0; j < ngh; ++j) {
+            float e = fmaf(-A.x, s_x[j], delta);
+            s = fmaf(s_w[j], rcp_approx(fmaf(e, e, A.y)), s);
+        }
+        return A.z * s;
+    } else {
+        float s = 0.f;
+        for (int j = 0; j < ngh; ++j) {
+            float e = fmaf(-A.x, s_x[j], delta);
+            s = fmaf(s_w[j], atan2f(A.y, fmaf(e, e, A.z)), s);
+        }
+        return A.w * s;
+    }
+}
+
+// FP32 register partials -> FP64 output (each thread owns its points)
+template <int R, int CG>
+__device__ __forceinline__ void fold_acc(float (&acc)[R][CG], const int (&ji)[R], int64_t kw, int grp,
+                                         const GatherParams &p, const double *sScale, bool first) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int64_t k = kw + ji[r];
+        if (k < p.n_pts) {
+#pragma unroll
+            for (int c = 0; c < CG; ++c) {
+                int cc = grp * CG + c;
+                if (cc < p.n_cond) {
+                    double *dst = p.sigma + (size_t)cc * (size_t)p.n_pts + (size_t)k;
+                    double v = (double)acc[r][c] * sScale[c];
+                    if (first) *dst = v; else *dst += v;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[r][c] = 0.f;
+    }
+}
+
+template <int PROF, int R, int CG>
+struct SmemLayout {
+    static constexpr bool kHasB = (PROF == XC_VOIGT_W4);
+    static constexpr size_t kA = (size_t)SCH * CG * sizeof(float4);
+    static constexpr size_t kB = kHasB ? kA : 0;
+    static constexpr size_t kMetaI = (size_t)SCH * sizeof(int4);
+    static constexpr size_t kMetaF = (size_t)SCH * sizeof(float2);
+    static constexpr size_t kScale = (size_t)CG * sizeof(double);
+    static constexpr size_t kNodes = 2 * 64 * sizeof(float);
+    static constexpr size_t total = kA + kB + kMetaI + kMetaF + kScale + kNodes + 16;
+};
+
+template <int PROF, int R, int CG>
+__global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherParams p) {
+    using Lay = SmemLayout<PROF, R, CG>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *sA = reinterpret_cast<float4 *>(smem);
+    float4 *sB = reinterpret_cast<float4 *>(smem + Lay::kA);
+    int4 *sMi = reinterpret_cast<int4 *>(smem + Lay::kA + Lay::kB);
+    float2 *sMf = reinterpret_cast<float2 *>(smem + Lay::kA + Lay::kB + Lay::kMetaI);
+    double *sScale = reinterpret_cast<double *>(smem + Lay::kA + Lay::kB + Lay::kMetaI + Lay::kMetaF);
+    float *sX = reinterpret_cast<float *>(smem + Lay::kA + Lay::kB + Lay::kMetaI + Lay::kMetaF + Lay::kScale);
+    float *sW = sX + 64;
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int W = p.W;
+    const int span0 = warp * 32 * R, span1 = span0 + 32 * R - 1;
+    if (PROF == XC_VOIGT_GH_BINNED || PROF == XC_VOIGT_GH_SAMPLED) {
+        if (tid < p.ngh) {
+            sX[tid] = p.ghx[tid];
+            sW[tid] = p.ghw[tid];
+        }
+    }
+    float jf[R];
+    int ji[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ji[r] = span0 + r * 32 + lane;
+        jf[r] = (float)ji[r];
+    }
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= p.n_tiles) break;
+        const int tile = p.tile_order[t];
+        const int win = tile / p.n_groups, grp = tile % p.n_groups;
+        const int64_t kw = (int64_t)win * W;
+        const unsigned lo = p.win_lo[win];
+        unsigned hi = p.win_hi[win];
+        if (p.max_lines_per_tile > 0 && hi - lo > (unsigned)p.max_lines_per_tile) hi = lo + p.max_lines_per_tile;
+        if (tid < CG) {
+            int c = grp * CG + tid;
+            sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
+        }
+        __syncthreads();
+        float acc[R][CG];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < CG; ++c) acc[r][c] = 0.f;
+        bool first_fold = true;
+        int chunk = 0;
+
+        for (unsigned l0 = lo; l0 < hi; l0 += SCH) {
+            const int cnt = (int)(hi - l0 < (unsigned)SCH ? hi - l0 : (unsigned)SCH);
+            __syncthreads();
+            // ---- stage: per-line geometry and per-(line, condition) constants
+            if (tid < cnt) {
+                size_t l = (size_t)l0 + tid;
+                int na = p.n_abs[l];
+                int ka = p.ka_abs[l], kb = p.kb_abs[l];
+                int64_t kaw = (int64_t)ka - kw, kbw = (int64_t)kb - kw;
+                if (kb < ka) { kaw = 1; kbw = 0; }
+                kaw = i64max(-1, i64min(kaw, W));
+                kbw = i64max(-1, i64min(kbw, W));
+                sMi[tid] = make_int4((int)((int64_t)na - kw), (int)kaw, (int)kbw, 0);
+                sMf[tid].x = p.f_frac[l];
+            }
+#pragma unroll 1
+            for (int pb = 0; pb < SCH * CG; pb += GT) {
+                int q = pb + tid;
+                int i = q / CG, c = q % CG;
+                int cc = grp * CG + c;
+                bool v = (i < cnt);
+                float t2 = -1.f;
+                if (v) {
+                    float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
+                    if (cc < p.n_cond) {
+                        line_consts<PROF>(p.L, (size_t)l0 + i, p.cp[cc], p.h, p.inv_h, &A, &B, &t2);
+                    } else {  // padding condition: contributes exactly 0
+                        if (PROF == XC_VOIGT_W4) A = make_float4(1.f, 1.f, 0.f, 0.f);
+                        else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
+                        else if (PROF == XC_VOIGT_GH_BINNED) A = make_float4(0.f, 1.f, 1.f, 0.f);
+                        else A = make_float4(1.f, 0.f, 0.f, 0.f);
+                    }
+                    sA[i * CG + c] = A;
+                    if (Lay::kHasB) sB[i * CG + c] = B;
+                }
+                if (CG > 1) {
+#pragma unroll
+                    for (int o = CG / 2; o > 0; o >>= 1) t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
+                }
+                if (v && c == 0) sMf[i].y = t2;
+            }
+            __syncthreads();
+
+            // ---- evaluate: classify lines for this warp's span, then accumulate
+            for (int ib = 0; ib < cnt; ib += 32) {
+                int i = ib + lane;
+                bool fast = false, slow = false;
+                if (i < cnt) {
+                    int4 mi = sMi[i];
+                    float2 mf = sMf[i];
+                    bool none = (mi.z < span0) || (mi.y > span1) || (mi.y > mi.z);
+                    bool full = (mi.y <= span0) && (mi.z >= span1);
+                    bool core = false;
+                    if (PROF == XC_VOIGT_W4 && mf.y > 0.f) {
+                        float cpos = (float)mi.x + mf.x;
+                        float thr = sqrtf(mf.y) + 1.f;
+                        core = (cpos + thr >= (float)span0) && (cpos - thr <= (float)span1);
+                    }
+                    bool pairable = (PROF == XC_VOIGT_W4 || PROF == XC_LORENTZ);
+                    fast = !none && full && !core && pairable;
+                    slow = !none && !fast;
+                }
+                unsigned fm = __ballot_sync(0xffffffffu, fast);
+                unsigned sm = __ballot_sync(0xffffffffu, slow);
+                if (PROF == XC_VOIGT_W4 || PROF == XC_LORENTZ) {
+                    while (__popc(fm) >= 2) {
+                        int i1 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        int i2 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int4 m1 = sMi[i1], m2 = sMi[i2];
+                        const float f1 = sMf[i1].x, f2 = sMf[i2].x;
+                        const float n1 = (float)m1.x, n2 = (float)m2.x;
+                        float u1[R], u2[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            float d1 = (jf[r] - n1) - f1;
+                            float d2 = (jf[r] - n2) - f2;
+                            u1[r] = d1 * d1;
+                            u2[r] = d2 * d2;
+                        }
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            const float4 A1 = sA[i1 * CG + c], A2 = sA[i2 * CG + c];
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                float D1, D2, q1, q2;
+                                if (PROF == XC_VOIGT_W4) {
+                                    D1 = fmaf(u1[r], u1[r] + A1.x, A1.y);
+                                    D2 = fmaf(u2[r], u2[r] + A2.x, A2.y);
+                                    q1 = fmaf(A1.z, u1[r], A1.w);
+                                    q2 = fmaf(A2.z, u2[r], A2.w);
+                                } else {
+                                    D1 = u1[r] + A1.x;
+                                    D2 = u2[r] + A2.x;
+                                    q1 = A1.y;
+                                    q2 = A2.y;
+                                }
+                                float num = fmaf(q1, D2, q2 * D1);
+                                acc[r][c] = fmaf(num, rcp_approx(D1 * D2), acc[r][c]);
+                            }
+                        }
+                    }
+                    sm |= fm;  // a leftover unpaired fast line takes the single path
+                }
+                while (sm) {
+                    int i1 = ib + __ffs(sm) - 1;
+                    sm &= sm - 1;
+                    const int4 m1 = sMi[i1];
+                    const float f1 = sMf[i1].x;
+                    const float n1 = (float)m1.x;
+                    float d1[R], u1[R];
+                    bool in1[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        d1[r] = (jf[r] - n1) - f1;
+                        u1[r] = d1[r] * d1[r];
+                        in1[r] = (ji[r] >= m1.y) && (ji[r] <= m1.z);
+                    }
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        const float4 A1 = sA[i1 * CG + c];
+                        const float4 B1 = Lay::kHasB ? sB[i1 * CG + c] : make_float4(0.f, 0.f, 0.f, -1.f);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            if (in1[r]) acc[r][c] += contrib_single<PROF>(u1[r], d1[r], A1, B1, sX, sW, p.ngh);
+                        }
+                    }
+                }
+            }
+            if (++chunk == FOLD_CHUNKS) {
+                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold);
+                first_fold = false;
+                chunk = 0;
+            }
+        }
+        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel table
+// ---------------------------------------------------------------------------
+typedef void (*GatherFn)(GatherParams);
+struct Variant {
+    int profile, R, CG;
+    GatherFn fn;
+    size_t smem;
+};
+
+#define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG>, SmemLayout<P, R, CG>::total}
+static const Variant kVariants[] = {
+    XC_VARIANT(XC_VOIGT_W4, 4, 16), XC_VARIANT(XC_VOIGT_W4, 2, 32), XC_VARIANT(XC_VOIGT_W4, 4, 8),
+    XC_VARIANT(XC_VOIGT_W4, 8, 4),  XC_VARIANT(XC_VOIGT_W4, 8, 2),  XC_VARIANT(XC_VOIGT_W4, 8, 1),
+    XC_VARIANT(XC_LORENTZ, 4, 16),  XC_VARIANT(XC_LORENTZ, 8, 4),   XC_VARIANT(XC_LORENTZ, 8, 1),
+    XC_VARIANT(XC_DOPPLER, 4, 16),  XC_VARIANT(XC_DOPPLER, 8, 4),   XC_VARIANT(XC_DOPPLER, 8, 1),
+    XC_VARIANT(XC_VOIGT_GH_SAMPLED, 4, 16), XC_VARIANT(XC_VOIGT_GH_SAMPLED, 8, 4),
+    XC_VARIANT(XC_VOIGT_GH_SAMPLED, 8, 1),
+    XC_VARIANT(XC_VOIGT_GH_BINNED, 4, 16), XC_VARIANT(XC_VOIGT_GH_BINNED, 8, 4),
+    XC_VARIANT(XC_VOIGT_GH_BINNED, 8, 1),
+};
+static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+#define BT_TRY(call)                                                                            \
+    do {                                                                                        \
+        cudaError_t _e = (call);                                                                \
+        if (_e == cudaErrorMemoryAllocation) {                                                  \
+            cudaGetLastError();                                                                 \
+            set_error("device allocation failed: %s", #call);                                   \
+            return XC_ENOMEM;                                                                   \
+        }                                                                                       \
+        if (_e != cudaSuccess) {                                                                \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+            return XC_ECUDA;                                                                    \
+        }                                                                                       \
+    } while (0)
+
+int num_sms(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// Everything the persistent kernel needs, carved out of the state's buffers.
+struct Plan {
+    const Variant *v = nullptr;
+    int W = 0, n_win = 0, n_groups = 0, n_tiles = 0, grid = 0;
+    int *n_abs = nullptr, *ka = nullptr, *kb = nullptr;
+    float *f = nullptr;
+    CParam *cp = nullptr;
+    unsigned *lo = nullptr, *hi = nullptr;
+    int *order = nullptr, *counter = nullptr;
+    GeomStats *gs = nullptr;
+    float *gx = nullptr, *gw = nullptr;
+};
+
+xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl) {
+    const size_t n = a.n_lines;
+    pl->v = v;
+    pl->W = GT * v->R;
+    pl->n_win = (int)((a.grid.n + pl->W - 1) / pl->W);
+    pl->n_groups = (n_cond_call + v->CG - 1) / v->CG;
+    pl->n_tiles = pl->n_win * pl->n_groups;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    size_t o_n = carve(n * 4), o_f = carve(n * 4), o_ka = carve(n * 4), o_kb = carve(n * 4);
+    size_t o_cp = carve((size_t)n_cond_call * sizeof(CParam));
+    size_t o_lo = carve((size_t)pl->n_win * 4), o_hi = carve((size_t)pl->n_win * 4);
+    size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
+    BT_TRY(st->tiles.ensure(off));
+    char *b = st->tiles.as<char>();
+    pl->n_abs = (int *)(b + o_n);
+    pl->f = (float *)(b + o_f);
+    pl->ka = (int *)(b + o_ka);
+    pl->kb = (int *)(b + o_kb);
+    pl->cp = (CParam *)(b + o_cp);
+    pl->lo = (unsigned *)(b + o_lo);
+    pl->hi = (unsigned *)(b + o_hi);
+    pl->order = (int *)(b + o_ord);
+    pl->counter = (int *)(b + o_ctr);
+    pl->gs = (GeomStats *)(b + o_gs);
+    pl->gx = (float *)(b + o_nodes);
+    pl->gw = pl->gx + 64;
+    return XC_OK;
+}
+
+// enqueue the whole sweep for conditions [c0, c0 + nc) on the stream
+xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid, int max_lines, int64_t *launches,
+                  bool per_cond_cut) {
+    cudaStream_t s = a.stream;
+    const size_t n = a.n_lines;
+    unsigned gblocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    if (gblocks == 0) gblocks = 1;
+    BT_TRY(cudaMemsetAsync(pl.gs, 0, sizeof(GeomStats), s));
+    k_line_geom<<<gblocks, 256, 0, s>>>(a.L, n, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
+                                        per_cond_cut ? a.opts.width_mult : 0.0,
+                                        per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
+                                        pl.gs);
+    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp);
+    k_win_ranges32<<<(pl.n_win + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
+                                                           pl.W, a.opts.cutoff, pl.n_win, pl.lo, pl.hi);
+    k_rank_tiles<<<(pl.n_tiles + 127) / 128, 128, 0, s>>>(pl.lo, pl.hi, pl.n_win, pl.n_groups, pl.n_tiles,
+                                                          pl.order, pl.n_tiles <= 16384);
+    *launches += 4;
+    if (a.ghx) {
+        k_nodes_to_float<<<1, 64, 0, s>>>(a.ghx, a.ghw, a.opts.n_gh, pl.gx, pl.gw);
+        *launches += 1;
+    }
+    BT_TRY(cudaMemsetAsync(pl.counter, 0, sizeof(int), s));
+    GatherParams gp;
+    gp.L = a.L;
+    gp.n_abs = pl.n_abs;
+    gp.f_frac = pl.f;
+    gp.ka_abs = pl.ka;
+    gp.kb_abs = pl.kb;
+    gp.cp = pl.cp;
+    gp.win_lo = pl.lo;
+    gp.win_hi = pl.hi;
+    gp.tile_order = pl.order;
+    gp.counter = pl.counter;
+    gp.n_tiles = pl.n_tiles;
+    gp.n_groups = pl.n_groups;
+    gp.n_cond = nc;
+    gp.W = pl.W;
+    gp.n_pts = a.grid.n;
+    gp.h = (float)a.grid.step;
+    gp.inv_h = (float)(1.0 / a.grid.step);
+    gp.max_lines_per_tile = max_lines;
+    gp.ghx = pl.gx;
+    gp.ghw = pl.gw;
+    gp.ngh = a.opts.n_gh;
+    gp.sigma = a.sigma + (size_t)c0 * (size_t)a.grid.n;
+    pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
+    *launches += 1;
+    BT_TRY(cudaGetLastError());
+    return XC_OK;
+}
+
+std::string shape_key(const BatchedArgs &a, int nc) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "p%d n%zu c%d g%lld/%.17g/%.17g cut%.17g wm%.17g gh%d", a.opts.profile,
+             a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff, a.opts.width_mult,
+             a.opts.n_gh);
+    return buf;
+}
+
+xc_status configure_variant(const Variant *v, int dev) {
+    static bool done[64] = {};
+    int idx = (int)(v - kVariants);
+    if (done[idx]) return XC_OK;
+    BT_TRY(cudaFuncSetAttribute((const void *)v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
+    done[idx] = true;
+    (void)dev;
+    return XC_OK;
+}
+
+int grid_size(const Variant *v, int dev, int n_tiles) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)v->fn, GT, v->smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int g = num_sms(dev) * per_sm;
+    return std::max(1, std::min(g, n_tiles));
+}
+
+// Autotune: time each candidate variant on a probe (every tile, first 4096 lines)
+// and predict the full run from the measured time per (tile line x condition);
+// the prediction includes the wave quantisation of the tile count.
+xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out, int64_t *launches) {
+    std::string key = shape_key(a, nc);
+    auto it = st->tuned.find(key);
+    if (it != st->tuned.end()) {
+        *out = it->second;
+        return XC_OK;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<int> cands;
+    for (int i = 0; i < kNumVariants; ++i) {
+        const Variant &v = kVariants[i];
+        if (v.profile != a.opts.profile) continue;
+        if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
+        if (v.CG > 1 && v.CG / 2 >= nc) continue;             // no more than half the group padded
+        cands.push_back(i);
+    }
+    if (cands.empty()) {
+        set_error("no FP32 kernel variant for profile %d", a.opts.profile);
+        return XC_EUNSUPPORTED;
+    }
+    TileCfg best;
+    best.variant = cands[0];
+    best.points = GT * kVariants[cands[0]].R;
+    best.cgroup = kVariants[cands[0]].CG;
+    best.ms = 0.f;
+    if (cands.size() > 1) {
+        cudaEvent_t e0, e1;
+        BT_TRY(cudaEventCreate(&e0));
+        BT_TRY(cudaEventCreate(&e1));
+        float best_pred = 1e30f;
+        for (int vi : cands) {
+            const Variant *v = &kVariants[vi];
+            xc_status s = configure_variant(v, dev);
+            if (s) return s;
+            Plan pl;
+            int ncv = a.opts.width_mult > 0.0 ? 1 : nc;
+            if ((s = make_plan(st, a, v, ncv, &pl))) return s;
+            int grid = grid_size(v, dev, pl.n_tiles);
+            const int probe_lines = 4096;
+            if ((s = enqueue(a, pl, 0, ncv, grid, probe_lines, launches, a.opts.width_mult > 0.0))) return s;
+            BT_TRY(cudaEventRecord(e0, a.stream));
+            if ((s = enqueue(a, pl, 0, ncv, grid, probe_lines, launches, a.opts.width_mult > 0.0))) return s;
+            BT_TRY(cudaEventRecord(e1, a.stream));
+            BT_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BT_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            // measured: all tiles, <= probe_lines lines each. Predict for the full line count:
+            std::vector<unsigned> lo(pl.n_win), hi(pl.n_win);
+            BT_TRY(cudaMemcpy(lo.data(), pl.lo, pl.n_win * 4, cudaMemcpyDeviceToHost));
+            BT_TRY(cudaMemcpy(hi.data(), pl.hi, pl.n_win * 4, cudaMemcpyDeviceToHost));
+            double probe_max = 0.0, full_work = 0.0, max_tile = 0.0, probe_sum = 0.0;
+            for (int w = 0; w < pl.n_win; ++w) {
+                double cntl = (double)(hi[w] - lo[w]);
+                double pc = std::min(cntl, (double)probe_lines);
+                probe_sum += pc;
+                probe_max = std::max(probe_max, pc);
+                full_work += cntl;
+                max_tile = std::max(max_tile, cntl);
+            }
+            // time per tile-line for one slot, from waves x mean probe tile
+            double waves = std::ceil((double)pl.n_tiles / grid);
+            double probe_avg = probe_sum / pl.n_win;
+            double t_line = (probe_avg > 0 && waves > 0) ? ms / (waves * probe_avg) : 0.0;
+            double avg_tile = full_work / pl.n_win;
+            double pred = t_line * std::max(waves * avg_tile, max_tile);
+            if (pred < best_pred) {
+                best_pred = (float)pred;
+                best.variant = vi;
+                best.points = pl.W;
+                best.cgroup = v->CG;
+                best.ms = (float)pred;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    st->tuned[key] = best;
+    *out = best;
+    return XC_OK;
+}
+
+}  // namespace
+
+xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches) {
+    if (a.grid.n >= ((int64_t)1 << 31) - (1 << 20)) {
+        set_error("the FP32 path needs fewer than 2^31 grid points");
+        return XC_EINVAL;
+    }
+    if (a.n_lines == 0 || a.n_cond == 0 || a.grid.n == 0) return XC_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    TileCfg cfg;
+    xc_status s = autotune(st, a, a.n_cond, &cfg, launches);
+    if (s) return s;
+    const Variant *v = &kVariants[cfg.variant];
+    if ((s = configure_variant(v, dev))) return s;
+    const bool per_cond = a.opts.width_mult > 0.0;
+    if (per_cond) {
+        // per-condition cut: one launch sequence per condition
+        if (a.timing) cudaEventRecord(a.ev_begin, a.stream);
+        for (int c = 0; c < a.n_cond; ++c) {
+            Plan pl;
+            if ((s = make_plan(st, a, v, 1, &pl))) return s;
+            if ((s = enqueue(a, pl, c, 1, grid_size(v, dev, pl.n_tiles), 0, launches, true))) return s;
+        }
+        if (a.timing) cudaEventRecord(a.ev_end, a.stream);
+        return XC_OK;
+    }
+    Plan pl;
+    if ((s = make_plan(st, a, v, a.n_cond, &pl))) return s;
+    const int grid = grid_size(v, dev, pl.n_tiles);
+    // graph cache: the sweep (geometry, constants, ranges, tile ranking, counter
+    // reset, persistent kernel) is captured once per shape and buffer set, then replayed
+    char kb[512];
+    snprintf(kb, sizeof(kb), "%s v%d L%p C%p S%p T%p", shape_key(a, a.n_cond).c_str(), cfg.variant,
+             (const void *)a.L.nu, (const void *)a.conds_dev, (void *)a.sigma, (void *)st->tiles.p);
+    std::string gkey = kb;
+    auto it = st->graphs.find(gkey);
+    if (it == st->graphs.end()) {
+        GraphEntry ge;
+        cudaStream_t cs;
+        BT_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        BatchedArgs ac = a;
+        ac.stream = cs;
+        int64_t nl = 0;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            BT_TRY(e);
+        }
+        xc_status se = enqueue(ac, pl, 0, a.n_cond, grid, 0, &nl, false);
+        e = cudaStreamEndCapture(cs, &ge.graph);
+        cudaStreamDestroy(cs);
+        if (se) return se;
+        BT_TRY(e);
+        BT_TRY(cudaGraphInstantiate(&ge.exec, ge.graph, 0));
+        it = st->graphs.emplace(gkey, ge).first;
+    }
+    if (a.timing) cudaEventRecord(a.ev_begin, a.stream);
+    BT_TRY(cudaGraphLaunch(it->second.exec, a.stream));
+    if (a.timing) cudaEventRecord(a.ev_end, a.stream);
+    *launches += a.ghx ? 6 : 5;
+    return XC_OK;
+}
+
+void batched_invalidate(BatchedState *st) {
+    for (auto &kv : st->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    st->graphs.clear();
+    st->tuned.clear();
+}
+
+void batched_release(BatchedState *st) {
+    batched_invalidate(st);
+    st->tiles.release();
+    st->cparams.release();
+    st->counter.release();
+    st->vjp_buf.release();
+    st->gsig32.release();
+    st->staging.release();
+}
+
+}  // namespace xc

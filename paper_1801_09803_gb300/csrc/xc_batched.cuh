@@ -1,0 +1,73 @@
+// xc_batched.cuh -- interface of the FP32 / batched profile kernels and the adjoint.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "xc_internal.cuh"
+
+namespace xc {
+
+struct BatchedArgs {
+    LinesDev L{};
+    size_t n_lines = 0;
+    const CondDev *conds_dev = nullptr;     // resolved conditions (Q filled) on the device
+    const xc_condition *conds_host = nullptr;
+    int n_cond = 0;
+    xc_grid grid{};
+    xc_opts opts{};
+    double *sigma = nullptr;                // device, [n_cond][grid.n]
+    cudaStream_t stream = nullptr;
+    bool timing = false;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    const double *ghx = nullptr, *ghw = nullptr;  // device Gauss-Hermite nodes/weights
+};
+
+struct VjpArgs {
+    LinesDev L{};
+    size_t n_lines = 0;
+    const CondDev *conds_dev = nullptr;
+    const xc_condition *conds_host = nullptr;
+    int n_cond = 0;
+    xc_grid grid{};
+    xc_opts opts{};
+    cudaStream_t stream = nullptr;
+    int mem = XC_MEM_DEVICE;
+    const double *grad_sigma = nullptr;
+    double *dT = nullptr, *dP = nullptr, *d_gamma_scale = nullptr, *d_n_shift = nullptr;
+    double *d_gamma_ref_line = nullptr, *d_n_line = nullptr;
+    bool timing = false;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+};
+
+// Tile shape of the FP32 gather kernel, chosen by the autotuner.
+struct TileCfg {
+    int variant = 0;   // index into the compiled kernel table
+    int points = 0;    // grid points per window
+    int cgroup = 0;    // conditions per tile
+    float ms = 0.f;    // autotune measurement
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct BatchedState {
+    DevBuf tiles;      // tile table (window, group, line range, cost order)
+    DevBuf cparams;    // per-condition constants
+    DevBuf counter;    // work-queue counter
+    DevBuf vjp_buf;    // adjoint scratch
+    DevBuf gsig32;     // grad sigma as float
+    DevBuf staging;    // host <-> device staging for the adjoint
+    std::map<std::string, TileCfg> tuned;       // autotune cache: shape key -> config
+    std::map<std::string, GraphEntry> graphs;   // graph cache: shape key + pointers -> graph
+};
+
+xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches);
+xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches);
+void batched_invalidate(BatchedState *st);
+void batched_release(BatchedState *st);
+
+}  // namespace xc

@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+  FP64 path: max relative error <= 1e-5 over bins above 1e-6 of the peak
+             (measured ~1e-12: only the rounding of exp/pow differs).
+  FP32 path: max relative error <= 2e-4 over bins above 1e-6 of the peak and
+             relative error of the band-integrated cross section <= 1e-5.
+Integer / index work (sort, permutation, eval counts) is bit-exact.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import xcsynth as xs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PROFILES = ["doppler", "lorentz", "voigt_w4", "voigt_gh_binned", "voigt_gh_sampled"]
+TOL64 = 1e-5
+TOL32 = 2e-4
+TOL32_BAND = 1e-5
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def xc():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1801_09803_gb300 as m
+    m.build.build()
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def eng(xc):
+    e = xc.Engine(0)
+    yield e
+    e.close()
+
+
+def metrics(got, ref, frac=1e-6):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    if ref.max() <= 0:
+        return float(np.max(np.abs(got))), 0.0
+    m = ref > frac * ref.max()
+    mr = float(np.max(np.abs(got[m] - ref[m]) / ref[m]))
+    band = float(abs(got.sum() - ref.sum()) / ref.sum())
+    return mr, band
+
+
+def oracle_sigma(oracle, lines, E, g, T, P, nu_A, step, n, profile, cut, wm=0.0, n_gh=20, **kw):
+    Q, dQ = oracle.partition_function(E, g, T)
+    c = oracle.make_condition(T, P, Q, dQ, **kw)
+    return oracle.cross_section(lines, c, nu_A, step, n, oracle.make_opts(profile, cut, wm, n_gh),
+                                nthreads=NTHREADS)
+
+
+# ------------------------------------------------------------------ sort
+def test_sort_is_stable_and_exact(eng, xc):
+    L = xs.gen_lines(101, 0, 100_003, 1000.0, 1100.0)
+    L["nu"][5000:5100] = L["nu"][77]          # ties: equal wavenumbers keep input order
+    L["nu"][9000] = L["nu"][9001]
+    eng.load_lines(L)
+    got = eng.get_lines()
+    perm = eng.get_permutation()
+    order = np.argsort(L["nu"], kind="stable")
+    assert np.array_equal(perm, order.astype(np.uint32))
+    for k in L:
+        assert np.array_equal(got[k], L[k][order]), k
+
+
+def test_sort_device_input_and_many_tiles(eng, xc):
+    L = xs.gen_lines(102, 0, 2_000_000, 0.0, 10000.0)
+    eng.load_lines({k: torch.as_tensor(v).cuda() for k, v in L.items()})
+    order = np.argsort(L["nu"], kind="stable")
+    assert np.array_equal(eng.get_permutation(), order.astype(np.uint32))
+    assert np.array_equal(eng.get_lines()["nu"], L["nu"][order])
+
+
+def test_assume_sorted_and_invalid_input(eng, xc):
+    L = xs.gen_lines(103, 0, 5000, 1000.0, 1010.0)
+    o = np.argsort(L["nu"], kind="stable")
+    S = {k: v[o] for k, v in L.items()}
+    eng.load_lines(S, assume_sorted=True)
+    assert np.array_equal(eng.get_permutation(), np.arange(5000, dtype=np.uint32))
+    with pytest.raises(xc.XcError) as ei:
+        eng.load_lines(L, assume_sorted=True)
+    assert ei.value.status == 1
+    for field, bad in (("nu", 0.0), ("nu", np.nan), ("A", -1.0), ("gamma_ref", -0.1), ("elower", np.inf)):
+        B = {k: v.copy() for k, v in L.items()}
+        B[field][17] = bad
+        with pytest.raises(xc.XcError) as ei:
+            eng.load_lines(B)
+        assert ei.value.status == 1, field
+
+
+# ------------------------------------------------------------------ Q(T), line parameters, counts
+def test_partition_function(xc, oracle_lib):
+    E, g = xs.gen_states(7, 5000)
+    T = np.array([300.0, 296.0, 1000.0, 3000.0, 12345.0])
+    Q, dQ = xc.partition_function(E, g, T)
+    for i, t in enumerate(T):
+        q, dq = oracle_lib.partition_function(E, g, t)
+        assert abs(Q[i] - q) <= 1e-13 * q
+        assert abs(dQ[i] - dq) <= 1e-12 * dq
+    Td = torch.as_tensor(T).cuda()
+    Qd, _ = xc.partition_function(torch.as_tensor(E).cuda(), torch.as_tensor(g).cuda(), Td)
+    assert np.allclose(Qd.cpu().numpy(), Q, rtol=1e-15, atol=0)
+
+
+def test_line_params(eng, xc, oracle_lib):
+    L = xs.gen_lines(104, 0, 20000, 0.0, 10000.0)
+    E, g = xs.gen_states(104, 3000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    S = eng.get_lines()
+    for T, P in ((300.0, 1e-3), (1500.0, 1.0), (3000.0, 10.0)):
+        I, a, gm = eng.line_params(xc.make_condition(T, P, gamma_scale=1.05, n_shift=0.1))
+        Q, dQ = oracle_lib.partition_function(E, g, T)
+        c = oracle_lib.make_condition(T, P, Q, dQ, gamma_scale=1.05, n_shift=0.1)
+        for l in range(0, 20000, 397):
+            assert I[l] == pytest.approx(oracle_lib.intensity(S["nu"][l], S["elower"][l], S["A"][l], S["g_up"][l], c),
+                                         rel=1e-13, abs=0)
+            assert a[l] == pytest.approx(oracle_lib.alpha_doppler(S["nu"][l], c), rel=1e-14)
+            assert gm[l] == pytest.approx(oracle_lib.gamma_lorentz(S["gamma_ref"][l], S["n_T"][l], c), rel=1e-13)
+
+
+@pytest.mark.parametrize("wm", [0.0, 500.0, 20.0])
+def test_count_evals_exact(eng, xc, oracle_lib, wm):
+    L = xs.gen_lines(105, 0, 30000, 0.0, 60.0)
+    E, g = xs.gen_states(105, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    grid = xc.make_grid(0.0, 0.01, 6001)
+    conds = [xc.make_condition(T, P) for T, P in ((400.0, 0.1), (1500.0, 1.0))]
+    got = eng.count_evals(conds, grid, xc.make_opts("voigt_w4", "fp64", 25.0, wm))
+    exp = 0
+    for cd in conds:
+        Q, dQ = oracle_lib.partition_function(E, g, cd.T)
+        exp += oracle_lib.count_evals(L, oracle_lib.make_condition(cd.T, cd.P, Q, dQ), 0.0, 0.01, 6001,
+                                      oracle_lib.make_opts("voigt_w4", 25.0, wm))
+    assert got == exp
+
+
+# ------------------------------------------------------------------ cross sections
+def _small_case():
+    # 8000 lines over 80 cm-1, grid of 3001 points (ragged last window), cut 3 cm-1,
+    # lines on both sides of the grid edges
+    L = xs.gen_lines(106, 0, 8000, 995.0, 1035.0)
+    E, g = xs.gen_states(106, 2000)
+    return L, E, g, 1000.0, 0.01, 3001
+
+
+@pytest.mark.parametrize("profile", PROFILES)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cross_section_profiles(eng, xc, oracle_lib, profile, precision):
+    L, E, g, nu_A, step, n = _small_case()
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    T, P = 1200.0, 0.5
+    got = eng.cross_section(xc.make_condition(T, P), xc.make_grid(nu_A, step, n),
+                            xc.make_opts(profile, precision, 3.0, n_gh=20))
+    ref = oracle_sigma(oracle_lib, L, E, g, T, P, nu_A, step, n, profile, 3.0)
+    mr, band = metrics(got, ref)
+    print(f"{profile} {precision}: max rel {mr:.3g}, band {band:.3g}")
+    if precision == "fp64":
+        assert mr < TOL64 and band < TOL64
+    else:
+        assert mr < TOL32 and band < TOL32_BAND
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_conditions(eng, xc, oracle_lib, precision):
+    # the 8 x 4 (T, P) sweep of the batched workload on a small line list, cut 25
+    L = xs.gen_lines(107, 0, 20000, 0.0, 200.0)
+    E, g = xs.gen_states(107, 5000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    W = xs.WORKLOADS["C3"]
+    conds = xs.conditions_for(W)
+    nu_A, step, n = 0.0, 0.01, 20001
+    sel = list(range(32)) if precision == "fp32" else [0, 13, 31]
+    cx = [xc.make_condition(conds[i]["T"], conds[i]["P"]) for i in sel]
+    got = eng.cross_section_batched(cx, xc.make_grid(nu_A, step, n), xc.make_opts("voigt_w4", precision, 25.0))
+    worst = (0.0, 0.0)
+    for j, i in enumerate(sel):
+        if precision == "fp32" and i % 5 != 0:
+            continue  # oracle on a subset of the conditions keeps the test short
+        ref = oracle_sigma(oracle_lib, L, E, g, conds[i]["T"], conds[i]["P"], nu_A, step, n, "voigt_w4", 25.0)
+        mr, band = metrics(got[j], ref)
+        worst = (max(worst[0], mr), max(worst[1], band))
+    print(f"batched {precision}: worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
+    tol = (TOL64, TOL64) if precision == "fp64" else (TOL32, TOL32_BAND)
+    assert worst[0] < tol[0] and worst[1] < tol[1]
+
+
+@pytest.mark.parametrize("profile", ["voigt_w4", "voigt_gh_binned"])
+def test_width_limited_cut(eng, xc, oracle_lib, profile):
+    L = xs.gen_lines(108, 0, 10000, 0.0, 100.0)
+    E, g = xs.gen_states(108, 2000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    grid = xc.make_grid(0.0, 0.01, 10001)
+    ref = oracle_sigma(oracle_lib, L, E, g, 1500.0, 1.0, 0.0, 0.01, 10001, profile, 25.0, wm=500.0)
+    for precision, tol in (("fp64", (TOL64, TOL64)), ("fp32", (TOL32, TOL32_BAND))):
+        got = eng.cross_section(xc.make_condition(1500.0, 1.0), grid, xc.make_opts(profile, precision, 25.0, 500.0))
+        mr, band = metrics(got, ref)
+        print(f"width-limited {profile} {precision}: {mr:.3g} {band:.3g}")
+        assert mr < tol[0] and band < tol[1]
+
+
+def test_c1_full_size(eng, xc, oracle_lib):
+    """The single-condition FP64 workload at full size: 1e5 lines, 200001 points."""
+    W = xs.WORKLOADS["C1"]
+    L = xs.gen_lines(W.seed, 0, W.n_lines, W.nu_lo, W.nu_hi)
+    E, g = xs.gen_states(W.seed, W.n_states)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    ref = oracle_sigma(oracle_lib, L, E, g, 1000.0, 1.0, W.grid_lo, W.step, W.n_points, "voigt_w4", 25.0)
+    for precision in ("fp64", "fp32"):
+        got = eng.cross_section(xc.make_condition(1000.0, 1.0), grid, xc.make_opts("voigt_w4", precision, 25.0))
+        mr, band = metrics(got, ref)
+        print(f"C1 {precision}: max rel {mr:.3g}, band {band:.3g}")
+        if precision == "fp64":
+            assert mr < TOL64 and band < TOL64
+        else:
+            assert mr < TOL32 and band < TOL32_BAND
+
+
+def test_edge_cases(eng, xc, oracle_lib):
+    E, g = xs.gen_states(109, 500)
+    eng.set_states(E, g)
+    opts64 = xc.make_opts("voigt_w4", "fp64", 1.0)
+    opts32 = xc.make_opts("voigt_w4", "fp32", 1.0)
+    # lines entirely outside the grid and beyond the cut: exact zeros
+    L = xs.gen_lines(109, 0, 100, 2000.0, 2001.0)
+    eng.load_lines(L)
+    for o in (opts64, opts32):
+        s = eng.cross_section(xc.make_condition(800.0, 1.0), xc.make_grid(1000.0, 0.01, 1001), o)
+        assert np.all(s == 0.0)
+    # one grid point; empty grid
+    L = xs.gen_lines(110, 0, 300, 999.5, 1000.5)
+    eng.load_lines(L)
+    ref = oracle_sigma(oracle_lib, L, E, g, 800.0, 1.0, 1000.0, 0.01, 1, "voigt_w4", 1.0)
+    for o, tol in ((opts64, TOL64), (opts32, TOL32)):
+        s = eng.cross_section(xc.make_condition(800.0, 1.0), xc.make_grid(1000.0, 0.01, 1), o)
+        assert abs(s[0] - ref[0]) <= tol * ref[0]
+        z = eng.cross_section_batched([xc.make_condition(800.0, 1.0)], xc.make_grid(1000.0, 0.01, 0), o)
+        assert z.shape == (1, 0)
+    # empty line list
+    eng.load_lines({k: v[:0] for k, v in L.items()})
+    for o in (opts64, opts32):
+        s = eng.cross_section(xc.make_condition(800.0, 1.0), xc.make_grid(1000.0, 0.01, 301), o)
+        assert np.all(s == 0.0)
+    # invalid arguments are rejected
+    eng.load_lines(L)
+    with pytest.raises(xc.XcError):
+        eng.cross_section(xc.make_condition(-5.0, 1.0), xc.make_grid(1000.0, 0.01, 10), opts64)
+    with pytest.raises(xc.XcError):
+        eng.cross_section(xc.make_condition(500.0, 1.0), xc.make_grid(1000.0, -0.01, 10), opts64)
+    with pytest.raises(xc.XcError):
+        eng.cross_section(xc.make_condition(500.0, 1.0), xc.make_grid(1000.0, 0.01, 10),
+                          xc.make_opts("voigt_gh_binned", "fp32", 1.0, n_gh=0))
+
+
+def test_deterministic_and_memory_kinds_agree(eng, xc):
+    L = xs.gen_lines(111, 0, 20000, 0.0, 100.0)
+    E, g = xs.gen_states(111, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    grid = xc.make_grid(0.0, 0.01, 10001)
+    conds = [xc.make_condition(T, 1.0) for T in (300.0, 900.0, 2700.0)]
+    o = xc.make_opts("voigt_w4", "fp32", 25.0)
+    a = eng.cross_section_batched(conds, grid, o)
+    b = eng.cross_section_batched(conds, grid, o)
+    d = torch.zeros((3, 10001), dtype=torch.float64, device="cuda:0")
+    eng.cross_section_batched(conds, grid, o, d)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, d.cpu().numpy())
