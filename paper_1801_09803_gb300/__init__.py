@@ -318,3 +318,35 @@ class Engine:
         v = C.c_int64()
         _check(lib().xc_last_launch_count(self._h, C.byref(v)))
         return v.value
+
+
+# ---------------------------------------------------------------------------- autograd
+def cross_section_autograd(engine: "Engine", T, P, gamma_scale, n_shift, grid: XcGrid, opts: XcOpts,
+                           mass_da: float = 18.0, T_ref: float = 296.0, P_ref: float = 1.0):
+    """Differentiable batched cross section: sigma[C][N] as a function of the tensors
+    T[C], P[C] and the scalars gamma_scale, n_shift (float64 tensors).  The backward
+    pass calls the library's adjoint (xc_cross_section_vjp)."""
+    import torch
+
+    class _CrossSection(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, T_, P_, s_, n_):
+            conds = [make_condition(float(t), float(p), mass_da=mass_da, T_ref=T_ref, P_ref=P_ref,
+                                    gamma_scale=float(s_), n_shift=float(n_))
+                     for t, p in zip(T_.detach().cpu().tolist(), P_.detach().cpu().tolist())]
+            ctx.conds = conds
+            out = torch.empty((len(conds), grid.n), dtype=torch.float64, device=f"cuda:{engine.device}")
+            engine.cross_section_batched(conds, grid, opts, out)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            r = engine.cross_section_vjp(ctx.conds, grid, opts, g.contiguous().to(torch.float64),
+                                         per_line=False)
+            dT = r["dT"].to(T.device)
+            dP = r["dP"].to(P.device)
+            ds = r["d_gamma_scale"].reshape(()).to(torch.as_tensor(gamma_scale).device)
+            dn = r["d_n_shift"].reshape(()).to(torch.as_tensor(n_shift).device)
+            return dT, dP, ds, dn
+
+    return _CrossSection.apply(T, P, gamma_scale, n_shift)
