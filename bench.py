@@ -321,6 +321,7 @@ def run_xc(args, dist, rank, world, local):
                    "generation_s": round(t_gen, 1)},
         "e2e": e2e, "roofline": rl, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "stage_ms": {"sort": sort_t["sort"], "gather": sort_t["gather"], "profile_mean": prof},
+        "tuning": eng.tuning(),
     }
     if fp64:
         out["fp64_plain"] = fp64

@@ -215,6 +215,11 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
 xc_status xc_set_timing(xc_handle *h, int enable);
 xc_status xc_last_timings(xc_handle *h, float *ms_out8);
 
+/* Description of the FP32 kernel configuration the autotuner chose for the most
+ * recent batched call (tile shape and the prediction of every candidate), as a
+ * NUL-terminated string truncated to `len` bytes. */
+xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len);
+
 /* Kernel launches issued by the last call (for launch accounting). */
 xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out);
 

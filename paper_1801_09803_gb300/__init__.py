@@ -30,7 +30,7 @@ EXPORTED_SYMBOLS = [
     "xc_version", "xc_last_error", "xc_create", "xc_destroy", "xc_load_lines", "xc_num_lines", "xc_get_lines",
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
-    "xc_last_launch_count",
+    "xc_get_tuning", "xc_last_launch_count",
 ]
 
 
@@ -94,6 +94,7 @@ def lib(build_if_missing: bool = False):
                                   vp, vp, vp, vp, vp, vp, i, vp], i),
         "xc_set_timing": ([vp, i], i), "xc_last_timings": ([vp, vp], i),
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
+        "xc_get_tuning": ([vp, C.c_char_p, st], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -313,6 +314,11 @@ class Engine:
         _check(lib().xc_last_timings(self._h, ms))
         names = ["sort", "gather", "Q", "params", "ranges", "profile", "vjp", "finish"]
         return {k: float(v) for k, v in zip(names, ms)}
+
+    def tuning(self) -> str:
+        buf = C.create_string_buffer(4096)
+        _check(lib().xc_get_tuning(self._h, buf, 4096))
+        return buf.value.decode()
 
     def last_launch_count(self) -> int:
         v = C.c_int64()

@@ -741,6 +741,14 @@ xc_status xc_last_timings(xc_handle *h, float *ms_out8) {
     return XC_OK;
 }
 
+xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (!buf || !len) { set_error("NULL buffer"); return XC_EINVAL; }
+    snprintf(buf, len, "%s", h->batched.last_tuning.c_str());
+    return XC_OK;
+}
+
 xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out) {
     xc_status st = check_handle(h);
     if (st) return st;

@@ -730,7 +730,10 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
         const Variant &v = kVariants[i];
         if (v.profile != a.opts.profile) continue;
         if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
-        if (v.CG > 1 && v.CG / 2 >= nc) continue;             // no more than half the group padded
+        if (a.opts.width_mult <= 0.0) {
+            if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
+            if (v.CG < std::min(nc, 8)) continue;              // enough conditions share each staged line
+        }
         cands.push_back(i);
     }
     if (cands.empty()) {
@@ -782,6 +785,12 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
             double t_line = (probe_avg > 0 && waves > 0) ? ms / (waves * probe_avg) : 0.0;
             double avg_tile = full_work / pl.n_win;
             double pred = t_line * std::max(waves * avg_tile, max_tile);
+            {
+                char lb[160];
+                snprintf(lb, sizeof(lb), "[R=%d CG=%d W=%d grid=%d probe %.3f ms pred %.1f ms] ", v->R, v->CG,
+                         pl.W, grid, ms, pred);
+                st->tune_log[key] += lb;
+            }
             if (pred < best_pred) {
                 best_pred = (float)pred;
                 best.variant = vi;
@@ -813,6 +822,11 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     if (s) return s;
     const Variant *v = &kVariants[cfg.variant];
     if ((s = configure_variant(v, dev))) return s;
+    {
+        char lb[256];
+        snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points; ", v->profile, v->R, v->CG, GT * v->R);
+        st->last_tuning = std::string(lb) + st->tune_log[shape_key(a, a.n_cond)];
+    }
     const bool per_cond = a.opts.width_mult > 0.0;
     if (per_cond) {
         // per-condition cut: one launch sequence per condition

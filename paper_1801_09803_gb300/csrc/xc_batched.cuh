@@ -63,6 +63,8 @@ struct BatchedState {
     DevBuf staging;    // host <-> device staging for the adjoint
     std::map<std::string, TileCfg> tuned;       // autotune cache: shape key -> config
     std::map<std::string, GraphEntry> graphs;   // graph cache: shape key + pointers -> graph
+    std::map<std::string, std::string> tune_log; // shape key -> candidate predictions
+    std::string last_tuning;                     // description of the last batched configuration
 };
 
 xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches);
