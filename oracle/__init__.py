@@ -86,6 +86,9 @@ def lib():
         L.xo_cross_section.argtypes = [vp] * 6 + [C.c_size_t, C.POINTER(Condition), d, d, C.c_longlong,
                                                    C.POINTER(Opts), vp, i]
         L.xo_cross_section.restype = i
+        L.xo_cross_section_points.argtypes = [vp] * 6 + [C.c_size_t, C.POINTER(Condition), d, d, vp,
+                                                          C.c_longlong, C.POINTER(Opts), vp, i]
+        L.xo_cross_section_points.restype = i
         L.xo_count_evals.argtypes = [vp, vp, vp, C.c_size_t, C.POINTER(Condition), d, d, C.c_longlong,
                                      C.POINTER(Opts)]
         L.xo_count_evals.restype = C.c_longlong
@@ -203,6 +206,19 @@ def cross_section(lines: Dict[str, np.ndarray], cond: Condition, nu_A: float, st
                                 float(step), int(n_pts), C.byref(opts), _p(out), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"xo_cross_section failed: {rc}")
+    return out
+
+
+def cross_section_points(lines_sorted: Dict[str, np.ndarray], cond: Condition, nu_A: float, step: float,
+                         k_list, opts: Opts, nthreads: int = 1) -> np.ndarray:
+    """sigma at the grid points k_list, one point at a time (lines must be sorted by nu)."""
+    arrs = _line_arrays(lines_sorted)
+    ks = np.ascontiguousarray(k_list, np.int64)
+    out = np.zeros(len(ks), np.float64)
+    rc = lib().xo_cross_section_points(*[_p(a) for a in arrs], len(arrs[0]), C.byref(cond), float(nu_A),
+                                       float(step), _p(ks), len(ks), C.byref(opts), _p(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"xo_cross_section_points failed: {rc}")
     return out
 
 

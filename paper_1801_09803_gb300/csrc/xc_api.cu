@@ -399,7 +399,8 @@ xc_status xc_load_lines(xc_handle *h, const xc_lines *L, size_t n, unsigned flag
         h->cap_lines = n;
     }
     h->n_lines = 0;
-    batched_invalidate(&h->batched);
+    // graphs and tuning stay valid: they key on shapes and buffer addresses, and read the
+    // line data when replayed
     if (n == 0) return XC_OK;
     LinesDev in{L->nu, L->elower, L->A, L->gamma_ref, L->n_T, L->g_up, L->j_lo};
     bool used[ST_COUNT] = {};
@@ -503,7 +504,6 @@ xc_status xc_set_states(xc_handle *h, const double *E, const int32_t *g, size_t 
     h->st_E = nullptr;
     h->st_g = nullptr;
     h->n_states = 0;
-    batched_invalidate(&h->batched);
     if (!n_states) return XC_OK;
     XC_TRY_MEM(cudaMalloc(&h->st_E, n_states * 8));
     XC_TRY_MEM(cudaMalloc(&h->st_g, n_states * 4));

@@ -84,11 +84,7 @@ struct GatherParams {
     double *sigma;
 };
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+__device__ __forceinline__ float rcp_approx(float x) { return recip(x); }
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -245,7 +241,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     float z = fmaf(E, c.kT_hi, E * c.kT_lo);
     float boltz = exp2_neg(z);
     float stim = -expm1f(-c.c2T * nu);
-    float I = c.pref * ((float)L.g_up[l] * L.A[l]) / (nu * nu) * boltz * stim;
+    float I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ga = c.pscale * L.gamma_ref[l] * ex2_approx((L.n_T[l] + c.nshift) * c.log2Tr);  // Eq. e:gamma_L
     float ah = al * inv_h, gh = ga * inv_h;   // widths in grid steps
@@ -256,18 +252,19 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         float C = b + g2;
         float P = I * kKappa * gh * inv_h;
         *A = make_float4(2.f * (g2 - b), C * C, P, P * C);
-        float a = kSqrtLn2f / ah;  // x = a |delta|
+        float rah = rcp_approx(ah);
+        float a = kSqrtLn2f * rah;  // x = a |delta|
         float y = a * gh;
-        float Pv = I * kSqrtLn2OverPi / al;
-        float thr = (15.f - y) / a;
+        float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
+        float thr = (15.f - y) * ah * (1.f / kSqrtLn2f);
         float t2 = y < 15.f ? thr * thr : -1.f;
         *B = make_float4(a, y, Pv, t2);
         *thr2 = t2;
     } else if (PROF == XC_LORENTZ) {
         *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
     } else if (PROF == XC_DOPPLER) {
-        float qd = 1.f / (ah * ah);
-        *A = make_float4(qd, I * kSqrtLn2OverPi / al, 0.f, 0.f);
+        float qd = rcp_approx(ah * ah);
+        *A = make_float4(qd, I * kSqrtLn2OverPi * rcp_approx(al), 0.f, 0.f);
     } else if (PROF == XC_VOIGT_GH_SAMPLED) {
         *A = make_float4(ah / kSqrtLn2f, fmaxf(gh * gh, 1e-30f), I * kPiM32 * gh * inv_h, 0.f);
     } else {
@@ -276,7 +273,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
 }
 
 // full FP32 w4 Voigt value (all regions) times Pv, at grid offset delta
-__device__ __noinline__ float w4_value_f32(float delta, const float4 &B) {
+__device__ __forceinline__ float w4_value_f32(float delta, const float4 &B) {
     float x = B.x * fabsf(delta);
     Cx<float> w = w4_eval<float>(x, B.y, nullptr);
     return B.z * w.re;
@@ -401,12 +398,17 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         bool first_fold = true;
         int chunk = 0;
 
-        for (unsigned l0 = lo; l0 < hi; l0 += SCH) {
-            const int cnt = (int)(hi - l0 < (unsigned)SCH ? hi - l0 : (unsigned)SCH);
+        // Chunk ci holds lines lo + ci + j * nch (j < SCH): every chunk samples the whole
+        // wavenumber range of the window, so the centre-zone (w4 region II-IV) work of a
+        // chunk falls on all warps instead of on the one warp that owns those centres.
+        const unsigned nl = hi - lo;
+        const unsigned nch = (nl + SCH - 1) / SCH;
+        for (unsigned ci = 0; ci < nch; ++ci) {
+            const int cnt = (int)((nl - ci + nch - 1) / nch);
             __syncthreads();
             // ---- stage: per-line geometry and per-(line, condition) constants
             if (tid < cnt) {
-                size_t l = (size_t)l0 + tid;
+                size_t l = (size_t)lo + ci + (size_t)tid * nch;
                 int na = p.n_abs[l];
                 int ka = p.ka_abs[l], kb = p.kb_abs[l];
                 int64_t kaw = (int64_t)ka - kw, kbw = (int64_t)kb - kw;
@@ -426,7 +428,8 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 if (v) {
                     float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
                     if (cc < p.n_cond) {
-                        line_consts<PROF>(p.L, (size_t)l0 + i, p.cp[cc], p.h, p.inv_h, &A, &B, &t2);
+                        line_consts<PROF>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
+                                          &t2);
                     } else {  // padding condition: contributes exactly 0
                         if (PROF == XC_VOIGT_W4) A = make_float4(1.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);

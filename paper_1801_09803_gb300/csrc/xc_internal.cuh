@@ -104,9 +104,17 @@ template <typename R>
 __device__ inline Cx<R> operator*(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
 template <typename R>
 __device__ inline Cx<R> operator+(R s, Cx<R> a) { return {s + a.re, a.im}; }
+// reciprocal: IEEE in FP64; the hardware approximation (about 1 ulp) in FP32
+__device__ inline double recip(double x) { return 1.0 / x; }
+__device__ inline float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename R>
 __device__ inline Cx<R> cdiv(Cx<R> a, Cx<R> b) {
-    R d = R(1) / (b.re * b.re + b.im * b.im);
+    R d = recip(b.re * b.re + b.im * b.im);
     return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
 }
 

@@ -1,0 +1,107 @@
+"""Full-size workloads in the benchmark's launch configuration, checked against
+the FP64 oracle on sampled grid points (the oracle evaluates them one by one
+over the whole list, sorted here with numpy), plus properties that hold at any
+size (exact eval counts, non-negativity, determinism).
+
+FP32 tolerance: 2e-4 relative at sampled points above 1e-6 of the largest
+sampled value; FP64: 1e-5.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import xcsynth as xs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def xc():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1801_09803_gb300 as m
+    m.build.build()
+    m.lib()
+    return m
+
+
+def _sample_points(n, seed, m=24):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, m)])).astype(np.int64)
+
+
+def _check(oracle, S, E, g, W, cond_py, sigma_row, ks, profile, tol, wm=0.0):
+    Q, dQ = oracle.partition_function(E, g, cond_py["T"])
+    oc = oracle.make_condition(cond_py["T"], cond_py["P"], Q, dQ, mass_da=W.mass_da)
+    ref = oracle.cross_section_points(S, oc, W.grid_lo, W.step, ks, oracle.make_opts(profile, W.cutoff, wm, W.n_gh),
+                                      nthreads=NTHREADS)
+    got = sigma_row[ks]
+    m = ref > 1e-6 * ref.max()
+    err = float(np.max(np.abs(got[m] - ref[m]) / ref[m])) if m.any() else 0.0
+    assert np.all(got >= 0)
+    return err
+
+
+def test_c3_batched_full_size(xc, oracle_lib):
+    """1e8 lines x 32 conditions, FP32 batched persistent kernel (the benchmark's step)."""
+    W = xs.WORKLOADS["C3"]
+    L = xs.gen_lines(W.seed, 0, W.n_lines, W.nu_lo, W.nu_hi)
+    E, g = xs.gen_states(W.seed, W.n_states)
+    conds_py = xs.conditions_for(W)
+    eng = xc.Engine(0)
+    eng.load_lines({k: torch.from_numpy(v).cuda() for k, v in L.items()})
+    eng.set_states(E, g)
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    opts = xc.make_opts("voigt_w4", "fp32", W.cutoff)
+    conds = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da) for c in conds_py]
+    sig = torch.empty((len(conds), W.n_points), dtype=torch.float64, device="cuda:0")
+    eng.cross_section_batched(conds, grid, opts, sig)
+    s1 = sig.cpu().numpy()
+    eng.cross_section_batched(conds, grid, opts, sig)           # graph replay: bitwise identical
+    assert np.array_equal(s1, sig.cpu().numpy())
+    # exact algorithmic count on the device vs the closed count for interior lines
+    evals = eng.count_evals(conds, grid, opts)
+    assert 0.98 * 32 * W.n_lines * 5001 < evals <= 32 * W.n_lines * 5001
+    eng.close()
+    o = np.argsort(L["nu"], kind="stable")
+    S = {k: v[o] for k, v in L.items()}
+    del L
+    ks = _sample_points(W.n_points, 3)
+    worst = 0.0
+    for c in range(0, 32, 3):
+        worst = max(worst, _check(oracle_lib, S, E, g, W, conds_py[c], s1[c], ks, "voigt_w4", 2e-4))
+    print(f"C3 full size, FP32 batched: worst sampled relative error {worst:.3g}")
+    assert worst < 2e-4
+
+
+@pytest.mark.parametrize("profile", ["voigt_w4", "voigt_gh_binned"])
+def test_c2_full_size(xc, oracle_lib, profile):
+    """1e7 lines, one condition, width-limited cut; FP64 plain and FP32 kernels."""
+    W = xs.WORKLOADS["C2"]
+    L = xs.gen_lines(W.seed, 0, W.n_lines, W.nu_lo, W.nu_hi)
+    E, g = xs.gen_states(W.seed, W.n_states)
+    c = xs.conditions_for(W)[0]
+    eng = xc.Engine(0)
+    eng.load_lines({k: torch.from_numpy(v).cuda() for k, v in L.items()})
+    eng.set_states(E, g)
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    cond = xc.make_condition(c["T"], c["P"], mass_da=W.mass_da)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        d = torch.empty((1, W.n_points), dtype=torch.float64, device="cuda:0")
+        eng.cross_section_batched([cond], grid, xc.make_opts(profile, prec, W.cutoff, W.cutoff_width_mult, 20), d)
+        out[prec] = d[0].cpu().numpy()
+    eng.close()
+    o = np.argsort(L["nu"], kind="stable")
+    S = {k: v[o] for k, v in L.items()}
+    ks = _sample_points(W.n_points, 4)
+    e64 = _check(oracle_lib, S, E, g, W, c, out["fp64"], ks, profile, 1e-5, W.cutoff_width_mult)
+    e32 = _check(oracle_lib, S, E, g, W, c, out["fp32"], ks, profile, 2e-4, W.cutoff_width_mult)
+    m = out["fp64"] > 1e-6 * out["fp64"].max()
+    band = abs(out["fp32"].sum() - out["fp64"].sum()) / out["fp64"].sum()
+    print(f"C2 {profile}: FP64 {e64:.3g}, FP32 {e32:.3g} (sampled); FP32 vs FP64 band {band:.3g}, "
+          f"max rel over all bins {np.max(np.abs(out['fp32'][m] - out['fp64'][m]) / out['fp64'][m]):.3g}")
+    assert e64 < 1e-5 and e32 < 2e-4 and band < 1e-5

@@ -386,3 +386,20 @@ def test_vjp_matches_central_differences(oracle_lib, profile):
     fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
     assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4)
     assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12)
+
+
+def test_point_evaluation_matches_full_grid(oracle_lib):
+    L = xs.gen_lines(23, 0, 3000, 1000.0, 1100.0)
+    o = np.argsort(L["nu"], kind="stable")
+    S = {k: v[o] for k, v in L.items()}
+    E, g = xs.gen_states(23, 500)
+    Q, dQ = oracle_lib.partition_function(E, g, 900.0)
+    c = oracle_lib.make_condition(900.0, 1.0, Q, dQ)
+    for prof, wm in (("voigt_w4", 0.0), ("voigt_gh_binned", 300.0), ("doppler", 0.0)):
+        op = oracle_lib.make_opts(prof, 25.0, wm)
+        full = oracle_lib.cross_section(S, c, 1000.0, 0.01, 10001, op, nthreads=1)
+        ks = np.array([0, 17, 5000, 9999, 10000])
+        pts = oracle_lib.cross_section_points(S, c, 1000.0, 0.01, ks, op, nthreads=2)
+        assert np.allclose(pts, full[ks], rtol=1e-14, atol=0)
+    with pytest.raises(RuntimeError):  # unsorted input is refused
+        oracle_lib.cross_section_points(L, c, 1000.0, 0.01, ks, oracle_lib.make_opts(), nthreads=1)
