@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 form on a subset")
+    ap.add_argument("--profile", default=None, help="override the workload's line profile")
     return ap.parse_args()
 
 
@@ -202,6 +203,8 @@ def run_xc(args, dist, rank, world, local):
     conds_py = xs.conditions_for(W)
     conds = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da) for c in conds_py]
     grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    if args.profile:
+        W.profile = args.profile
     opts = xc.make_opts(W.profile, "fp32", W.cutoff, W.cutoff_width_mult, W.n_gh)
     nc = len(conds)
 

@@ -132,58 +132,67 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                 const float yv = a_sc * gaf;
                 const float thr = yv < 15.f ? (15.f - yv) / a_sc : -1.f;  // region I iff |D| >= thr
                 const float thr2 = thr > 0.f ? thr * thr : -1.f;
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // region I: sum g N/D, g (D - 2Nt)/D^2, g (..)/D^2
-                float c0 = 0.f, c1 = 0.f, c2 = 0.f;  // other regions / other profiles
+                // FP32 terms summed 8 at a time, folded into FP64; centre points (w4 regions
+                // II-IV), which carry the largest terms of sums that cancel (the derivatives of
+                // a unit-area profile integrate to zero), are evaluated in FP64.
+                double S0 = 0.0, S1 = 0.0, S2 = 0.0, C0 = 0.0, C1 = 0.0, C2 = 0.0;
                 const float *gc = g32 + (size_t)c * n_pts;
-                for (int64_t k = ka + lane; k <= kb; k += 32) {
-                    float D = ((float)(k - nabs) - ff) * h;
-                    float u = D * D;
-                    float g = gc[k];
-                    if (PROF == XC_VOIGT_W4) {
-                        if (u >= thr2) {
-                            float t = bg - u;
-                            float Dn = fmaf(t, t, 4.f * g2 * u);
-                            float N = u + bg;
-                            float rD = 1.f / Dn;
-                            float rD2 = rD * rD;
-                            s0 = fmaf(g, N * rD, s0);
-                            s1 = fmaf(g, fmaf(-2.f * N, t, Dn) * rD2, s1);
-                            float q = fmaf(Dn, N + 2.f * g2, -4.f * g2 * N * N);
-                            s2 = fmaf(g, q * rD2, s2);
+                for (int64_t kb8 = ka + lane; kb8 <= kb; kb8 += 32 * 8) {
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll 4
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t k = kb8 + 32 * j;
+                        if (k > kb) break;
+                        float D = ((float)(k - nabs) - ff) * h;
+                        float u = D * D;
+                        float g = gc[k];
+                        if (PROF == XC_VOIGT_W4) {
+                            if (u >= thr2) {
+                                float t = bg - u;
+                                float Dn = fmaf(t, t, 4.f * g2 * u);
+                                float N = u + bg;
+                                float rD = 1.f / Dn;
+                                float rD2 = rD * rD;
+                                s0 = fmaf(g, N * rD, s0);
+                                s1 = fmaf(g, fmaf(-2.f * N, t, Dn) * rD2, s1);
+                                float q = fmaf(Dn, N + 2.f * g2, -4.f * g2 * N * N);
+                                s2 = fmaf(g, q * rD2, s2);
+                            } else {
+                                double D64 = __dsub_rn(grid_x(nu_A, step, k), nu);
+                                double V, dVa, dVg;
+                                prof_deriv64<XC_VOIGT_W4>(D64, al, ga, &V, &dVa, &dVg);
+                                double gd = (double)g;
+                                C0 += gd * V;
+                                C1 += gd * dVa;
+                                C2 += gd * dVg;
+                            }
+                        } else if (PROF == XC_DOPPLER) {
+                            float e = expf(-(float)kLn2 * u / (alf * alf));
+                            c0 = fmaf(g, e, c0);
+                            c1 = fmaf(g, e * u, c1);
                         } else {
-                            Cx<float> dF;
-                            Cx<float> w = w4_eval<float>(a_sc * D, yv, &dF);
-                            float v = (float)0.46971863934982566 / alf * w.re;
-                            float k2 = (float)(0.6931471805599453 / 1.772453850905516027) / (alf * alf);
-                            float dVD = k2 * dF.im, dg = k2 * dF.re;
-                            c0 = fmaf(g, v, c0);
-                            c1 = fmaf(g, -(v + D * dVD + gaf * dg) / alf, c1);
-                            c2 = fmaf(g, dg, c2);
+                            float r = 1.f / (u + g2);
+                            c0 = fmaf(g, r, c0);
+                            c2 = fmaf(g, (u - g2) * r * r, c2);
                         }
-                    } else if (PROF == XC_DOPPLER) {
-                        float e = expf(-(float)kLn2 * u / (alf * alf));
-                        c0 = fmaf(g, e, c0);
-                        c1 = fmaf(g, e * u, c1);
-                    } else {
-                        float r = 1.f / (u + g2);
-                        c0 = fmaf(g, r, c0);
-                        c2 = fmaf(g, (u - g2) * r * r, c2);
                     }
+                    S0 += s0; S1 += s1; S2 += s2;
+                    C0 += c0; C1 += c1; C2 += c2;
                 }
                 if (PROF == XC_VOIGT_W4) {
                     double kg = kKappa64 * ga;
-                    SI = kg * (double)s0 + (double)c0;
-                    Sa = kg * (double)s1 * (al / kLn2) + (double)c1;  // dV/dalpha = dV/db * alpha/ln2
-                    Sg = kKappa64 * (double)s2 + (double)c2;
+                    SI = kg * S0 + C0;
+                    Sa = kg * S1 * (al / kLn2) + C1;  // dV/dalpha = dV/db * alpha/ln2
+                    Sg = kKappa64 * S2 + C2;
                 } else if (PROF == XC_DOPPLER) {
                     double pd = 0.46971863934982566 / al;
-                    SI = pd * (double)c0;
-                    Sa = pd * (-(double)c0 / al + 2.0 * kLn2 / (al * al * al) * (double)c1);
+                    SI = pd * C0;
+                    Sa = pd * (-C0 / al + 2.0 * kLn2 / (al * al * al) * C1);
                     Sg = 0.0;
                 } else {
-                    SI = ga / kPi * (double)c0;
+                    SI = ga / kPi * C0;
                     Sa = 0.0;
-                    Sg = (double)c2 / kPi;
+                    Sg = C2 / kPi;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
