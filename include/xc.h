@@ -215,6 +215,35 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
 xc_status xc_set_timing(xc_handle *h, int enable);
 xc_status xc_last_timings(xc_handle *h, float *ms_out8);
 
+/* Allocation-free FP32 batched cross section.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory while
+ * they run -- code inside another framework's memory pool or a fixed memory
+ * budget, real-time loops where cudaMalloc/cudaFree (which can synchronise the
+ * device) are not allowed, or hosts that can only hand over buffers they own.
+ * It needs no handle and allocates nothing: its scratch (per-line grid
+ * geometry, per-condition constants, window ranges, tile order, work counter)
+ * is one fixed array of about 18 MB (17.9e6 bytes) in device memory that every GPU loading
+ * the library holds until the process exits.
+ *   lines      device arrays (lines->mem == XC_MEM_DEVICE), already sorted by
+ *              ascending nu (checked: EINVAL if not), n_lines <= 1,048,576.
+ *   E, g       device state list for conditions with Q <= 0 (else may be NULL).
+ *   conds      host array, n_cond <= 64.   grid->n <= 4,194,304 points.
+ *   opts       precision XC_FP32, width_mult 0, profile Doppler, Lorentz or
+ *              Voigt-w4 (EUNSUPPORTED otherwise).
+ *   sigma_out  device float64[n_cond][grid->n].
+ * Sizes beyond these limits return XC_EINVAL with a message naming the limit.
+ * The first call on each device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Every call on a device shares the same scratch array, which keeps the last
+ * call's contents (the parts that must start at zero are cleared by each call):
+ * calls whose work overlaps on the GPU (different streams or threads) race and
+ * must be serialised by the caller.  The call synchronises `stream` while it
+ * uploads the conditions. */
+xc_status xc_cross_section_batched_static(const xc_lines *lines, size_t n_lines, const double *E,
+                                          const int32_t *g, size_t n_states, const xc_condition *conds,
+                                          size_t n_cond, const xc_grid *grid, const xc_opts *opts,
+                                          double *sigma_out, void *stream);
+
 /* Description of the FP32 kernel configuration the autotuner chose for the most
  * recent batched call (tile shape and the prediction of every candidate), as a
  * NUL-terminated string truncated to `len` bytes. */

@@ -30,7 +30,7 @@ EXPORTED_SYMBOLS = [
     "xc_version", "xc_last_error", "xc_create", "xc_destroy", "xc_load_lines", "xc_num_lines", "xc_get_lines",
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
-    "xc_get_tuning", "xc_last_launch_count",
+    "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static",
 ]
 
 
@@ -95,6 +95,8 @@ def lib(build_if_missing: bool = False):
         "xc_set_timing": ([vp, i], i), "xc_last_timings": ([vp, vp], i),
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
         "xc_get_tuning": ([vp, C.c_char_p, st], i),
+        "xc_cross_section_batched_static": ([C.POINTER(XcLines), st, vp, vp, st, C.POINTER(XcCondition), st,
+                                             C.POINTER(XcGrid), C.POINTER(XcOpts), vp, vp], i),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)

@@ -32,6 +32,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -898,4 +899,233 @@ void batched_release(BatchedState *st) {
     st->staging.release();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant (xc_cross_section_batched_static).
+//
+// Some callers cannot allocate device memory while they run: code that executes
+// inside another framework's memory pool or a pre-planned memory budget, real-time
+// loops that must not call cudaMalloc/cudaFree (both can synchronise the device),
+// or hosts that hand this library nothing but the buffers they already own.  For
+// them, the per-call scratch of the FP32 batched kernel (per-line grid geometry,
+// per-condition constants, window ranges, tile order, work counter) lives in the
+// fixed-size array below, which every GPU that loads the library holds until the
+// process exits.  Host code must not take the array's address directly (the name
+// is only a host-side stand-in); it asks the runtime for the device address once
+// per device and passes that pointer to the kernels.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticMaxLines = (size_t)1 << 20;      // 1,048,576 lines
+constexpr int kStaticMaxCond = 64;
+constexpr int64_t kStaticMaxPoints = (int64_t)1 << 22;   // 4,194,304 grid points
+constexpr int kStaticR = 4;                               // tile shape used by this entry point
+constexpr int kStaticMinW = GT * kStaticR;
+constexpr int kStaticMaxWin = (int)((kStaticMaxPoints + kStaticMinW - 1) / kStaticMinW);
+constexpr int kStaticMaxTiles = kStaticMaxWin * kStaticMaxCond;
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct StaticLayout {
+    static constexpr size_t o_n = 0;
+    static constexpr size_t o_f = o_n + al256(kStaticMaxLines * 4);
+    static constexpr size_t o_ka = o_f + al256(kStaticMaxLines * 4);
+    static constexpr size_t o_kb = o_ka + al256(kStaticMaxLines * 4);
+    static constexpr size_t o_cp = o_kb + al256(kStaticMaxLines * 4);
+    static constexpr size_t o_cd = o_cp + al256(kStaticMaxCond * sizeof(CParam));
+    static constexpr size_t o_q = o_cd + al256(kStaticMaxCond * sizeof(CondDev));
+    static constexpr size_t o_lo = o_q + al256(kStaticMaxCond * 3 * sizeof(double) + kStaticMaxCond * sizeof(int));
+    static constexpr size_t o_hi = o_lo + al256((size_t)kStaticMaxWin * 4);
+    static constexpr size_t o_ord = o_hi + al256((size_t)kStaticMaxWin * 4);
+    static constexpr size_t o_ctr = o_ord + al256((size_t)kStaticMaxTiles * 4);
+    static constexpr size_t o_gs = o_ctr + 256;
+    static constexpr size_t o_nodes = o_gs + 256;
+    static constexpr size_t o_flag = o_nodes + 512;
+    static constexpr size_t total = o_flag + 256;
+};
+
+static __device__ __align__(256) unsigned char g_static_scratch[StaticLayout::total];
+
+// per device: the device address of g_static_scratch, looked up once
+static std::mutex g_static_mu;
+static void *g_static_ptr[256] = {};
+
+__global__ void k_static_fill_conds(CondDev *c, int n, const int *tix, const double *Q, const double *dQ) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || tix[i] < 0) return;
+    c[i].Q = Q[tix[i]];
+    c[i].dQdT = dQ[tix[i]];
+}
+
+__global__ void k_static_check_lines(LinesDev L, size_t n, int *flag) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double v = L.nu[i];
+        bool ok = isfinite(v) && v > 0.0 && isfinite(L.elower[i]) && L.elower[i] >= 0.f && L.A[i] >= 0.f &&
+                  L.gamma_ref[i] >= 0.f && isfinite(L.n_T[i]) && L.g_up[i] >= 0;
+        if (!ok) atomicOr(flag, 1);
+        if (i + 1 < n && !(v <= L.nu[i + 1])) atomicOr(flag, 2);
+    }
+}
+
 }  // namespace xc
+
+extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size_t n_lines, const double *E,
+                                                     const int32_t *g, size_t n_states, const xc_condition *conds,
+                                                     size_t n_cond, const xc_grid *grid, const xc_opts *opts,
+                                                     double *sigma_out, void *stream) {
+    using namespace xc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!lines || !conds || !grid || !opts || (!sigma_out && n_cond && grid->n)) {
+        set_error("NULL argument");
+        return XC_EINVAL;
+    }
+    if (lines->mem != XC_MEM_DEVICE) { set_error("lines must be device arrays (sorted by nu)"); return XC_EINVAL; }
+    if (n_lines > kStaticMaxLines) {
+        set_error("n_lines = %zu exceeds the static scratch limit of %zu lines", n_lines, kStaticMaxLines);
+        return XC_EINVAL;
+    }
+    if (n_cond > (size_t)kStaticMaxCond) {
+        set_error("n_cond = %zu exceeds the static scratch limit of %d conditions", n_cond, kStaticMaxCond);
+        return XC_EINVAL;
+    }
+    if (grid->n < 0 || grid->n > kStaticMaxPoints) {
+        set_error("grid n = %lld exceeds the static scratch limit of %lld points", (long long)grid->n,
+                  (long long)kStaticMaxPoints);
+        return XC_EINVAL;
+    }
+    if (!(grid->step > 0.0) || !isfinite(grid->step) || !isfinite(grid->nu_A)) { set_error("bad grid"); return XC_EINVAL; }
+    if (opts->precision != XC_FP32 || opts->width_mult != 0.0) {
+        set_error("the allocation-free entry point computes the FP32 kernel with a fixed cut");
+        return XC_EUNSUPPORTED;
+    }
+    if (opts->profile < XC_DOPPLER || opts->profile > XC_VOIGT_GH_SAMPLED || !(opts->cutoff > 0.0)) {
+        set_error("bad opts");
+        return XC_EINVAL;
+    }
+    if (opts->profile == XC_VOIGT_GH_BINNED || opts->profile == XC_VOIGT_GH_SAMPLED) {
+        set_error("Gauss-Hermite profiles need node tables: use xc_cross_section_batched");
+        return XC_EUNSUPPORTED;
+    }
+    for (size_t i = 0; i < n_cond; ++i) {
+        const xc_condition &c = conds[i];
+        if (!(c.T > 0.0) || !(c.P >= 0.0) || !(c.mass_da > 0.0) || !(c.T_ref > 0.0) || !(c.P_ref > 0.0)) {
+            set_error("condition %zu: bad T/P/mass/reference values", i);
+            return XC_EINVAL;
+        }
+        if (c.Q <= 0.0 && (!E || !g || !n_states)) {
+            set_error("condition %zu: Q <= 0 needs a device state list (E, g)", i);
+            return XC_EINVAL;
+        }
+    }
+    if (n_cond == 0 || grid->n == 0) return XC_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) { set_error("cudaGetDevice failed"); return XC_ECUDA; }
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p) {
+                set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+                cudaGetLastError();
+                return XC_ECUDA;
+            }
+            g_static_ptr[dev] = p;
+        }
+        base = static_cast<char *>(g_static_ptr[dev]);
+    }
+    const int nc = (int)n_cond;
+    const Variant *v = nullptr;
+    int want_cg = nc >= 16 ? 16 : (nc >= 8 ? 8 : (nc >= 4 ? 4 : 1));
+    for (int i = 0; i < kNumVariants && !v; ++i)
+        if (kVariants[i].profile == opts->profile && kVariants[i].CG == want_cg) v = &kVariants[i];
+    for (int i = 0; i < kNumVariants && !v; ++i)  // profiles compiled with fewer group sizes
+        if (kVariants[i].profile == opts->profile && kVariants[i].CG <= want_cg) v = &kVariants[i];
+    if (!v) { set_error("no kernel variant for this profile"); return XC_EUNSUPPORTED; }
+    xc_status st = configure_variant(v, dev);
+    if (st) return st;
+    // carve the static scratch
+    Plan pl;
+    pl.v = v;
+    pl.W = GT * v->R;
+    pl.n_win = (int)((grid->n + pl.W - 1) / pl.W);
+    pl.n_groups = (nc + v->CG - 1) / v->CG;
+    pl.n_tiles = pl.n_win * pl.n_groups;
+    if (pl.n_win > kStaticMaxWin || pl.n_tiles > kStaticMaxTiles) { set_error("tile table too large"); return XC_EINVAL; }
+    pl.n_abs = (int *)(base + StaticLayout::o_n);
+    pl.f = (float *)(base + StaticLayout::o_f);
+    pl.ka = (int *)(base + StaticLayout::o_ka);
+    pl.kb = (int *)(base + StaticLayout::o_kb);
+    pl.cp = (CParam *)(base + StaticLayout::o_cp);
+    pl.lo = (unsigned *)(base + StaticLayout::o_lo);
+    pl.hi = (unsigned *)(base + StaticLayout::o_hi);
+    pl.order = (int *)(base + StaticLayout::o_ord);
+    pl.counter = (int *)(base + StaticLayout::o_ctr);
+    pl.gs = (GeomStats *)(base + StaticLayout::o_gs);
+    pl.gx = (float *)(base + StaticLayout::o_nodes);
+    pl.gw = pl.gx + 64;
+    CondDev *dc = (CondDev *)(base + StaticLayout::o_cd);
+    double *qT = (double *)(base + StaticLayout::o_q), *qQ = qT + kStaticMaxCond, *qD = qQ + kStaticMaxCond;
+    int *tix_d = (int *)(qD + kStaticMaxCond);
+    int *flag = (int *)(base + StaticLayout::o_flag);
+    LinesDev L{lines->nu, lines->elower, lines->A, lines->gamma_ref, lines->n_T, lines->g_up, lines->j_lo};
+    // conditions: host -> static scratch, Q(T) for those that need it
+    CondDev hc[kStaticMaxCond];
+    double uT[kStaticMaxCond];
+    int tix[kStaticMaxCond];
+    int nT = 0;
+    for (int i = 0; i < nc; ++i) {
+        const xc_condition &c = conds[i];
+        hc[i] = CondDev{c.T, c.P, c.Q, c.dQdT, c.mass_da, c.T_ref, c.P_ref, c.gamma_scale, c.n_shift, c.abundance};
+        tix[i] = -1;
+        if (c.Q <= 0.0) {
+            int j = 0;
+            while (j < nT && uT[j] != c.T) ++j;
+            if (j == nT) uT[nT++] = c.T;
+            tix[i] = j;
+        }
+    }
+#define ST_TRY(call)                                                                             \
+    do {                                                                                         \
+        cudaError_t _e = (call);                                                                 \
+        if (_e != cudaSuccess) {                                                                 \
+            set_error("%s failed: %s", #call, cudaGetErrorString(_e));                            \
+            return XC_ECUDA;                                                                     \
+        }                                                                                        \
+    } while (0)
+    ST_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    if (n_lines) {
+        k_static_check_lines<<<(unsigned)std::max<size_t>(1, std::min<size_t>((n_lines + 255) / 256, 152 * 8)), 256, 0, s>>>(
+            L, n_lines, flag);
+    }
+    int hflag = 0;
+    ST_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ST_TRY(cudaMemcpyAsync(dc, hc, nc * sizeof(CondDev), cudaMemcpyHostToDevice, s));
+    ST_TRY(cudaStreamSynchronize(s));  // host arrays above are on this stack frame
+    if (hflag & 1) { set_error("invalid line values"); return XC_EINVAL; }
+    if (hflag & 2) { set_error("lines must be sorted by nu"); return XC_EINVAL; }
+    if (nT) {
+        ST_TRY(cudaMemcpyAsync(qT, uT, nT * sizeof(double), cudaMemcpyHostToDevice, s));
+        ST_TRY(cudaMemcpyAsync(tix_d, tix, nc * sizeof(int), cudaMemcpyHostToDevice, s));
+        ST_TRY(launch_partition_function(E, g, n_states, qT, nT, qQ, qD, s));
+        k_static_fill_conds<<<1, 64, 0, s>>>(dc, nc, tix_d, qQ, qD);
+        ST_TRY(cudaStreamSynchronize(s));  // uT and tix live on this stack frame
+    }
+    if (n_lines == 0) {
+        ST_TRY(cudaMemsetAsync(sigma_out, 0, (size_t)nc * grid->n * sizeof(double), s));
+        return XC_OK;
+    }
+    BatchedArgs a;
+    a.L = L;
+    a.n_lines = n_lines;
+    a.conds_dev = dc;
+    a.conds_host = conds;
+    a.n_cond = nc;
+    a.grid = *grid;
+    a.opts = *opts;
+    a.sigma = sigma_out;
+    a.stream = s;
+    int64_t nl = 0;
+    st = enqueue(a, pl, 0, nc, grid_size(v, dev, pl.n_tiles), 0, &nl, false);
+#undef ST_TRY
+    return st;
+}
