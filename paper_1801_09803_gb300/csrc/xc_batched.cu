@@ -245,7 +245,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     float I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ga = c.pscale * L.gamma_ref[l] * ex2_approx((L.n_T[l] + c.nshift) * c.log2Tr);  // Eq. e:gamma_L
-    float ah = al * inv_h, gh = ga * inv_h;   // widths in grid steps
+    float ah = __fmul_rn(al, inv_h), gh = __fmul_rn(ga, inv_h);   // widths in grid steps
     *thr2 = -1.f;
     if (PROF == XC_VOIGT_W4) {
         float b = ah * ah * (float)(0.5 / 0.6931471805599453);
@@ -253,12 +253,15 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         float C = b + g2;
         float P = I * kKappa * gh * inv_h;
         *A = make_float4(2.f * (g2 - b), C * C, P, P * C);
+        // a, y and the region-I threshold decide which kernel evaluates a point (the
+        // main kernel: |x| + y >= 15; the centre-zone kernel: the rest); both kernels get
+        // them from this code, with explicitly rounded operations so they agree bit for bit
         float rah = rcp_approx(ah);
-        float a = kSqrtLn2f * rah;  // x = a |delta|
-        float y = a * gh;
+        float a = __fmul_rn(kSqrtLn2f, rah);  // x = a |delta|
+        float y = __fmul_rn(a, gh);
         float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
-        float thr = (15.f - y) * ah * (1.f / kSqrtLn2f);
-        float t2 = y < 15.f ? thr * thr : -1.f;
+        float thr = __fmul_rn(__fmul_rn(__fsub_rn(15.f, y), ah), 1.f / kSqrtLn2f);
+        float t2 = y < 15.f ? __fmul_rn(thr, thr) : -1.f;
         *B = make_float4(a, y, Pv, t2);
         *thr2 = t2;
     } else if (PROF == XC_LORENTZ) {
@@ -273,8 +276,28 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     }
 }
 
+// Re w in w4's region II (5.5 <= |x| + y < 15) in real arithmetic.  The region-II
+// rational t(a + b t^2)/(t^4 + 3 t^2 + 3/4) has denominator (t^2 + Q1)(t^2 + Q2) with
+// Q1,2 = (3 -+ sqrt 6)/2, so it splits into two partial fractions A_m t/(t^2 + Q_m),
+// A_m = (a - b Q_m)/(Q_other - Q_m); each is a pair of Lorentzians in x at +-sqrt(Q_m):
+//   Re w = y sum_m A_m (X + Y + Q_m) / ((X + Y - Q_m)^2 + 4 Q_m Y),  X = x^2, Y = y^2.
+// (The nodes +-sqrt(Q_m) are those of 4-point Gauss-Hermite quadrature.)
+__device__ __forceinline__ float w4_region2_re(float x, float y) {
+    constexpr double a = 1.410474, b = 0.5641896, s6 = 2.449489742783178098;
+    constexpr float Q1 = (float)((3.0 - s6) / 2.0), Q2 = (float)((3.0 + s6) / 2.0);
+    constexpr float A1 = (float)((a - b * ((3.0 - s6) / 2.0)) / s6);
+    constexpr float A2 = (float)(-(a - b * ((3.0 + s6) / 2.0)) / s6);
+    float X = x * x, Y = y * y;
+    float t1 = X + Y - Q1, t2 = X + Y - Q2;
+    float D1 = fmaf(t1, t1, 4.f * Q1 * Y), D2 = fmaf(t2, t2, 4.f * Q2 * Y);
+    float N1 = A1 * (X + Y + Q1), N2 = A2 * (X + Y + Q2);
+    return y * fmaf(N1, D2, N2 * D1) * rcp_approx(D1 * D2);
+}
+
 // full FP32 w4 Voigt value (all regions) times Pv, at grid offset delta
-__device__ __forceinline__ float w4_value_f32(float delta, const float4 &B) {
+// (kept out of line: only the few points with |x| + y < 5.5 reach it, and inlining
+// its four regions into every unrolled (point, condition) slot bloats the kernel)
+__device__ __noinline__ float w4_value_f32(float delta, const float4 &B) {
     float x = B.x * fabsf(delta);
     Cx<float> w = w4_eval<float>(x, B.y, nullptr);
     return B.z * w.re;
@@ -284,10 +307,10 @@ template <int PROF>
 __device__ __forceinline__ float contrib_single(float u, float delta, const float4 &A, const float4 &B,
                                                 const float *s_x, const float *s_w, int ngh) {
     if (PROF == XC_VOIGT_W4) {
-        if (u < B.w) return w4_value_f32(delta, B);
+        // region I only; points with |x| + y < 15 belong to the centre-zone kernel
         float D = fmaf(u, u + A.x, A.y);
         float q = fmaf(A.z, u, A.w);
-        return q * rcp_approx(D);
+        return u >= B.w ? q * rcp_approx(D) : 0.f;
     } else if (PROF == XC_LORENTZ) {
         return A.y * rcp_approx(u + A.x);
     } else if (PROF == XC_DOPPLER) {
@@ -546,6 +569,137 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 }
 
 // ---------------------------------------------------------------------------
+// Centre-zone kernel (Voigt w4): the points with |x| + y < 15, which the main
+// kernel skips.  Gather form again: a CTA owns CORE_T consecutive grid points
+// (one per thread) and a group of conditions, walks the lines whose centre zone
+// can reach its window (|nu - x| < 18.02 alpha_max, a range of the sorted list),
+// and for each of its points sums, in line order, Re w by region: I (rounding
+// cases at the boundary), II (real two-Lorentzian-pair form) or III/IV (complex
+// w4).  It runs after the main kernel and adds its FP32 sums into the FP64
+// output each thread owns, so the result stays deterministic.  Which kernel
+// evaluates a (line, point, condition) is decided by the same test u < thr^2
+// on bit-identical values, so every contribution is counted exactly once.
+// ---------------------------------------------------------------------------
+constexpr int CORE_T = 256;
+constexpr int CORE_CG = 32;
+constexpr int CORE_SCH = 16;
+
+struct CoreParams {
+    LinesDev L;
+    const int *n_abs;
+    const float *f_frac;
+    const int *ka_abs, *kb_abs;
+    const CParam *cp;
+    const unsigned *win_lo, *win_hi;
+    int n_cond;
+    int64_t n_pts;
+    float h, inv_h;
+    double *sigma;
+};
+
+// Re w in w4's region I from (x, y): 0.5641896 y (0.5 + X + Y) / ((X + Y - 0.5)^2 + 2Y)
+__device__ __forceinline__ float w4_region1_re(float x, float y) {
+    float X = x * x, Y = y * y;
+    float t = X + Y - 0.5f;
+    return 0.5641896f * y * (0.5f + X + Y) * rcp_approx(fmaf(t, t, 2.f * Y));
+}
+
+__global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
+    __shared__ float4 sB[CORE_SCH][CORE_CG];
+    __shared__ int4 sMi[CORE_SCH];
+    __shared__ float2 sMf[CORE_SCH];
+    __shared__ double sScale[CORE_CG];
+    __shared__ float sAcc[CORE_CG][CORE_T];  // per-thread column: the thread's point, every condition
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t kw = (int64_t)blockIdx.x * CORE_T;
+    const int grp = blockIdx.y;
+    const float jf = (float)tid;
+    if (tid < CORE_CG) {
+        int c = grp * CORE_CG + tid;
+        sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < CORE_CG; ++c) sAcc[c][tid] = 0.f;
+    const unsigned lo = p.win_lo[blockIdx.x], hi = p.win_hi[blockIdx.x];
+    for (unsigned l0 = lo; l0 < hi; l0 += CORE_SCH) {
+        const int cnt = (int)(hi - l0 < (unsigned)CORE_SCH ? hi - l0 : (unsigned)CORE_SCH);
+        __syncthreads();
+        if (tid < cnt) {
+            size_t l = (size_t)l0 + tid;
+            int ka = p.ka_abs[l], kb = p.kb_abs[l];
+            int64_t kaw = (int64_t)ka - kw, kbw = (int64_t)kb - kw;
+            if (kb < ka) { kaw = 1; kbw = 0; }
+            kaw = i64max(-1, i64min(kaw, CORE_T));
+            kbw = i64max(-1, i64min(kbw, CORE_T));
+            sMi[tid] = make_int4((int)((int64_t)p.n_abs[l] - kw), (int)kaw, (int)kbw, 0);
+            sMf[tid].x = p.f_frac[l];
+        }
+#pragma unroll 1
+        for (int pb = 0; pb < CORE_SCH * CORE_CG; pb += CORE_T) {
+            int q = pb + tid;
+            int i = q / CORE_CG, c = q % CORE_CG;
+            int cc = grp * CORE_CG + c;
+            float t2 = -1.f;
+            float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
+            if (i < cnt && cc < p.n_cond)
+                line_consts<XC_VOIGT_W4>(p.L, (size_t)l0 + i, p.cp[cc], p.h, p.inv_h, &A, &B, &t2);
+            if (i < cnt) sB[i][c] = B;
+#pragma unroll
+            for (int o = CORE_CG / 2; o > 0; o >>= 1) t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
+            if (i < cnt && lane == 0) sMf[i].y = t2;  // CORE_CG == 32: one line per warp
+        }
+        __syncthreads();
+        for (int i = 0; i < cnt; ++i) {
+            const int4 m = sMi[i];
+            const float2 mf = sMf[i];
+            const float d = (jf - (float)m.x) - mf.x;
+            const float u = d * d;
+            if (!(u < mf.y) || tid < m.y || tid > m.z) continue;
+            const float ad = fabsf(d);
+#pragma unroll 1
+            for (int c = 0; c < CORE_CG; ++c) {
+                const float4 B = sB[i][c];
+                if (u < B.w) {
+                    float x = B.x * ad, y = B.y, s = x + y;
+                    float w = s >= 15.f ? w4_region1_re(x, y)
+                                        : (s >= 5.5f ? w4_region2_re(x, y) : w4_eval<float>(x, y, nullptr).re);
+                    sAcc[c][tid] = fmaf(B.z, w, sAcc[c][tid]);
+                }
+            }
+        }
+    }
+    const int64_t k = kw + tid;
+    if (k < p.n_pts) {
+#pragma unroll
+        for (int c = 0; c < CORE_CG; ++c) {
+            int cc = grp * CORE_CG + c;
+            float a = sAcc[c][tid];
+            if (cc < p.n_cond && a != 0.f)
+                p.sigma[(size_t)cc * (size_t)p.n_pts + (size_t)k] += (double)a * sScale[c];
+        }
+    }
+}
+
+// window -> line range for the centre zone: |nu - x| < K nu with K = 18.02 alpha_max/nu
+__global__ void k_core_ranges(const double *__restrict__ nu, int64_t n, double nu_A, double step, int64_t n_pts,
+                              double K, int n_win, unsigned *lo, unsigned *hi) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_win) return;
+    int64_t k0 = (int64_t)w * CORE_T;
+    int64_t k1 = i64min(k0 + CORE_T, n_pts) - 1;
+    double x0 = grid_x(nu_A, step, k0), x1 = grid_x(nu_A, step, k1);
+    double a0 = x0 > 0.0 ? x0 / (1.0 + K) : x0, a1 = x1 > 0.0 ? x1 / (1.0 - K) : x1;
+    a0 -= 1e-9 * (fabs(x0) + 1.0);
+    a1 += 1e-9 * (fabs(x1) + 1.0);
+    int64_t a = 0, b = n;
+    while (a < b) { int64_t m = a + ((b - a) >> 1); if (nu[m] < a0) a = m + 1; else b = m; }
+    lo[w] = (unsigned)a;
+    int64_t a2 = a, b2 = n;
+    while (a2 < b2) { int64_t m = a2 + ((b2 - a2) >> 1); if (nu[m] <= a1) a2 = m + 1; else b2 = m; }
+    hi[w] = (unsigned)(a2 < a ? a : a2);
+}
+
+// ---------------------------------------------------------------------------
 // kernel table
 // ---------------------------------------------------------------------------
 typedef void (*GatherFn)(GatherParams);
@@ -604,6 +758,8 @@ struct Plan {
     int *order = nullptr, *counter = nullptr;
     GeomStats *gs = nullptr;
     float *gx = nullptr, *gw = nullptr;
+    int n_win_core = 0;                         // centre-zone kernel windows (Voigt w4)
+    unsigned *core_lo = nullptr, *core_hi = nullptr;
 };
 
 xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl) {
@@ -619,6 +775,8 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_cp = carve((size_t)n_cond_call * sizeof(CParam));
     size_t o_lo = carve((size_t)pl->n_win * 4), o_hi = carve((size_t)pl->n_win * 4);
     size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
+    pl->n_win_core = (int)((a.grid.n + CORE_T - 1) / CORE_T);
+    size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
     BT_TRY(st->tiles.ensure(off));
     char *b = st->tiles.as<char>();
     pl->n_abs = (int *)(b + o_n);
@@ -633,6 +791,8 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     pl->gs = (GeomStats *)(b + o_gs);
     pl->gx = (float *)(b + o_nodes);
     pl->gw = pl->gx + 64;
+    pl->core_lo = (unsigned *)(b + o_clo);
+    pl->core_hi = (unsigned *)(b + o_chi);
     return XC_OK;
 }
 
@@ -684,6 +844,33 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     gp.sigma = a.sigma + (size_t)c0 * (size_t)a.grid.n;
     pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
     *launches += 1;
+    if (a.opts.profile == XC_VOIGT_W4 && max_lines == 0) {
+        // centre zone: |x| + y < 15, |nu - x| < 18.02 alpha <= K nu
+        double amax = 0.0;
+        for (int c = 0; c < nc; ++c)
+            amax = std::max(amax, alpha_coef(a.conds_host[c0 + c].T, a.conds_host[c0 + c].mass_da));
+        const double K = 18.05 * amax;
+        k_core_ranges<<<(pl.n_win_core + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step,
+                                                                   a.grid.n, K, pl.n_win_core, pl.core_lo,
+                                                                   pl.core_hi);
+        CoreParams cp;
+        cp.L = a.L;
+        cp.n_abs = pl.n_abs;
+        cp.f_frac = pl.f;
+        cp.ka_abs = pl.ka;
+        cp.kb_abs = pl.kb;
+        cp.cp = pl.cp;
+        cp.win_lo = pl.core_lo;
+        cp.win_hi = pl.core_hi;
+        cp.n_cond = nc;
+        cp.n_pts = a.grid.n;
+        cp.h = gp.h;
+        cp.inv_h = gp.inv_h;
+        cp.sigma = gp.sigma;
+        dim3 cg(pl.n_win_core, (nc + CORE_CG - 1) / CORE_CG);
+        k_core_w4_f32<<<cg, CORE_T, 0, s>>>(cp);
+        *launches += 2;
+    }
     BT_TRY(cudaGetLastError());
     return XC_OK;
 }
@@ -920,6 +1107,7 @@ constexpr int kStaticR = 4;                               // tile shape used by 
 constexpr int kStaticMinW = GT * kStaticR;
 constexpr int kStaticMaxWin = (int)((kStaticMaxPoints + kStaticMinW - 1) / kStaticMinW);
 constexpr int kStaticMaxTiles = kStaticMaxWin * kStaticMaxCond;
+constexpr int kStaticMaxCoreWin = (int)((kStaticMaxPoints + CORE_T - 1) / CORE_T);
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -934,7 +1122,9 @@ struct StaticLayout {
     static constexpr size_t o_lo = o_q + al256(kStaticMaxCond * 3 * sizeof(double) + kStaticMaxCond * sizeof(int));
     static constexpr size_t o_hi = o_lo + al256((size_t)kStaticMaxWin * 4);
     static constexpr size_t o_ord = o_hi + al256((size_t)kStaticMaxWin * 4);
-    static constexpr size_t o_ctr = o_ord + al256((size_t)kStaticMaxTiles * 4);
+    static constexpr size_t o_clo = o_ord + al256((size_t)kStaticMaxTiles * 4);
+    static constexpr size_t o_chi = o_clo + al256((size_t)kStaticMaxCoreWin * 4);
+    static constexpr size_t o_ctr = o_chi + al256((size_t)kStaticMaxCoreWin * 4);
     static constexpr size_t o_gs = o_ctr + 256;
     static constexpr size_t o_nodes = o_gs + 256;
     static constexpr size_t o_flag = o_nodes + 512;
@@ -1063,6 +1253,9 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
     pl.gs = (GeomStats *)(base + StaticLayout::o_gs);
     pl.gx = (float *)(base + StaticLayout::o_nodes);
     pl.gw = pl.gx + 64;
+    pl.n_win_core = (int)((grid->n + CORE_T - 1) / CORE_T);
+    pl.core_lo = (unsigned *)(base + StaticLayout::o_clo);
+    pl.core_hi = (unsigned *)(base + StaticLayout::o_chi);
     CondDev *dc = (CondDev *)(base + StaticLayout::o_cd);
     double *qT = (double *)(base + StaticLayout::o_q), *qQ = qT + kStaticMaxCond, *qD = qQ + kStaticMaxCond;
     int *tix_d = (int *)(qD + kStaticMaxCond);
