@@ -31,7 +31,10 @@ import xcsynth as xs  # noqa: E402
 
 METRIC = "line x gridpoint Voigt evals/s (FP32 batched, 32 conditions)"
 UNIT = "evals/s"
-ALG_FLOPS_PER_EVAL = 11  # w4 region-I rational with hoisted line constants (FMA = 2)
+# FP32 flops of one region-I w4 evaluation with the per-line constants hoisted:
+# t = u + E (1), D = u t + F (2), q = P u + PC (2), q / D (1), accumulate (2).
+# At the FMA/MUFU bound of 32 evals/clk/SM this is exactly the FP32 peak of 256 flops/clk/SM.
+ALG_FLOPS_PER_EVAL = 8
 
 
 def parse():

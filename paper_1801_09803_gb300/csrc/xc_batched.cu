@@ -41,7 +41,6 @@
 namespace xc {
 
 constexpr int GT = 256;          // threads per CTA
-constexpr int NWARP = GT / 32;
 constexpr int SCH = 64;          // lines per staged chunk
 constexpr int FOLD_CHUNKS = 8;   // FP32 -> FP64 fold period, in chunks (512 lines)
 constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 region-I constant / sqrt(pi)
@@ -86,6 +85,45 @@ struct GatherParams {
 };
 
 __device__ __forceinline__ float rcp_approx(float x) { return recip(x); }
+
+// Two FP32 values in one 64-bit register pair, for the packed f32x2 arithmetic of
+// sm_100-class GPUs: one instruction issue performs two FP32 adds / multiplies /
+// FMAs (the FMA pipe throughput is unchanged; the issue slots are halved).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ float lo2(f32x2 v) { float a, b; upk2(v, a, b); return a; }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 rcp2(f32x2 a) {
+    float x, y;
+    upk2(a, x, y);
+    return pk2(rcp_approx(x), rcp_approx(y));
+}
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -334,32 +372,69 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
 
 // FP32 register partials -> FP64 output (each thread owns its points)
 template <int R, int CG>
-__device__ __forceinline__ void fold_acc(float (&acc)[R][CG], const int (&ji)[R], int64_t kw, int grp,
+__device__ __forceinline__ void fold_acc(f32x2 (&acc)[R / 2][CG], const int (&ji)[R], int64_t kw, int grp,
                                          const GatherParams &p, const double *sScale, bool first) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int64_t k = kw + ji[r];
-        if (k < p.n_pts) {
+    for (int q = 0; q < R / 2; ++q) {
 #pragma unroll
-            for (int c = 0; c < CG; ++c) {
-                int cc = grp * CG + c;
-                if (cc < p.n_cond) {
+        for (int c = 0; c < CG; ++c) {
+            float v2[2];
+            upk2(acc[q][c], v2[0], v2[1]);
+            int cc = grp * CG + c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int64_t k = kw + ji[2 * q + h];
+                if (k < p.n_pts && cc < p.n_cond) {
                     double *dst = p.sigma + (size_t)cc * (size_t)p.n_pts + (size_t)k;
-                    double v = (double)acc[r][c] * sScale[c];
+                    double v = (double)v2[h] * sScale[c];
                     if (first) *dst = v; else *dst += v;
                 }
             }
+            acc[q][c] = 0ull;
         }
-#pragma unroll
-        for (int c = 0; c < CG; ++c) acc[r][c] = 0.f;
+    }
+}
+
+// per-(line, condition) constants in shared memory: Voigt w4 and Lorentz keep them
+// duplicated in packed pairs ((E,E),(F,F),(P,P),(PC,PC) / (G,G),(P,P)) for the f32x2 path
+template <int PROF>
+struct ConstLayout {
+    static constexpr int kU2 = (PROF == XC_VOIGT_W4) ? 2 : 1;   // ulonglong2 per (line, condition)
+    static constexpr size_t kBytes = (PROF == XC_VOIGT_W4) ? 32 : 16;
+};
+
+template <int PROF>
+__device__ __forceinline__ void store_consts(unsigned char *base, int idx, const float4 &A) {
+    if (PROF == XC_VOIGT_W4) {
+        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(base) + 2 * idx;
+        q[0] = make_ulonglong2(pk2(A.x, A.x), pk2(A.y, A.y));
+        q[1] = make_ulonglong2(pk2(A.z, A.z), pk2(A.w, A.w));
+    } else if (PROF == XC_LORENTZ) {
+        reinterpret_cast<ulonglong2 *>(base)[idx] = make_ulonglong2(pk2(A.x, A.x), pk2(A.y, A.y));
+    } else {
+        reinterpret_cast<float4 *>(base)[idx] = A;
+    }
+}
+
+template <int PROF>
+__device__ __forceinline__ float4 load_consts(const unsigned char *base, int idx) {
+    if (PROF == XC_VOIGT_W4) {
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base) + 2 * idx;
+        ulonglong2 a = q[0], b = q[1];
+        return make_float4(lo2(a.x), lo2(a.y), lo2(b.x), lo2(b.y));
+    } else if (PROF == XC_LORENTZ) {
+        ulonglong2 a = reinterpret_cast<const ulonglong2 *>(base)[idx];
+        return make_float4(lo2(a.x), lo2(a.y), 0.f, 0.f);
+    } else {
+        return reinterpret_cast<const float4 *>(base)[idx];
     }
 }
 
 template <int PROF, int R, int CG>
 struct SmemLayout {
     static constexpr bool kHasB = (PROF == XC_VOIGT_W4);
-    static constexpr size_t kA = (size_t)SCH * CG * sizeof(float4);
-    static constexpr size_t kB = kHasB ? kA : 0;
+    static constexpr size_t kA = (size_t)SCH * CG * ConstLayout<PROF>::kBytes;
+    static constexpr size_t kB = kHasB ? (size_t)SCH * CG * sizeof(float4) : 0;
     static constexpr size_t kMetaI = (size_t)SCH * sizeof(int4);
     static constexpr size_t kMetaF = (size_t)SCH * sizeof(float2);
     static constexpr size_t kScale = (size_t)CG * sizeof(double);
@@ -371,7 +446,7 @@ template <int PROF, int R, int CG>
 __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherParams p) {
     using Lay = SmemLayout<PROF, R, CG>;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *sA = reinterpret_cast<float4 *>(smem);
+    // per-(line, condition) constants start at smem (see store_consts / load_consts)
     float4 *sB = reinterpret_cast<float4 *>(smem + Lay::kA);
     int4 *sMi = reinterpret_cast<int4 *>(smem + Lay::kA + Lay::kB);
     float2 *sMf = reinterpret_cast<float2 *>(smem + Lay::kA + Lay::kB + Lay::kMetaI);
@@ -396,6 +471,9 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         ji[r] = span0 + r * 32 + lane;
         jf[r] = (float)ji[r];
     }
+    f32x2 jf2[R / 2];
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) jf2[q] = pk2(jf[2 * q], jf[2 * q + 1]);
 
     for (;;) {
         __syncthreads();
@@ -414,11 +492,11 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
             sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
         }
         __syncthreads();
-        float acc[R][CG];
+        f32x2 acc[R / 2][CG];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int q = 0; q < R / 2; ++q)
 #pragma unroll
-            for (int c = 0; c < CG; ++c) acc[r][c] = 0.f;
+            for (int c = 0; c < CG; ++c) acc[q][c] = 0ull;
         bool first_fold = true;
         int chunk = 0;
 
@@ -460,7 +538,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                         else if (PROF == XC_VOIGT_GH_BINNED) A = make_float4(0.f, 1.f, 1.f, 0.f);
                         else A = make_float4(1.f, 0.f, 0.f, 0.f);
                     }
-                    sA[i * CG + c] = A;
+                    store_consts<PROF>(smem, i * CG + c, A);
                     if (Lay::kHasB) sB[i * CG + c] = B;
                 }
                 if (CG > 1) {
@@ -493,45 +571,67 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 unsigned fm = __ballot_sync(0xffffffffu, fast);
                 unsigned sm = __ballot_sync(0xffffffffu, slow);
                 if (PROF == XC_VOIGT_W4 || PROF == XC_LORENTZ) {
-                    while (__popc(fm) >= 2) {
-                        int i1 = ib + __ffs(fm) - 1;
+                    // lines covering the whole span with no centre-zone point in it:
+                    // unmasked, two grid points per packed f32x2 operation
+                    const ulonglong2 *cq = reinterpret_cast<const ulonglong2 *>(smem);
+                    // Lorentz: two lines share one reciprocal, (P1 D2 + P2 D1) / (D1 D2): its
+                    // unpaired form would be bound by the MUFU pipe (1/4 of the FMA rate)
+                    while (PROF == XC_LORENTZ && __popc(fm) >= 2) {
+                        const int i1 = ib + __ffs(fm) - 1;
                         fm &= fm - 1;
-                        int i2 = ib + __ffs(fm) - 1;
+                        const int i2 = ib + __ffs(fm) - 1;
                         fm &= fm - 1;
                         const int4 m1 = sMi[i1], m2 = sMi[i2];
-                        const float f1 = sMf[i1].x, f2 = sMf[i2].x;
-                        const float n1 = (float)m1.x, n2 = (float)m2.x;
-                        float u1[R], u2[R];
+                        const float f1 = sMf[i1].x, n1 = (float)m1.x, f2 = sMf[i2].x, n2 = (float)m2.x;
+                        const f32x2 nn1 = pk2(n1, n1), ff1 = pk2(f1, f1), nn2 = pk2(n2, n2), ff2 = pk2(f2, f2);
+                        f32x2 ua[R / 2], ub[R / 2];
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            float d1 = (jf[r] - n1) - f1;
-                            float d2 = (jf[r] - n2) - f2;
-                            u1[r] = d1 * d1;
-                            u2[r] = d2 * d2;
+                        for (int q = 0; q < R / 2; ++q) {
+                            f32x2 da = sub2(sub2(jf2[q], nn1), ff1), db = sub2(sub2(jf2[q], nn2), ff2);
+                            ua[q] = mul2(da, da);
+                            ub[q] = mul2(db, db);
                         }
 #pragma unroll
                         for (int c = 0; c < CG; ++c) {
-                            const float4 A1 = sA[i1 * CG + c], A2 = sA[i2 * CG + c];
+                            const ulonglong2 a = cq[i1 * CG + c], b = cq[i2 * CG + c];
 #pragma unroll
-                            for (int r = 0; r < R; ++r) {
-                                float D1, D2, q1, q2;
-                                if (PROF == XC_VOIGT_W4) {
-                                    D1 = fmaf(u1[r], u1[r] + A1.x, A1.y);
-                                    D2 = fmaf(u2[r], u2[r] + A2.x, A2.y);
-                                    q1 = fmaf(A1.z, u1[r], A1.w);
-                                    q2 = fmaf(A2.z, u2[r], A2.w);
-                                } else {
-                                    D1 = u1[r] + A1.x;
-                                    D2 = u2[r] + A2.x;
-                                    q1 = A1.y;
-                                    q2 = A2.y;
-                                }
-                                float num = fmaf(q1, D2, q2 * D1);
-                                acc[r][c] = fmaf(num, rcp_approx(D1 * D2), acc[r][c]);
+                            for (int q = 0; q < R / 2; ++q) {
+                                f32x2 D1 = add2(ua[q], a.x), D2 = add2(ub[q], b.x);
+                                f32x2 num = fma2(a.y, D2, mul2(b.y, D1));
+                                acc[q][c] = fma2(num, rcp2(mul2(D1, D2)), acc[q][c]);
                             }
                         }
                     }
-                    sm |= fm;  // a leftover unpaired fast line takes the single path
+                    while (fm) {
+                        const int i1 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int4 m1 = sMi[i1];
+                        const float f1 = sMf[i1].x, n1 = (float)m1.x;
+                        const f32x2 nn = pk2(n1, n1), ff = pk2(f1, f1);
+                        f32x2 u2[R / 2];
+#pragma unroll
+                        for (int q = 0; q < R / 2; ++q) {
+                            f32x2 d2 = sub2(sub2(jf2[q], nn), ff);
+                            u2[q] = mul2(d2, d2);
+                        }
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            if (PROF == XC_VOIGT_W4) {
+                                const ulonglong2 a0 = cq[2 * (i1 * CG + c)], a1 = cq[2 * (i1 * CG + c) + 1];
+#pragma unroll
+                                for (int q = 0; q < R / 2; ++q) {
+                                    f32x2 D = fma2(u2[q], add2(u2[q], a0.x), a0.y);
+                                    f32x2 num = fma2(a1.x, u2[q], a1.y);
+                                    acc[q][c] = fma2(num, rcp2(D), acc[q][c]);
+                                }
+                            } else {
+                                const ulonglong2 a0 = cq[i1 * CG + c];
+#pragma unroll
+                                for (int q = 0; q < R / 2; ++q)
+                                    acc[q][c] = fma2(a0.y, rcp2(add2(u2[q], a0.x)), acc[q][c]);
+                            }
+                        }
+                    }
                 }
                 while (sm) {
                     int i1 = ib + __ffs(sm) - 1;
@@ -549,11 +649,16 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     }
 #pragma unroll
                     for (int c = 0; c < CG; ++c) {
-                        const float4 A1 = sA[i1 * CG + c];
+                        const float4 A1 = load_consts<PROF>(smem, i1 * CG + c);
                         const float4 B1 = Lay::kHasB ? sB[i1 * CG + c] : make_float4(0.f, 0.f, 0.f, -1.f);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if (in1[r]) acc[r][c] += contrib_single<PROF>(u1[r], d1[r], A1, B1, sX, sW, p.ngh);
+                        for (int q = 0; q < R / 2; ++q) {
+                            float a0, a1;
+                            upk2(acc[q][c], a0, a1);
+                            if (in1[2 * q]) a0 += contrib_single<PROF>(u1[2 * q], d1[2 * q], A1, B1, sX, sW, p.ngh);
+                            if (in1[2 * q + 1])
+                                a1 += contrib_single<PROF>(u1[2 * q + 1], d1[2 * q + 1], A1, B1, sX, sW, p.ngh);
+                            acc[q][c] = pk2(a0, a1);
                         }
                     }
                 }
@@ -621,11 +726,15 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
 #pragma unroll
     for (int c = 0; c < CORE_CG; ++c) sAcc[c][tid] = 0.f;
     const unsigned lo = p.win_lo[blockIdx.x], hi = p.win_hi[blockIdx.x];
-    for (unsigned l0 = lo; l0 < hi; l0 += CORE_SCH) {
-        const int cnt = (int)(hi - l0 < (unsigned)CORE_SCH ? hi - l0 : (unsigned)CORE_SCH);
+    // strided chunks (lines lo + ci + j * nch): the centre zones of one chunk spread
+    // over the whole window instead of piling onto the threads of one spot
+    const unsigned nl = hi - lo;
+    const unsigned nch = (nl + CORE_SCH - 1) / CORE_SCH;
+    for (unsigned ci = 0; ci < nch; ++ci) {
+        const int cnt = (int)((nl - ci + nch - 1) / nch);
         __syncthreads();
         if (tid < cnt) {
-            size_t l = (size_t)l0 + tid;
+            size_t l = (size_t)lo + ci + (size_t)tid * nch;
             int ka = p.ka_abs[l], kb = p.kb_abs[l];
             int64_t kaw = (int64_t)ka - kw, kbw = (int64_t)kb - kw;
             if (kb < ka) { kaw = 1; kbw = 0; }
@@ -642,7 +751,8 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             float t2 = -1.f;
             float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
             if (i < cnt && cc < p.n_cond)
-                line_consts<XC_VOIGT_W4>(p.L, (size_t)l0 + i, p.cp[cc], p.h, p.inv_h, &A, &B, &t2);
+                line_consts<XC_VOIGT_W4>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
+                                         &t2);
             if (i < cnt) sB[i][c] = B;
 #pragma unroll
             for (int o = CORE_CG / 2; o > 0; o >>= 1) t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
