@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 form on a subset")
     ap.add_argument("--profile", default=None, help="override the workload's line profile")
+    ap.add_argument("--no-extras", action="store_true", help="skip the C1/C2/C4 secondary timings")
     return ap.parse_args()
 
 
@@ -195,6 +196,56 @@ def run_reference(args, dist, rank, world):
 
 
 # ---------------------------------------------------------------------------- GB300 arm
+def _timed(torch, fn, reps=1):
+    fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def secondary_measurements(xc, torch, dev):
+    """The other workloads, one timing each (CUDA events, device-resident inputs):
+    C1 (1e5 lines, FP64 plain and FP32), C2 (1e7 lines, width-limited cut, Voigt w4
+    FP64 plain and FP32, GH binned FP32), C4 (1e7 lines, 2x2 conditions: FP32
+    forward and FP32 adjoint).  Values are evals/s over the exact eval count."""
+    out = {}
+    for name in ("C1", "C2", "C4"):
+        W = xs.WORKLOADS[name]
+        L = {k: torch.from_numpy(v).to(dev) for k, v in xs.gen_lines(W.seed, 0, W.n_lines, W.nu_lo, W.nu_hi).items()}
+        E, g = xs.gen_states(W.seed, W.n_states)
+        eng = xc.Engine(dev.index or 0)
+        eng.load_lines(L)
+        eng.set_states(E, g)
+        grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+        conds = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da) for c in xs.conditions_for(W)]
+        sig = torch.empty((len(conds), W.n_points), dtype=torch.float64, device=dev)
+        res = {}
+        cases = [("voigt_w4", "fp64"), ("voigt_w4", "fp32")]
+        if name == "C2":
+            cases.append(("voigt_gh_binned", "fp32"))
+        for prof, prec in cases:
+            o = xc.make_opts(prof, prec, W.cutoff, W.cutoff_width_mult, W.n_gh)
+            ev = eng.count_evals(conds, grid, o)
+            ms = _timed(torch, lambda: eng.cross_section_batched(conds, grid, o, sig))
+            res[f"{prof}_{prec}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+        if name == "C4":
+            o = xc.make_opts("voigt_w4", "fp32", W.cutoff)
+            gs = torch.ones((len(conds), W.n_points), dtype=torch.float64, device=dev)
+            ev = eng.count_evals(conds, grid, o)
+            ms = _timed(torch, lambda: eng.cross_section_vjp(conds, grid, o, gs, per_line=True))
+            res["vjp_voigt_w4_fp32"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+        out[name] = res
+        eng.close()
+        del L, sig
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_xc(args, dist, rank, world, local):
     import torch
     import paper_1801_09803_gb300 as xc
@@ -297,6 +348,10 @@ def run_xc(args, dist, rank, world, local):
         ev1 = eng.count_evals(c1, grid, o64)
         fp64 = {"value": ev1 / dt, "unit": UNIT, "conditions": 1}
 
+    extras = None
+    if not args.no_extras and rank == 0:
+        extras = secondary_measurements(xc, torch, dev)
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -329,6 +384,8 @@ def run_xc(args, dist, rank, world, local):
         "stage_ms": {"sort": sort_t["sort"], "gather": sort_t["gather"], "profile_mean": prof},
         "tuning": eng.tuning(),
     }
+    if extras:
+        out["other_workloads"] = extras
     if fp64:
         out["fp64_plain"] = fp64
         out["fp32_over_fp64"] = (evals / (prof / 1e3)) / fp64["value"] if prof else None

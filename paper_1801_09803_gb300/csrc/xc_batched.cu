@@ -574,6 +574,40 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     // lines covering the whole span with no centre-zone point in it:
                     // unmasked, two grid points per packed f32x2 operation
                     const ulonglong2 *cq = reinterpret_cast<const ulonglong2 *>(smem);
+                    // Voigt w4 region I: two lines share one reciprocal,
+                    //   q1/D1 + q2/D2 = (q1 D2 + q2 D1) / (D1 D2),
+                    // 5 FMA-pipe ops + 0.5 reciprocal per eval; the unpaired form (4 + 1) is
+                    // bound by the MUFU reciprocal rate instead
+                    while (PROF == XC_VOIGT_W4 && __popc(fm) >= 2) {
+                        const int i1 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int i2 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int4 m1 = sMi[i1], m2 = sMi[i2];
+                        const float f1 = sMf[i1].x, n1 = (float)m1.x, f2 = sMf[i2].x, n2 = (float)m2.x;
+                        const f32x2 nn1 = pk2(n1, n1), ff1 = pk2(f1, f1), nn2 = pk2(n2, n2), ff2 = pk2(f2, f2);
+                        f32x2 ua[R / 2], ub[R / 2];
+#pragma unroll
+                        for (int q = 0; q < R / 2; ++q) {
+                            f32x2 da = sub2(sub2(jf2[q], nn1), ff1), db = sub2(sub2(jf2[q], nn2), ff2);
+                            ua[q] = mul2(da, da);
+                            ub[q] = mul2(db, db);
+                        }
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            const ulonglong2 a0 = cq[2 * (i1 * CG + c)], a1 = cq[2 * (i1 * CG + c) + 1];
+                            const ulonglong2 b0 = cq[2 * (i2 * CG + c)], b1 = cq[2 * (i2 * CG + c) + 1];
+#pragma unroll
+                            for (int q = 0; q < R / 2; ++q) {
+                                f32x2 D1 = fma2(ua[q], add2(ua[q], a0.x), a0.y);
+                                f32x2 D2 = fma2(ub[q], add2(ub[q], b0.x), b0.y);
+                                f32x2 q1 = fma2(a1.x, ua[q], a1.y);
+                                f32x2 q2 = fma2(b1.x, ub[q], b1.y);
+                                f32x2 num = fma2(q1, D2, mul2(q2, D1));
+                                acc[q][c] = fma2(num, rcp2(mul2(D1, D2)), acc[q][c]);
+                            }
+                        }
+                    }
                     // Lorentz: two lines share one reciprocal, (P1 D2 + P2 D1) / (D1 D2): its
                     // unpaired form would be bound by the MUFU pipe (1/4 of the FMA rate)
                     while (PROF == XC_LORENTZ && __popc(fm) >= 2) {

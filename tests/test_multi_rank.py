@@ -33,7 +33,9 @@ def _worker(rank, world, port, out):
     E, g = xs.gen_states(41, 500)
     Q, dQ = oracle.partition_function(E, g, 1300.0)
     cond = oracle.make_condition(1300.0, 1.0, Q, dQ)
-    nu_A, step, n, cut = 1000.0, 0.01, 5001, 5.0
+    # step 2^-7: every grid point nu_A + k*step is exact in binary, so a shard that starts
+    # its own grid at point k0 produces bit-identical grid points
+    nu_A, step, n, cut = 1000.0, 1.0 / 128.0, 6401, 5.0
     k0, k1 = grid_shard(n, world, rank)
     l0, l1 = halo_line_range(S["nu"], nu_A, step, k0, k1, cut)
     sub = {k: v[l0:l1] for k, v in S.items()}

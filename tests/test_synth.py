@@ -64,3 +64,14 @@ def test_workloads():
     T = np.array(c3.temperatures)
     assert abs(T[0] - 300.0) < 1e-9 and abs(T[-1] - 3000.0) < 1e-9
     assert np.allclose(np.diff(np.log(T)), np.log(10) / 7)
+
+
+def test_torch_generator_matches_numpy():
+    torch = __import__("pytest").importorskip("torch")
+    a = xs.gen_lines(77, 1000, 20000, 0.0, 20000.0)
+    b = xs.gen_lines_torch(77, 1000, 20000, 0.0, 20000.0, device="cpu", chunk=7001)
+    for k in ("nu", "j_lo", "g_up", "gamma_ref", "n_T"):
+        assert np.array_equal(a[k], b[k].numpy()), k
+    for k in ("elower", "A"):  # library log1p / pow may differ in the last bit before rounding
+        d = np.abs(a[k].astype(np.float64) - b[k].numpy().astype(np.float64)) / np.maximum(np.abs(a[k]), 1e-30)
+        assert d.max() <= 1.2e-7, k

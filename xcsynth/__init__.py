@@ -145,6 +145,59 @@ def gen_lines_at(seed: int, idx: np.ndarray, nu_lo: float, nu_hi: float,
     }
 
 
+def gen_lines_torch(seed: int, i0: int, n: int, nu_lo: float, nu_hi: float, device="cuda",
+                    jmax: int = 50, g_ns: int = 1, chunk: int = 1 << 26):
+    """The same lines as gen_lines, generated with torch on `device` (for lists too
+    large to build on the host).  uint64 arithmetic is emulated on int64 tensors:
+    products wrap modulo 2^64 and right shifts are masked to be logical.  nu, J'',
+    J', gamma_ref and n_T are bit-identical to gen_lines; E'' and A go through
+    log1p / pow of the device library and can differ from numpy's in the last
+    float64 bit before rounding to float32."""
+    import torch
+
+    def s64(v):  # uint64 constant as int64
+        v &= 0xFFFFFFFFFFFFFFFF
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    m1, m2, gold = s64(0xBF58476D1CE4E5B9), s64(0x94D049BB133111EB), s64(0x9E3779B97F4A7C15)
+    sd = s64(seed)
+
+    def lsr(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    def uni(idx, fld):
+        z = (idx * 8 + fld) * gold
+        z = z ^ sd
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        return lsr(z, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+    out = {
+        "nu": torch.empty(n, dtype=torch.float64, device=device),
+        "elower": torch.empty(n, dtype=torch.float32, device=device),
+        "A": torch.empty(n, dtype=torch.float32, device=device),
+        "gamma_ref": torch.empty(n, dtype=torch.float32, device=device),
+        "n_T": torch.empty(n, dtype=torch.float32, device=device),
+        "g_up": torch.empty(n, dtype=torch.int16, device=device),
+        "j_lo": torch.empty(n, dtype=torch.int16, device=device),
+    }
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        idx = torch.arange(i0 + s, i0 + e, dtype=torch.int64, device=device)
+        out["nu"][s:e] = nu_hi - uni(idx, F_NU) * (nu_hi - nu_lo)
+        out["elower"][s:e] = torch.clamp(-3000.0 * torch.log1p(-uni(idx, F_E)), max=20000.0).to(torch.float32)
+        jl = torch.floor(uni(idx, F_J) * (jmax + 1)).to(torch.int64)
+        dj = torch.floor(uni(idx, F_DJ) * 3).to(torch.int64) - 1
+        dj = torch.where((jl == 0) & (dj == -1), torch.ones_like(dj), dj)
+        out["j_lo"][s:e] = jl.to(torch.int16)
+        out["g_up"][s:e] = (g_ns * (2 * (jl + dj) + 1)).to(torch.int16)
+        out["A"][s:e] = torch.pow(10.0, -6.0 + 8.0 * uni(idx, F_A)).to(torch.float32)
+        out["gamma_ref"][s:e] = (0.02 + 0.08 * uni(idx, F_GAMMA)).to(torch.float32)
+        out["n_T"][s:e] = (0.4 + 0.4 * uni(idx, F_N)).to(torch.float32)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Workload descriptions (sizes and conditions of the five benchmark cases)
 # ---------------------------------------------------------------------------
