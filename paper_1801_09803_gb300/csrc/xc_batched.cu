@@ -856,8 +856,10 @@ struct Variant {
 #define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG>, SmemLayout<P, R, CG>::total}
 static const Variant kVariants[] = {
     XC_VARIANT(XC_VOIGT_W4, 4, 16), XC_VARIANT(XC_VOIGT_W4, 2, 32), XC_VARIANT(XC_VOIGT_W4, 4, 8),
-    XC_VARIANT(XC_VOIGT_W4, 8, 4),  XC_VARIANT(XC_VOIGT_W4, 8, 2),  XC_VARIANT(XC_VOIGT_W4, 8, 1),
-    XC_VARIANT(XC_LORENTZ, 4, 16),  XC_VARIANT(XC_LORENTZ, 8, 4),   XC_VARIANT(XC_LORENTZ, 8, 1),
+    XC_VARIANT(XC_VOIGT_W4, 8, 8),  XC_VARIANT(XC_VOIGT_W4, 8, 4),  XC_VARIANT(XC_VOIGT_W4, 8, 2),
+    XC_VARIANT(XC_VOIGT_W4, 8, 1),
+    XC_VARIANT(XC_LORENTZ, 4, 16),  XC_VARIANT(XC_LORENTZ, 8, 8),   XC_VARIANT(XC_LORENTZ, 8, 4),
+    XC_VARIANT(XC_LORENTZ, 8, 1),
     XC_VARIANT(XC_DOPPLER, 4, 16),  XC_VARIANT(XC_DOPPLER, 8, 4),   XC_VARIANT(XC_DOPPLER, 8, 1),
     XC_VARIANT(XC_VOIGT_GH_SAMPLED, 4, 16), XC_VARIANT(XC_VOIGT_GH_SAMPLED, 8, 4),
     XC_VARIANT(XC_VOIGT_GH_SAMPLED, 8, 1),

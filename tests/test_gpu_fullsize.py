@@ -105,3 +105,39 @@ def test_c2_full_size(xc, oracle_lib, profile):
     print(f"C2 {profile}: FP64 {e64:.3g}, FP32 {e32:.3g} (sampled); FP32 vs FP64 band {band:.3g}, "
           f"max rel over all bins {np.max(np.abs(out['fp32'][m] - out['fp64'][m]) / out['fp64'][m]):.3g}")
     assert e64 < 1e-5 and e32 < 2e-4 and band < 1e-5
+
+
+def test_c5_seeded_subset_against_oracle(xc, oracle_lib):
+    """Mixed precision at maximum size: the error is reported on a seeded 1e6-line
+    subset of the 1e9-line list (nu in (0, 20000], 2000 K, 1 bar, 2 000 001 points):
+    FP32 and FP64 GPU paths on that subset against the oracle's full grid, as max
+    relative error over bins above 1e-6 of the peak and integrated band error."""
+    W = xs.WORKLOADS["C5"]
+    idx = xs.subset_indices(W.n_lines, 1_000_000, 55)
+    L = xs.gen_lines_at(W.seed, idx, W.nu_lo, W.nu_hi)
+    E, g = xs.gen_states(W.seed, W.n_states)
+    c = xs.conditions_for(W)[0]
+    eng = xc.Engine(0)
+    eng.load_lines({k: torch.from_numpy(v).cuda() for k, v in L.items()})
+    eng.set_states(E, g)
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    cond = xc.make_condition(c["T"], c["P"], mass_da=W.mass_da)
+    got = {}
+    for prec in ("fp32", "fp64"):
+        d = torch.empty((1, W.n_points), dtype=torch.float64, device="cuda:0")
+        eng.cross_section_batched([cond], grid, xc.make_opts("voigt_w4", prec, W.cutoff), d)
+        got[prec] = d[0].cpu().numpy()
+    eng.close()
+    Q, dQ = oracle_lib.partition_function(E, g, c["T"])
+    ref = oracle_lib.cross_section(L, oracle_lib.make_condition(c["T"], c["P"], Q, dQ, mass_da=W.mass_da),
+                                   W.grid_lo, W.step, W.n_points, oracle_lib.make_opts("voigt_w4", W.cutoff),
+                                   nthreads=NTHREADS)
+    m = ref > 1e-6 * ref.max()
+    res = {}
+    for prec, tol in (("fp32", 2e-4), ("fp64", 1e-5)):
+        mr = float(np.max(np.abs(got[prec][m] - ref[m]) / ref[m]))
+        band = float(abs(got[prec].sum() - ref.sum()) / ref.sum())
+        res[prec] = (mr, band)
+        assert mr < tol and band < (1e-5 if prec == "fp32" else 1e-10)
+    print(f"C5 1e6-line subset: FP32 max rel {res['fp32'][0]:.3g} band {res['fp32'][1]:.3g}; "
+          f"FP64 max rel {res['fp64'][0]:.3g} band {res['fp64'][1]:.3g}")
