@@ -208,10 +208,12 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
                                double *d_gamma_ref_line, double *d_n_line, int mem, void *stream);
 
 /* Stage timing: when enabled, the library records CUDA events on the launch
- * stream around its kernels; xc_last_timings returns the milliseconds of the
- * most recent call per stage: [0] sort, [1] gather/load, [2] Q(T), [3] line
- * parameters, [4] window ranges, [5] profile kernel (or graph replay),
- * [6] VJP kernel, [7] reduce/finish.  Stages not run read 0. */
+ * stream around its kernels (as event nodes inside its CUDA graphs); xc_last_timings
+ * returns the milliseconds of the most recent call per stage: [0] sort,
+ * [1] gather/load, [2] Q(T), [3] line parameters (FP64 path) or the whole FP32
+ * sweep (setup kernels + profile kernels), [4] window ranges (FP64 path) or the
+ * FP32 centre-zone kernel (Voigt w4), [5] the main profile kernel, [6] adjoint,
+ * [7] host<->device copies.  Stages not run read 0. */
 xc_status xc_set_timing(xc_handle *h, int enable);
 xc_status xc_last_timings(xc_handle *h, float *ms_out8);
 

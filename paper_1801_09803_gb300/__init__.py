@@ -314,7 +314,7 @@ class Engine:
     def timings(self) -> Dict[str, float]:
         ms = (C.c_float * 8)()
         _check(lib().xc_last_timings(self._h, ms))
-        names = ["sort", "gather", "Q", "params", "ranges", "profile", "vjp", "finish"]
+        names = ["sort", "gather", "Q", "params_or_sweep", "ranges_or_core", "profile", "vjp", "copies"]
         return {k: float(v) for k, v in zip(names, ms)}
 
     def tuning(self) -> str:

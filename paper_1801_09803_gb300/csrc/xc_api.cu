@@ -654,8 +654,11 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         a.sigma = sig;
         a.stream = s;
         a.timing = h->timing;
-        a.ev_begin = h->ev[2 * ST_PROFILE];
-        a.ev_end = h->ev[2 * ST_PROFILE + 1];
+        a.ev_begin = h->ev[2 * ST_PARAMS];          // whole sweep (setup + kernels)
+        a.ev_end = h->ev[2 * ST_PARAMS + 1];
+        a.ev_main0 = h->ev[2 * ST_PROFILE];         // main kernel
+        a.ev_main1 = h->ev[2 * ST_PROFILE + 1];
+        a.ev_core1 = h->ev[2 * ST_RANGES + 1];      // centre-zone kernel: main end -> core end
         if (opts->profile == XC_VOIGT_GH_BINNED || opts->profile == XC_VOIGT_GH_SAMPLED) {
             if ((st = ensure_gh(h, opts->n_gh, s))) return st;
             a.ghx = h->gh.as<double>();
@@ -664,7 +667,7 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         int64_t nl = 0;
         if ((st = batched_run(&h->batched, a, &nl))) return st;
         h->launches += nl;
-        used[ST_PROFILE] = true;
+        used[ST_PARAMS] = true;  // whole sweep; per-kernel times are read below
     }
     if (mem == XC_MEM_HOST) {
         stage_begin(h, ST_FINISH, s);
@@ -674,6 +677,15 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
     }
     XC_TRY(cudaStreamSynchronize(s));
     collect_timing(h, used);
+    if (h->timing && opts->precision == XC_FP32 && h->n_lines > 0 && opts->width_mult <= 0.0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE], h->ev[2 * ST_PROFILE + 1]) == cudaSuccess)
+            h->last_ms[ST_PROFILE] = ms;
+        if (opts->profile == XC_VOIGT_W4 &&
+            cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE + 1], h->ev[2 * ST_RANGES + 1]) == cudaSuccess)
+            h->last_ms[ST_RANGES] = ms;
+        cudaGetLastError();
+    }
     return XC_OK;
 }
 

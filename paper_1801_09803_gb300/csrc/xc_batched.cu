@@ -988,7 +988,10 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     gp.ghw = pl.gw;
     gp.ngh = a.opts.n_gh;
     gp.sigma = a.sigma + (size_t)c0 * (size_t)a.grid.n;
+    const bool ev = a.timing && a.ev_main0 && max_lines == 0;
+    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main0, s, cudaEventRecordExternal));
     pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
+    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main1, s, cudaEventRecordExternal));
     *launches += 1;
     if (a.opts.profile == XC_VOIGT_W4 && max_lines == 0) {
         // centre zone: |x| + y < 15, |nu - x| < 18.02 alpha <= K nu
@@ -1017,6 +1020,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         k_core_w4_f32<<<cg, CORE_T, 0, s>>>(cp);
         *launches += 2;
     }
+    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_core1, s, cudaEventRecordExternal));
     BT_TRY(cudaGetLastError());
     return XC_OK;
 }
@@ -1182,7 +1186,8 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     // graph cache: the sweep (geometry, constants, ranges, tile ranking, counter
     // reset, persistent kernel) is captured once per shape and buffer set, then replayed
     char kb[512];
-    snprintf(kb, sizeof(kb), "%s v%d L%p C%p S%p T%p", shape_key(a, a.n_cond).c_str(), cfg.variant,
+    snprintf(kb, sizeof(kb), "%s v%d t%d L%p C%p S%p T%p", shape_key(a, a.n_cond).c_str(), cfg.variant,
+             a.timing ? 1 : 0,
              (const void *)a.L.nu, (const void *)a.conds_dev, (void *)a.sigma, (void *)st->tiles.p);
     std::string gkey = kb;
     auto it = st->graphs.find(gkey);

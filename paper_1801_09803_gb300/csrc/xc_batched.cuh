@@ -21,6 +21,9 @@ struct BatchedArgs {
     cudaStream_t stream = nullptr;
     bool timing = false;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    // with timing: events recorded (as graph event nodes when captured) before the main
+    // kernel, after it, and after the centre-zone kernel
+    cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr, ev_core1 = nullptr;
     const double *ghx = nullptr, *ghw = nullptr;  // device Gauss-Hermite nodes/weights
 };
 

@@ -58,6 +58,32 @@ __device__ inline VjpLineCond line_cond64(const LinesDev &L, size_t l, const Con
 
 __device__ inline double shfl64(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Re w and its partial derivatives d/dx, d/dy (x >= 0) in w4's regions I and II,
+// from their real forms: region I is one pair of Lorentzians (nodes +-1/sqrt2),
+// region II two pairs (nodes +-sqrt(Q_m), Q_m = (3 -+ sqrt 6)/2):
+//   Re w = y sum_m A_m (X + Y + Q_m) / ((X + Y - Q_m)^2 + 4 Q_m Y),  X = x^2, Y = y^2.
+__device__ inline float w4_re_grad_12(float x, float y, float *dx, float *dy) {
+    constexpr double a = 1.410474, b = 0.5641896, s6 = 2.449489742783178098;
+    const bool r1 = x + y >= 15.f;
+    const float Qm[2] = {r1 ? 0.5f : (float)((3.0 - s6) / 2.0), (float)((3.0 + s6) / 2.0)};
+    const float Am[2] = {r1 ? 0.5641896f : (float)((a - b * ((3.0 - s6) / 2.0)) / s6),
+                         r1 ? 0.f : (float)(-(a - b * ((3.0 + s6) / 2.0)) / s6)};
+    const float X = x * x, Y = y * y;
+    float S = 0.f, SX = 0.f, SY = 0.f;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        float N = X + Y + Qm[m], t = X + Y - Qm[m];
+        float D = fmaf(t, t, 4.f * Qm[m] * Y);
+        float rD = 1.f / D, rD2 = rD * rD;
+        S = fmaf(Am[m] * N, rD, S);
+        SX = fmaf(Am[m], (D - 2.f * N * t) * rD2, SX);                    // d(N/D)/dX
+        SY = fmaf(Am[m], (D - N * (2.f * t + 4.f * Qm[m])) * rD2, SY);    // d(N/D)/dY
+    }
+    *dx = y * SX * 2.f * x;
+    *dy = S + y * SY * 2.f * y;
+    return y * S;
+}
+
 // value and derivatives of the profile (FP64 reference form, all w4 regions)
 template <int PROF>
 __device__ inline void prof_deriv64(double D, double al, double ga, double *V, double *dVa, double *dVg) {
@@ -157,7 +183,19 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                                 s1 = fmaf(g, fmaf(-2.f * N, t, Dn) * rD2, s1);
                                 float q = fmaf(Dn, N + 2.f * g2, -4.f * g2 * N * N);
                                 s2 = fmaf(g, q * rD2, s2);
+                            } else if (a_sc * fabsf(D) + yv >= 5.5f) {
+                                // region II (or I by rounding at its edge): real form, FP32
+                                float rx, ry;
+                                float w = w4_re_grad_12(a_sc * fabsf(D), yv, &rx, &ry);
+                                float v = (float)0.46971863934982566 / alf * w;
+                                float k2 = (float)(0.6931471805599453 / 1.772453850905516027) / (alf * alf);
+                                float dVD = k2 * (D < 0.f ? -rx : rx), dg = k2 * ry;
+                                c0 = fmaf(g, v, c0);
+                                c1 = fmaf(g, -(v + D * dVD + gaf * dg) / alf, c1);
+                                c2 = fmaf(g, dg, c2);
                             } else {
+                                // regions III/IV: complex rationals whose derivative cancels in
+                                // FP32; evaluated in FP64 (a narrow band around the centre)
                                 double D64 = __dsub_rn(grid_x(nu_A, step, k), nu);
                                 double V, dVa, dVg;
                                 prof_deriv64<XC_VOIGT_W4>(D64, al, ga, &V, &dVa, &dVg);
