@@ -749,6 +749,8 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
     __shared__ float2 sMf[CORE_SCH];
     __shared__ double sScale[CORE_CG];
     __shared__ float sAcc[CORE_CG][CORE_T];  // per-thread column: the thread's point, every condition
+    __shared__ float sThr[CORE_SCH][CORE_CG];         // per line: thresholds u < thr^2, descending
+    __shared__ unsigned char sOrd[CORE_SCH][CORE_CG]; // ... and their conditions
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t kw = (int64_t)blockIdx.x * CORE_T;
     const int grp = blockIdx.y;
@@ -788,9 +790,30 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
                 line_consts<XC_VOIGT_W4>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
                                          &t2);
             if (i < cnt) sB[i][c] = B;
+            // one line per warp (CORE_CG == 32 lanes = conditions): bitonic sort of the
+            // thresholds, largest first, so the point loop can stop at the first
+            // condition whose centre zone does not reach the point
+            float key = -t2;
+            int val = c;
 #pragma unroll
-            for (int o = CORE_CG / 2; o > 0; o >>= 1) t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
-            if (i < cnt && lane == 0) sMf[i].y = t2;  // CORE_CG == 32: one line per warp
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    float pkey = __shfl_xor_sync(0xffffffffu, key, j);
+                    int pval = __shfl_xor_sync(0xffffffffu, val, j);
+                    bool asc = (lane & k) == 0, low = (lane & j) == 0;
+                    bool take = low ? (asc ? pkey < key : pkey > key) : (asc ? pkey > key : pkey < key);
+                    if (take) {
+                        key = pkey;
+                        val = pval;
+                    }
+                }
+            }
+            if (i < cnt) {
+                sThr[i][lane] = -key;
+                sOrd[i][lane] = (unsigned char)val;
+                if (lane == 0) sMf[i].y = -key;  // the largest threshold of the line
+            }
         }
         __syncthreads();
         for (int i = 0; i < cnt; ++i) {
@@ -801,14 +824,14 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             if (!(u < mf.y) || tid < m.y || tid > m.z) continue;
             const float ad = fabsf(d);
 #pragma unroll 1
-            for (int c = 0; c < CORE_CG; ++c) {
+            for (int kk = 0; kk < CORE_CG; ++kk) {
+                if (!(u < sThr[i][kk])) break;
+                const int c = sOrd[i][kk];
                 const float4 B = sB[i][c];
-                if (u < B.w) {
-                    float x = B.x * ad, y = B.y, s = x + y;
-                    float w = s >= 15.f ? w4_region1_re(x, y)
-                                        : (s >= 5.5f ? w4_region2_re(x, y) : w4_eval<float>(x, y, nullptr).re);
-                    sAcc[c][tid] = fmaf(B.z, w, sAcc[c][tid]);
-                }
+                float x = B.x * ad, y = B.y, s = x + y;
+                float w = s >= 15.f ? w4_region1_re(x, y)
+                                    : (s >= 5.5f ? w4_region2_re(x, y) : w4_eval<float>(x, y, nullptr).re);
+                sAcc[c][tid] = fmaf(B.z, w, sAcc[c][tid]);
             }
         }
     }
