@@ -47,6 +47,7 @@ constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 regio
 constexpr float kSqrtLn2f = 0.8325546111576977f;
 constexpr float kSqrtLn2OverPi = 0.46971863934982566f;  // sqrt(ln2/pi)
 constexpr float kPiM32 = 0.17958712212516656f;          // pi^(-3/2)
+constexpr float kFarU = 1.f / 0.003f;                    // far-wing series from u >= C / 0.003
 
 struct CParam {
     double inv_scale;   // 1 / scale (power of two)
@@ -273,7 +274,7 @@ __global__ void k_nodes_to_float(const double *x, const double *w, int n, float 
 // ---------------------------------------------------------------------------
 template <int PROF>
 __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
-                                            float4 *A, float4 *B, float *thr2) {
+                                            float4 *A, float4 *B, float *thr2, float4 *S) {
     const float nu = (float)L.nu[l];
     const float E = L.elower[l];
     // Boltzmann factor exp(-c2 E/T) = 2^-(E c2 log2e / T), product kept to ~1 ulp
@@ -285,6 +286,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     float ga = c.pscale * L.gamma_ref[l] * ex2_approx((L.n_T[l] + c.nshift) * c.log2Tr);  // Eq. e:gamma_L
     float ah = __fmul_rn(al, inv_h), gh = __fmul_rn(ga, inv_h);   // widths in grid steps
     *thr2 = -1.f;
+    *S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
     if (PROF == XC_VOIGT_W4) {
         float b = ah * ah * (float)(0.5 / 0.6931471805599453);
         float g2 = gh * gh;
@@ -302,6 +304,14 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         float t2 = y < 15.f ? __fmul_rn(thr, thr) : -1.f;
         *B = make_float4(a, y, Pv, t2);
         *thr2 = t2;
+        // far wing: the same rational as a series in r = 1/u,
+        //   P(u + C)/(u^2 + E u + F) = P r (1 + c1 r + c2 r^2 + ...),
+        //   c1 = C - E = 3b - g^2,  c2 = E^2 - C E - F = (g^2 - 5b)^2 - 20 b^2.
+        // u^2 + E u + F has its two roots on |u| = C, so |c_n| <= (2n + 1) C^n and the
+        // terms dropped beyond r^2 stay below 7 x^3 / (1 - 9x/7) with x = C r; at
+        // u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational.
+        float e5 = g2 - 5.f * b;
+        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), C * kFarU);
     } else if (PROF == XC_LORENTZ) {
         *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
     } else if (PROF == XC_DOPPLER) {
@@ -399,16 +409,18 @@ __device__ __forceinline__ void fold_acc(f32x2 (&acc)[R / 2][CG], const int (&ji
 // duplicated in packed pairs ((E,E),(F,F),(P,P),(PC,PC) / (G,G),(P,P)) for the f32x2 path
 template <int PROF>
 struct ConstLayout {
-    static constexpr int kU2 = (PROF == XC_VOIGT_W4) ? 2 : 1;   // ulonglong2 per (line, condition)
-    static constexpr size_t kBytes = (PROF == XC_VOIGT_W4) ? 32 : 16;
+    // Voigt w4: 48 B = packed (E,E),(F,F),(P,P),(PC,PC) for the rational, then
+    // {p0, p1, p2, u_far} of the far-wing series
+    static constexpr size_t kBytes = (PROF == XC_VOIGT_W4) ? 48 : 16;
 };
 
 template <int PROF>
-__device__ __forceinline__ void store_consts(unsigned char *base, int idx, const float4 &A) {
+__device__ __forceinline__ void store_consts(unsigned char *base, int idx, const float4 &A, const float4 &S) {
     if (PROF == XC_VOIGT_W4) {
-        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(base) + 2 * idx;
+        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(base + (size_t)48 * idx);
         q[0] = make_ulonglong2(pk2(A.x, A.x), pk2(A.y, A.y));
         q[1] = make_ulonglong2(pk2(A.z, A.z), pk2(A.w, A.w));
+        reinterpret_cast<float4 *>(q)[2] = S;
     } else if (PROF == XC_LORENTZ) {
         reinterpret_cast<ulonglong2 *>(base)[idx] = make_ulonglong2(pk2(A.x, A.x), pk2(A.y, A.y));
     } else {
@@ -419,7 +431,7 @@ __device__ __forceinline__ void store_consts(unsigned char *base, int idx, const
 template <int PROF>
 __device__ __forceinline__ float4 load_consts(const unsigned char *base, int idx) {
     if (PROF == XC_VOIGT_W4) {
-        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base) + 2 * idx;
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base + (size_t)48 * idx);
         ulonglong2 a = q[0], b = q[1];
         return make_float4(lo2(a.x), lo2(a.y), lo2(b.x), lo2(b.y));
     } else if (PROF == XC_LORENTZ) {
@@ -529,16 +541,17 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 float t2 = -1.f;
                 if (v) {
                     float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
+                    float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                     if (cc < p.n_cond) {
                         line_consts<PROF>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
-                                          &t2);
+                                          &t2, &S);
                     } else {  // padding condition: contributes exactly 0
                         if (PROF == XC_VOIGT_W4) A = make_float4(1.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_BINNED) A = make_float4(0.f, 1.f, 1.f, 0.f);
                         else A = make_float4(1.f, 0.f, 0.f, 0.f);
                     }
-                    store_consts<PROF>(smem, i * CG + c, A);
+                    store_consts<PROF>(smem, i * CG + c, A, S);
                     if (Lay::kHasB) sB[i * CG + c] = B;
                 }
                 if (CG > 1) {
@@ -593,10 +606,50 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                             ua[q] = mul2(da, da);
                             ub[q] = mul2(db, db);
                         }
+                        // conditions for which every point of the span lies in the far wing of
+                        // both lines (u >= u_far): series in r = 1/u, with r shared by them all
+                        unsigned far = 0;
+                        {
+                            const float c1 = n1 + f1, c2 = n2 + f2;
+                            const float dm1 = fmaxf(fmaxf((float)span0 - c1, c1 - (float)span1), 0.f);
+                            const float dm2 = fmaxf(fmaxf((float)span0 - c2, c2 - (float)span1), 0.f);
+                            bool fl = false;
+                            if (lane < CG) {
+                                const float uf1 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i1 * CG + lane))[2].w;
+                                const float uf2 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i2 * CG + lane))[2].w;
+                                fl = (dm1 * dm1 >= uf1) && (dm2 * dm2 >= uf2);
+                            }
+                            far = __ballot_sync(0xffffffffu, fl);
+                        }
+                        f32x2 ra[R / 2], rb[R / 2];
+                        if (far) {
+#pragma unroll
+                            for (int q = 0; q < R / 2; ++q) {
+                                ra[q] = rcp2(ua[q]);
+                                rb[q] = rcp2(ub[q]);
+                            }
+                        }
 #pragma unroll
                         for (int c = 0; c < CG; ++c) {
-                            const ulonglong2 a0 = cq[2 * (i1 * CG + c)], a1 = cq[2 * (i1 * CG + c) + 1];
-                            const ulonglong2 b0 = cq[2 * (i2 * CG + c)], b1 = cq[2 * (i2 * CG + c) + 1];
+                            const unsigned char *e1 = smem + (size_t)48 * (i1 * CG + c);
+                            const unsigned char *e2 = smem + (size_t)48 * (i2 * CG + c);
+                            if ((far >> c) & 1u) {
+                                const float4 s1 = reinterpret_cast<const float4 *>(e1)[2];
+                                const float4 s2 = reinterpret_cast<const float4 *>(e2)[2];
+                                const f32x2 p01 = pk2(s1.x, s1.x), p11 = pk2(s1.y, s1.y), p21 = pk2(s1.z, s1.z);
+                                const f32x2 p02 = pk2(s2.x, s2.x), p12 = pk2(s2.y, s2.y), p22 = pk2(s2.z, s2.z);
+#pragma unroll
+                                for (int q = 0; q < R / 2; ++q) {
+                                    f32x2 t1 = fma2(fma2(p21, ra[q], p11), ra[q], p01);
+                                    f32x2 t2 = fma2(fma2(p22, rb[q], p12), rb[q], p02);
+                                    acc[q][c] = fma2(t2, rb[q], fma2(t1, ra[q], acc[q][c]));
+                                }
+                                continue;
+                            }
+                            const ulonglong2 a0 = reinterpret_cast<const ulonglong2 *>(e1)[0];
+                            const ulonglong2 a1 = reinterpret_cast<const ulonglong2 *>(e1)[1];
+                            const ulonglong2 b0 = reinterpret_cast<const ulonglong2 *>(e2)[0];
+                            const ulonglong2 b1 = reinterpret_cast<const ulonglong2 *>(e2)[1];
 #pragma unroll
                             for (int q = 0; q < R / 2; ++q) {
                                 f32x2 D1 = fma2(ua[q], add2(ua[q], a0.x), a0.y);
@@ -651,7 +704,8 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 #pragma unroll
                         for (int c = 0; c < CG; ++c) {
                             if (PROF == XC_VOIGT_W4) {
-                                const ulonglong2 a0 = cq[2 * (i1 * CG + c)], a1 = cq[2 * (i1 * CG + c) + 1];
+                                const ulonglong2 *e1 = reinterpret_cast<const ulonglong2 *>(smem + (size_t)48 * (i1 * CG + c));
+                                const ulonglong2 a0 = e1[0], a1 = e1[1];
 #pragma unroll
                                 for (int q = 0; q < R / 2; ++q) {
                                     f32x2 D = fma2(u2[q], add2(u2[q], a0.x), a0.y);
@@ -785,10 +839,10 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             int i = q / CORE_CG, c = q % CORE_CG;
             int cc = grp * CORE_CG + c;
             float t2 = -1.f;
-            float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
+            float4 A, S, B = make_float4(0.f, 0.f, 0.f, -1.f);
             if (i < cnt && cc < p.n_cond)
                 line_consts<XC_VOIGT_W4>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
-                                         &t2);
+                                         &t2, &S);
             if (i < cnt) sB[i][c] = B;
             // one line per warp (CORE_CG == 32 lanes = conditions): bitonic sort of the
             // thresholds, largest first, so the point loop can stop at the first
