@@ -63,6 +63,13 @@ enum {
 /* xc_load_lines flags */
 enum { XC_ASSUME_SORTED = 1u };
 
+/* xc_opts.flags.  With XC_FP32, Voigt w4, a fixed cut and 16 or more conditions,
+ * the far wings (points at least D(l, c) grid steps from a line, D chosen so that
+ * the region-I rational equals its three-term series in 1/u to < 2e-7) are summed
+ * on the tensor cores as a matrix product (TF32 operands split hi + lo, FP32
+ * accumulation); XC_OPT_NO_TENSOR_CORES keeps every evaluation on the CUDA cores. */
+enum { XC_OPT_NO_TENSOR_CORES = 1 };
+
 typedef struct xc_handle xc_handle;
 
 /* Line list, structure of arrays, n entries each (28 bytes per line).
@@ -111,7 +118,7 @@ typedef struct {
     double cutoff;      /* cm^-1, > 0 */
     double width_mult;  /* 0 = fixed cut */
     int n_gh;
-    int flags;          /* reserved, 0 */
+    int flags;          /* XC_OPT_* bits, 0 by default */
 } xc_opts;
 
 /* Library version string (static storage). */
@@ -253,6 +260,13 @@ xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len);
 
 /* Kernel launches issued by the last call (for launch accounting). */
 xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out);
+
+/* Fix the tile shape of the FP32 CUDA-core kernel for later batched calls on this
+ * handle: R grid points per thread and CG conditions per tile, one of the compiled
+ * shapes of the profile (R in {2, 4, 8}; CG in {1, 2, 4, 8, 16, 32}); (0, 0) restores
+ * the autotuner.  A call whose profile has no such shape fails with XC_EUNSUPPORTED.
+ * For testing every compiled kernel and for reproducible timing. */
+xc_status xc_set_tile_shape(xc_handle *h, int R, int CG);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ EXPORTED_SYMBOLS = [
     "xc_version", "xc_last_error", "xc_create", "xc_destroy", "xc_load_lines", "xc_num_lines", "xc_get_lines",
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
-    "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static",
+    "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static", "xc_set_tile_shape",
 ]
 
 
@@ -95,6 +95,7 @@ def lib(build_if_missing: bool = False):
         "xc_set_timing": ([vp, i], i), "xc_last_timings": ([vp, vp], i),
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
         "xc_get_tuning": ([vp, C.c_char_p, st], i),
+        "xc_set_tile_shape": ([vp, i, i], i),
         "xc_cross_section_batched_static": ([C.POINTER(XcLines), st, vp, vp, st, C.POINTER(XcCondition), st,
                                              C.POINTER(XcGrid), C.POINTER(XcOpts), vp, vp], i),
     }
@@ -146,9 +147,14 @@ def make_grid(nu_A: float, step: float, n: int) -> XcGrid:
     return XcGrid(float(nu_A), float(step), int(n))
 
 
+XC_OPT_NO_TENSOR_CORES = 1
+
+
 def make_opts(profile: str = "voigt_w4", precision: str = "fp64", cutoff: float = 25.0,
-              width_mult: float = 0.0, n_gh: int = 20) -> XcOpts:
-    return XcOpts(PROFILES[profile], PRECISIONS[precision], float(cutoff), float(width_mult), int(n_gh), 0)
+              width_mult: float = 0.0, n_gh: int = 20, tensor_cores: bool = True) -> XcOpts:
+    """tensor_cores=False keeps the FP32 Voigt w4 far wings on the CUDA cores."""
+    return XcOpts(PROFILES[profile], PRECISIONS[precision], float(cutoff), float(width_mult), int(n_gh),
+                  0 if tensor_cores else XC_OPT_NO_TENSOR_CORES)
 
 
 _LINE_FIELDS = [("nu", np.float64), ("elower", np.float32), ("A", np.float32), ("gamma_ref", np.float32),
@@ -316,6 +322,11 @@ class Engine:
         _check(lib().xc_last_timings(self._h, ms))
         names = ["sort", "gather", "Q", "params_or_sweep", "ranges_or_core", "profile", "vjp", "copies"]
         return {k: float(v) for k, v in zip(names, ms)}
+
+    def set_tile_shape(self, R: int = 0, CG: int = 0):
+        """Fix the FP32 CUDA-core kernel's tile shape (R points per thread, CG conditions
+        per tile); (0, 0) returns to the autotuner."""
+        _check(lib().xc_set_tile_shape(self._h, int(R), int(CG)))
 
     def tuning(self) -> str:
         buf = C.create_string_buffer(4096)

@@ -161,6 +161,7 @@ xc_status check_opts(const xc_opts *o) {
     }
     if (!(o->cutoff > 0.0) || !isfinite(o->cutoff)) { set_error("cutoff must be > 0"); return XC_EINVAL; }
     if (o->width_mult < 0.0 || !isfinite(o->width_mult)) { set_error("width_mult must be >= 0"); return XC_EINVAL; }
+    if (o->flags & ~XC_OPT_NO_TENSOR_CORES) { set_error("unknown opts flags 0x%x", (unsigned)o->flags); return XC_EINVAL; }
     if ((o->profile == XC_VOIGT_GH_BINNED || o->profile == XC_VOIGT_GH_SAMPLED) && (o->n_gh < 1 || o->n_gh > 64)) {
         set_error("n_gh must be in 1..64");
         return XC_EINVAL;
@@ -676,6 +677,7 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         used[ST_FINISH] = true;
     }
     XC_TRY(cudaStreamSynchronize(s));
+    if (opts->precision == XC_FP32 && h->n_lines > 0 && (st = batched_check(&h->batched))) return st;
     collect_timing(h, used);
     if (h->timing && opts->precision == XC_FP32 && h->n_lines > 0 && opts->width_mult <= 0.0) {
         float ms = 0.f;
@@ -758,6 +760,15 @@ xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len) {
     if (st) return st;
     if (!buf || !len) { set_error("NULL buffer"); return XC_EINVAL; }
     snprintf(buf, len, "%s", h->batched.last_tuning.c_str());
+    return XC_OK;
+}
+
+xc_status xc_set_tile_shape(xc_handle *h, int R, int CG) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (R < 0 || CG < 0 || (R == 0) != (CG == 0)) { set_error("tile shape (%d, %d): both 0 or both > 0", R, CG); return XC_EINVAL; }
+    h->batched.force_R = R;
+    h->batched.force_CG = CG;
     return XC_OK;
 }
 

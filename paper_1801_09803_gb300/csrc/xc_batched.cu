@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "xc_batched.cuh"
+#include "xc_tcgen05.cuh"
 
 namespace xc {
 
@@ -82,6 +83,8 @@ struct GatherParams {
     int max_lines_per_tile;    // autotune probe: stop early (0 = all)
     const float *ghx, *ghw;    // Gauss-Hermite nodes (float), device
     int ngh;
+    int tc_far;                // Voigt w4: the far-wing kernel has written the (line, condition,
+                               // 128-point block) pairs with span_far; evaluate the rest, add
     double *sigma;
 };
 
@@ -310,8 +313,15 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         // u^2 + E u + F has its two roots on |u| = C, so |c_n| <= (2n + 1) C^n and the
         // terms dropped beyond r^2 stay below 7 x^3 / (1 - 9x/7) with x = C r; at
         // u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational.
+        // S.w = D: integer radius (grid steps) beyond which every point is in that far
+        // zone and in region I: a block of points [t0, t1] with n - D > t1 or n + D < t0
+        // (n = integer part of the line position) qualifies.  Integer tests, so every
+        // kernel that splits the work this way takes the same decision.
+        // (explicitly rounded: the same bits wherever this is inlined)
         float e5 = g2 - 5.f * b;
-        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), C * kFarU);
+        const float Crn = __fadd_rn(__fmul_rn(__fmul_rn(ah, ah), (float)(0.5 / 0.6931471805599453)), __fmul_rn(gh, gh));
+        float uf = fmaxf(__fmul_rn(Crn, kFarU), t2);
+        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), ceilf(__fsqrt_rn(uf)) + 1.f);
     } else if (PROF == XC_LORENTZ) {
         *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
     } else if (PROF == XC_DOPPLER) {
@@ -454,8 +464,38 @@ struct SmemLayout {
     static constexpr size_t total = kA + kB + kMetaI + kMetaF + kScale + kNodes + 16;
 };
 
+// the far radius D of (line, condition) idx among the staged Voigt w4 constants
+__device__ __forceinline__ float sfar_radius(const unsigned char *smem, int idx) {
+    return reinterpret_cast<const float4 *>(smem + (size_t)48 * idx)[2].w;
+}
+
+// every point of [t0, t1] lies beyond the far radius D of a line at integer position n
+// (all integers well below 2^24, so the float comparisons are exact; D = inf: never)
+__device__ __forceinline__ bool span_far(int n, float D, int t0, int t1) {
+    return (float)(n - t1) > D || (float)(t0 - n) > D;
+}
+
+// far-wing series of two lines (constants e1, e2) at R points, condition c:
+//   acc += r1 (p0 + r1 (p1 + r1 p2)) + r2 (...), two points per packed operation
+template <int R, int CG>
+__device__ __forceinline__ void w4_series_pair(f32x2 (&acc)[R / 2][CG], int c, const unsigned char *e1,
+                                               const unsigned char *e2, const f32x2 (&ra)[R / 2],
+                                               const f32x2 (&rb)[R / 2]) {
+    const float4 s1 = reinterpret_cast<const float4 *>(e1)[2];
+    const float4 s2 = reinterpret_cast<const float4 *>(e2)[2];
+    const f32x2 p01 = pk2(s1.x, s1.x), p11 = pk2(s1.y, s1.y), p21 = pk2(s1.z, s1.z);
+    const f32x2 p02 = pk2(s2.x, s2.x), p12 = pk2(s2.y, s2.y), p22 = pk2(s2.z, s2.z);
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+        f32x2 t1 = fma2(fma2(p21, ra[q], p11), ra[q], p01);
+        f32x2 t2 = fma2(fma2(p22, rb[q], p12), rb[q], p02);
+        acc[q][c] = fma2(t2, rb[q], fma2(t1, ra[q], acc[q][c]));
+    }
+}
+
 template <int PROF, int R, int CG>
 __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherParams p) {
+    constexpr unsigned kAllConds = CG >= 32 ? 0xffffffffu : ((1u << CG) - 1u);
     using Lay = SmemLayout<PROF, R, CG>;
     extern __shared__ __align__(16) unsigned char smem[];
     // per-(line, condition) constants start at smem (see store_consts / load_consts)
@@ -497,8 +537,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         const int win = tile / p.n_groups, grp = tile % p.n_groups;
         const int64_t kw = (int64_t)win * W;
         const unsigned lo = p.win_lo[win];
-        unsigned hi = p.win_hi[win];
-        if (p.max_lines_per_tile > 0 && hi - lo > (unsigned)p.max_lines_per_tile) hi = lo + p.max_lines_per_tile;
+        const unsigned hi = p.win_hi[win];
         if (tid < CG) {
             int c = grp * CG + tid;
             sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
@@ -517,7 +556,10 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         // chunk falls on all warps instead of on the one warp that owns those centres.
         const unsigned nl = hi - lo;
         const unsigned nch = (nl + SCH - 1) / SCH;
-        for (unsigned ci = 0; ci < nch; ++ci) {
+        // autotune probe: the first chunks only; each samples the whole line range, so
+        // the probe sees the same mix of line positions as the full tile
+        const unsigned nch_run = p.max_lines_per_tile > 0 ? min(nch, (unsigned)(p.max_lines_per_tile / SCH)) : nch;
+        for (unsigned ci = 0; ci < nch_run; ++ci) {
             const int cnt = (int)((nl - ci + nch - 1) / nch);
             __syncthreads();
             // ---- stage: per-line geometry and per-(line, condition) constants
@@ -529,7 +571,11 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 if (kb < ka) { kaw = 1; kbw = 0; }
                 kaw = i64max(-1, i64min(kaw, W));
                 kbw = i64max(-1, i64min(kbw, W));
-                sMi[tid] = make_int4((int)((int64_t)na - kw), (int)kaw, (int)kbw, 0);
+                // .w (largest far radius) is written by another thread in the loop below,
+                // before the next barrier: leave it alone here
+                sMi[tid].x = (int)((int64_t)na - kw);
+                sMi[tid].y = (int)kaw;
+                sMi[tid].z = (int)kbw;
                 sMf[tid].x = p.f_frac[l];
             }
 #pragma unroll 1
@@ -554,17 +600,69 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     store_consts<PROF>(smem, i * CG + c, A, S);
                     if (Lay::kHasB) sB[i * CG + c] = B;
                 }
+                // the largest far radius over the group's real conditions (Voigt w4)
+                float dm = (PROF == XC_VOIGT_W4 && v && cc < p.n_cond) ? sfar_radius(smem, i * CG + c) : -1.f;
                 if (CG > 1) {
 #pragma unroll
-                    for (int o = CG / 2; o > 0; o >>= 1) t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
+                    for (int o = CG / 2; o > 0; o >>= 1) {
+                        t2 = fmaxf(t2, __shfl_xor_sync(0xffffffffu, t2, o));
+                        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                    }
                 }
-                if (v && c == 0) sMf[i].y = t2;
+                if (v && c == 0) {
+                    sMf[i].y = t2;
+                    sMi[i].w = (int)fminf(dm, 1.0e9f);
+                }
             }
             __syncthreads();
 
             // ---- evaluate: classify lines for this warp's span, then accumulate
             for (int ib = 0; ib < cnt; ib += 32) {
                 int i = ib + lane;
+                if (PROF == XC_VOIGT_W4 && p.tc_far) {
+                    // the far-wing kernel took every (line, condition) with span_far on this
+                    // 128-point span; the rest, region I only, as masked single lines
+                    bool nr = false;
+                    if (i < cnt) {
+                        const int4 mi = sMi[i];
+                        const bool none = (mi.z < span0) || (mi.y > span1) || (mi.y > mi.z);
+                        nr = !none && !span_far(mi.x, (float)mi.w, span0, span1);
+                    }
+                    unsigned nm = __ballot_sync(0xffffffffu, nr);
+                    while (nm) {
+                        const int i1 = ib + __ffs(nm) - 1;
+                        nm &= nm - 1;
+                        const int4 m1 = sMi[i1];
+                        const float f1 = sMf[i1].x, n1 = (float)m1.x;
+                        float d1[R], u1[R];
+                        bool in1[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            d1[r] = (jf[r] - n1) - f1;
+                            u1[r] = d1[r] * d1[r];
+                            in1[r] = (ji[r] >= m1.y) && (ji[r] <= m1.z);
+                        }
+                        bool fl = false;
+                        if (lane < CG) fl = span_far(m1.x, sfar_radius(smem, i1 * CG + lane), span0, span1);
+                        const unsigned tcm = __ballot_sync(0xffffffffu, fl);
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            if ((tcm >> c) & 1u) continue;
+                            const float4 A1 = load_consts<PROF>(smem, i1 * CG + c);
+                            const float4 B1 = sB[i1 * CG + c];
+#pragma unroll
+                            for (int q = 0; q < R / 2; ++q) {
+                                float a0, a1;
+                                upk2(acc[q][c], a0, a1);
+                                if (in1[2 * q]) a0 += contrib_single<PROF>(u1[2 * q], d1[2 * q], A1, B1, sX, sW, p.ngh);
+                                if (in1[2 * q + 1])
+                                    a1 += contrib_single<PROF>(u1[2 * q + 1], d1[2 * q + 1], A1, B1, sX, sW, p.ngh);
+                                acc[q][c] = pk2(a0, a1);
+                            }
+                        }
+                    }
+                    continue;
+                }
                 bool fast = false, slow = false;
                 if (i < cnt) {
                     int4 mi = sMi[i];
@@ -610,14 +708,11 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                         // both lines (u >= u_far): series in r = 1/u, with r shared by them all
                         unsigned far = 0;
                         {
-                            const float c1 = n1 + f1, c2 = n2 + f2;
-                            const float dm1 = fmaxf(fmaxf((float)span0 - c1, c1 - (float)span1), 0.f);
-                            const float dm2 = fmaxf(fmaxf((float)span0 - c2, c2 - (float)span1), 0.f);
                             bool fl = false;
                             if (lane < CG) {
-                                const float uf1 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i1 * CG + lane))[2].w;
-                                const float uf2 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i2 * CG + lane))[2].w;
-                                fl = (dm1 * dm1 >= uf1) && (dm2 * dm2 >= uf2);
+                                const float D1 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i1 * CG + lane))[2].w;
+                                const float D2 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i2 * CG + lane))[2].w;
+                                fl = span_far(m1.x, D1, span0, span1) && span_far(m2.x, D2, span0, span1);
                             }
                             far = __ballot_sync(0xffffffffu, fl);
                         }
@@ -629,21 +724,19 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                                 rb[q] = rcp2(ub[q]);
                             }
                         }
+                        if (far == kAllConds) {  // the common case: no per-condition branch
+#pragma unroll
+                            for (int c = 0; c < CG; ++c)
+                                w4_series_pair<R, CG>(acc, c, smem + (size_t)48 * (i1 * CG + c),
+                                                      smem + (size_t)48 * (i2 * CG + c), ra, rb);
+                            continue;
+                        }
 #pragma unroll
                         for (int c = 0; c < CG; ++c) {
                             const unsigned char *e1 = smem + (size_t)48 * (i1 * CG + c);
                             const unsigned char *e2 = smem + (size_t)48 * (i2 * CG + c);
                             if ((far >> c) & 1u) {
-                                const float4 s1 = reinterpret_cast<const float4 *>(e1)[2];
-                                const float4 s2 = reinterpret_cast<const float4 *>(e2)[2];
-                                const f32x2 p01 = pk2(s1.x, s1.x), p11 = pk2(s1.y, s1.y), p21 = pk2(s1.z, s1.z);
-                                const f32x2 p02 = pk2(s2.x, s2.x), p12 = pk2(s2.y, s2.y), p22 = pk2(s2.z, s2.z);
-#pragma unroll
-                                for (int q = 0; q < R / 2; ++q) {
-                                    f32x2 t1 = fma2(fma2(p21, ra[q], p11), ra[q], p01);
-                                    f32x2 t2 = fma2(fma2(p22, rb[q], p12), rb[q], p02);
-                                    acc[q][c] = fma2(t2, rb[q], fma2(t1, ra[q], acc[q][c]));
-                                }
+                                w4_series_pair<R, CG>(acc, c, e1, e2, ra, rb);
                                 continue;
                             }
                             const ulonglong2 a0 = reinterpret_cast<const ulonglong2 *>(e1)[0];
@@ -735,8 +828,36 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                         u1[r] = d1[r] * d1[r];
                         in1[r] = (ji[r] >= m1.y) && (ji[r] <= m1.z);
                     }
+                    // Voigt w4: far-wing series where the whole span is far for a condition
+                    // (typically the spans holding a cut edge)
+                    unsigned far = 0;
+                    float rr[R];
+                    if (PROF == XC_VOIGT_W4) {
+                        bool fl = false;
+                        if (lane < CG)
+                            fl = span_far(m1.x, reinterpret_cast<const float4 *>(smem + (size_t)48 * (i1 * CG + lane))[2].w,
+                                          span0, span1);
+                        far = __ballot_sync(0xffffffffu, fl);
+                        if (far) {
+#pragma unroll
+                            for (int r = 0; r < R; ++r) rr[r] = in1[r] ? rcp_approx(u1[r]) : 0.f;
+                        }
+                    }
 #pragma unroll
                     for (int c = 0; c < CG; ++c) {
+                        if (PROF == XC_VOIGT_W4 && ((far >> c) & 1u)) {
+                            const float4 s1 = reinterpret_cast<const float4 *>(smem + (size_t)48 * (i1 * CG + c))[2];
+#pragma unroll
+                            for (int q = 0; q < R / 2; ++q) {
+                                float a0, a1;
+                                upk2(acc[q][c], a0, a1);
+                                const float r0 = rr[2 * q], r1 = rr[2 * q + 1];
+                                a0 = fmaf(fmaf(fmaf(s1.z, r0, s1.y), r0, s1.x), r0, a0);
+                                a1 = fmaf(fmaf(fmaf(s1.z, r1, s1.y), r1, s1.x), r1, a1);
+                                acc[q][c] = pk2(a0, a1);
+                            }
+                            continue;
+                        }
                         const float4 A1 = load_consts<PROF>(smem, i1 * CG + c);
                         const float4 B1 = Lay::kHasB ? sB[i1 * CG + c] : make_float4(0.f, 0.f, 0.f, -1.f);
 #pragma unroll
@@ -752,13 +873,242 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 }
             }
             if (++chunk == FOLD_CHUNKS) {
-                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold);
+                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold && !p.tc_far);
                 first_fold = false;
                 chunk = 0;
             }
         }
-        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold);
+        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold && !p.tc_far);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Far-wing kernel on the tensor cores (Voigt w4, FP32, fixed cut, many conditions).
+//
+// For a block of 128 grid points and a line l far from all of them (integer
+// radius D(l, c), see line_consts), the region-I rational of condition c equals
+// its series r (p0 + p1 r + p2 r^2), r = 1/u, to < 2e-7.  Summed over lines,
+//   F[k, c] = sum_l sum_j r_kl^(j+1) p_j(l, c)
+// is a matrix product: A[k, (j, l)] = r_kl^(j+1) depends on the point and the
+// line only, B[(j, l), c] = p_j(l, c) on the line and the condition only.  Each
+// CTA owns one block of TC_T = 128 points (one TMEM lane each) and 32 conditions
+// (the MMA's N), walks the lines whose cut reaches the block in chunks of TC_L,
+// and per chunk: computes B in shared memory (zero where (l, c) is not far from
+// the block: the CUDA-core kernel evaluates those), writes A to tensor memory,
+// and issues tcgen05.mma kind::tf32 with M = 128, N = 32, K = 8.  FP32 inputs
+// are split x = hi + lo with hi exact in TF32, and D += Ahi Bhi + Ahi Blo +
+// Alo Bhi (the dropped Alo Blo is < 2^-21 of the product).  A and B are double
+// buffered (the next chunk is built while the MMAs of this one run).  The tensor
+// core adds in FP32 with truncation, a bias that grows with the number of MMAs
+// summed into one accumulator, so D (FP32 in TMEM) is restarted every TC_FOLD
+// chunks after its value is added into compensated (Kahan) FP32 sums in shared
+// memory; the block is written (not added) to the output at the end.
+// ---------------------------------------------------------------------------
+constexpr int TC_T = 128;                 // threads = points per block = MMA M
+constexpr int TC_N = 32;                  // conditions per tile = MMA N
+constexpr int TC_L = 8;                   // lines per chunk
+constexpr int TC_J = 3;                   // series terms
+constexpr int TC_K = TC_L * TC_J;         // K elements per chunk (3 MMA K-steps of 8)
+constexpr int TC_FOLD = 8;                // chunks per tensor-memory accumulation period (64 lines)
+constexpr uint32_t TC_COLS = 128;         // TMEM columns: D 32 + 2 buffers x (24 hi + 24 lo)
+constexpr int TC_BFLOATS = TC_N * TC_K;   // one B operand (hi or lo): 768 floats
+constexpr size_t TC_SMEM_B = (size_t)4 * TC_BFLOATS * sizeof(float);   // 2 buffers x (hi, lo)
+constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);   // compensated FP32 sums
+constexpr size_t TC_SMEM = 50 * 1024;     // B + FP64 sums + barriers; sized so that 4 CTAs (4 x 128 TMEM
+                                          // columns) and never 5 share an SM
+static_assert(TC_SMEM_B + TC_SMEM_ACC + 64 <= TC_SMEM, "far-wing kernel shared memory");
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+
+struct TcParams {
+    LinesDev L;
+    const int *n_abs;
+    const float *f_frac;
+    const int *ka_abs, *kb_abs;
+    const CParam *cp;
+    const unsigned *blk_lo, *blk_hi;   // per 128-point block: line range
+    int *counter;
+    int *status;                       // set to 1 if a wait ran out
+    int n_tiles, n_groups, n_cond;
+    int64_t n_pts;
+    float h, inv_h;
+    double *sigma;
+};
+
+// B element (n, k) of a K-major operand with 8 x 16-byte core matrices:
+// core (n / 8, k / 4) at ((n / 8) * (TC_K / 4) + k / 4) * 128 bytes
+__device__ __forceinline__ int tc_b_index(int n, int k) {
+    return (((n >> 3) * (TC_K / 4) + (k >> 2)) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
+}
+
+__global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sB = reinterpret_cast<float *>(smem);                           // [buf][hi, lo][768]
+    float *sSum = reinterpret_cast<float *>(smem + TC_SMEM_B);             // [c][point]
+    float *sCmp = sSum + TC_N * TC_T;                                       // Kahan compensation
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_SMEM_B + TC_SMEM_ACC);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(mbar + 2);
+    int *sTile = reinterpret_cast<int *>(sTmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(sTmem, TC_COLS);
+    for (int c = 0; c < TC_N; ++c) sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *sTmem;
+    const uint32_t t_lane = tbase + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+    constexpr uint32_t kIdesc = tc::idesc_tf32(128, TC_N);
+    const uint32_t sB_addr = tc::smem_u32(sB);
+
+    uint32_t uses[2] = {0u, 0u};   // commits per barrier so far (uniform over the CTA)
+    bool ok = true;
+    // the (line, condition) pair this thread turns into B entries: line tid / 16, conditions tid % 16 (+16)
+    const int lB = tid >> 4, cB = tid & 15;
+
+    for (;;) {
+        if (tid == 0) *sTile = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int t = *sTile;
+        __syncthreads();
+        if (t >= p.n_tiles) break;
+        const int blk = t / p.n_groups, grp = t % p.n_groups;
+        const int t0 = blk * TC_T, t1 = t0 + TC_T - 1;
+        const int k = t0 + tid;
+        const unsigned lo = p.blk_lo[blk], hi = p.blk_hi[blk];
+        const unsigned nl = hi - lo;
+        const int nch = (int)((nl + TC_L - 1) / TC_L);
+        CParam cpr[2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int cc = grp * TC_N + cB + 16 * h2;
+            if (cc < p.n_cond) cpr[h2] = p.cp[cc];
+        }
+        int in_fold = 0;
+        for (int ci = 0; ci < nch; ++ci) {
+            const int b = ci & 1;
+            // buffer b is free once the MMAs of its previous chunk have completed
+            if (uses[b] > 0u) {
+                ok &= tc::mbar_wait(&mbar[b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
+                tc::fence_after_sync();
+            }
+            const unsigned base = lo + (unsigned)ci * TC_L;
+            // ---- B: series coefficients of the far (line, condition) pairs, split hi + lo
+            {
+                float *bh = sB + (size_t)b * 2 * TC_BFLOATS, *bl = bh + TC_BFLOATS;
+                const unsigned li = base + lB;
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int c = cB + 16 * h2, cc = grp * TC_N + c;
+                    float v[TC_J] = {0.f, 0.f, 0.f};
+                    if (li < hi && cc < p.n_cond) {
+                        float4 A, B, S;
+                        float t2;
+                        line_consts<XC_VOIGT_W4>(p.L, li, cpr[h2], p.h, p.inv_h, &A, &B, &t2, &S);
+                        const int na = p.n_abs[li];
+                        if (p.kb_abs[li] >= p.ka_abs[li] && span_far(na, S.w, t0, t1)) {
+                            v[0] = S.x;
+                            v[1] = S.y;
+                            v[2] = S.z;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < TC_J; ++j) {
+                        const float vh = tc::tf32_hi(v[j]);
+                        const int ix = tc_b_index(c, j * TC_L + lB);
+                        bh[ix] = vh;
+                        bl[ix] = v[j] - vh;
+                    }
+                }
+            }
+            // ---- A: r^(j+1) of this thread's point for the chunk's lines, split hi + lo
+            {
+                float av[2 * TC_K];
+#pragma unroll
+                for (int l8 = 0; l8 < TC_L; ++l8) {
+                    const unsigned li = base + l8;
+                    float r = 0.f;
+                    if (li < hi) {
+                        const int na = p.n_abs[li], ka = p.ka_abs[li], kb = p.kb_abs[li];
+                        const float d = (float)(k - na) - p.f_frac[li];
+                        // inside the cut; points within one step of the centre only ever meet
+                        // zero B entries (not far), r is kept finite there
+                        if (k >= ka && k <= kb) r = rcp_approx(fmaxf(d * d, 1.f));
+                    }
+                    float pw = r;
+#pragma unroll
+                    for (int j = 0; j < TC_J; ++j) {
+                        const float vh = tc::tf32_hi(pw);
+                        av[j * TC_L + l8] = vh;
+                        av[TC_K + j * TC_L + l8] = pw - vh;
+                        pw *= r;
+                    }
+                }
+                const uint32_t ta = t_lane + 32u + (uint32_t)b * (2u * TC_K);
+                float v16[16];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v16[i] = av[16 * q + i];
+                    tc::tmem_st16(ta + 16u * q, v16);
+                }
+                tc::tmem_st_wait();
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t a_hi = tbase + 32u + (uint32_t)b * (2u * TC_K), a_lo = a_hi + TC_K;
+                const uint32_t bh_addr = sB_addr + (uint32_t)(b * 2 * TC_BFLOATS * 4);
+                const uint32_t bl_addr = bh_addr + (uint32_t)(TC_BFLOATS * 4);
+#pragma unroll
+                for (int s = 0; s < TC_K / 8; ++s) {
+                    // K-step s: two core matrices along K (256 bytes), LBO 128, SBO 6 x 128
+                    const uint64_t dh = tc::smem_desc(bh_addr + 256u * s, 128u, 128u * (TC_K / 4));
+                    const uint64_t dl = tc::smem_desc(bl_addr + 256u * s, 128u, 128u * (TC_K / 4));
+                    tc::mma_tf32_ts(tbase, a_hi + 8u * s, dh, kIdesc, (in_fold > 0 || s > 0) ? 1u : 0u);
+                    tc::mma_tf32_ts(tbase, a_hi + 8u * s, dl, kIdesc, 1u);
+                    tc::mma_tf32_ts(tbase, a_lo + 8u * s, dh, kIdesc, 1u);
+                }
+                tc::mma_commit(&mbar[b]);
+            }
+            ++uses[b];
+            if (++in_fold == TC_FOLD || ci == nch - 1) {
+                // tensor-memory sums -> compensated FP32 sums (each thread owns its point's row)
+                ok &= tc::mbar_wait(&mbar[b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
+                tc::fence_after_sync();
+                float v[32];
+                tc::tmem_ld32(t_lane, v);
+#pragma unroll
+                for (int c = 0; c < TC_N; ++c) {
+                    const float sm = sSum[c * TC_T + tid];
+                    const float y = __fsub_rn(v[c], sCmp[c * TC_T + tid]);
+                    const float tt = __fadd_rn(sm, y);
+                    sCmp[c * TC_T + tid] = __fsub_rn(__fsub_rn(tt, sm), y);
+                    sSum[c * TC_T + tid] = tt;
+                }
+                tc::fence_before_sync();
+                in_fold = 0;
+            }
+        }
+        // ---- the block's far-wing sums: first writer of these outputs
+        for (int c = 0; c < TC_N; ++c) {
+            const int cc = grp * TC_N + c;
+            if ((int64_t)k < p.n_pts && cc < p.n_cond)
+                p.sigma[(size_t)cc * (size_t)p.n_pts + (size_t)k] =
+                    ((double)sSum[c * TC_T + tid] - (double)sCmp[c * TC_T + tid]) * p.cp[cc].inv_scale;
+            sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, TC_COLS);
+    if (!ok) atomicExch(p.status, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -983,11 +1333,17 @@ struct Plan {
     float *gx = nullptr, *gw = nullptr;
     int n_win_core = 0;                         // centre-zone kernel windows (Voigt w4)
     unsigned *core_lo = nullptr, *core_hi = nullptr;
+    bool tc = false;                            // far wings on the tensor cores (Voigt w4)
+    int n_blk = 0, n_tc_tiles = 0;              // 128-point blocks, (block, 32-condition group) tiles
+    unsigned *blk_lo = nullptr, *blk_hi = nullptr;
+    int *tc_counter = nullptr, *tc_status = nullptr;
 };
 
-xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl) {
+xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl,
+                    bool tc) {
     const size_t n = a.n_lines;
     pl->v = v;
+    pl->tc = tc;
     pl->W = GT * v->R;
     pl->n_win = (int)((a.grid.n + pl->W - 1) / pl->W);
     pl->n_groups = (n_cond_call + v->CG - 1) / v->CG;
@@ -1000,6 +1356,14 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
     pl->n_win_core = (int)((a.grid.n + CORE_T - 1) / CORE_T);
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
+    size_t o_blo = 0, o_bhi = 0, o_tcc = 0;
+    if (tc) {
+        pl->n_blk = (int)((a.grid.n + TC_T - 1) / TC_T);
+        pl->n_tc_tiles = pl->n_blk * ((n_cond_call + TC_N - 1) / TC_N);
+        o_blo = carve((size_t)pl->n_blk * 4);
+        o_bhi = carve((size_t)pl->n_blk * 4);
+        o_tcc = carve(64);
+    }
     BT_TRY(st->tiles.ensure(off));
     char *b = st->tiles.as<char>();
     pl->n_abs = (int *)(b + o_n);
@@ -1016,8 +1380,17 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     pl->gw = pl->gx + 64;
     pl->core_lo = (unsigned *)(b + o_clo);
     pl->core_hi = (unsigned *)(b + o_chi);
+    if (tc) {
+        pl->blk_lo = (unsigned *)(b + o_blo);
+        pl->blk_hi = (unsigned *)(b + o_bhi);
+        pl->tc_counter = (int *)(b + o_tcc);
+        pl->tc_status = pl->tc_counter + 1;
+        st->tc_status = pl->tc_status;
+    }
     return XC_OK;
 }
+
+int tc_grid_size(int n_tiles);
 
 // enqueue the whole sweep for conditions [c0, c0 + nc) on the stream
 xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid, int max_lines, int64_t *launches,
@@ -1064,9 +1437,36 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     gp.ghx = pl.gx;
     gp.ghw = pl.gw;
     gp.ngh = a.opts.n_gh;
+    gp.tc_far = pl.tc ? 1 : 0;
     gp.sigma = a.sigma + (size_t)c0 * (size_t)a.grid.n;
     const bool ev = a.timing && a.ev_main0 && max_lines == 0;
     if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main0, s, cudaEventRecordExternal));
+    if (pl.tc && max_lines == 0) {
+        // far wings on the tensor cores: first writer of every output of the sweep
+        k_win_ranges32<<<(pl.n_blk + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
+                                                              TC_T, a.opts.cutoff, pl.n_blk, pl.blk_lo, pl.blk_hi);
+        BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 2 * sizeof(int), s));
+        TcParams tp;
+        tp.L = a.L;
+        tp.n_abs = pl.n_abs;
+        tp.f_frac = pl.f;
+        tp.ka_abs = pl.ka;
+        tp.kb_abs = pl.kb;
+        tp.cp = pl.cp;
+        tp.blk_lo = pl.blk_lo;
+        tp.blk_hi = pl.blk_hi;
+        tp.counter = pl.tc_counter;
+        tp.status = pl.tc_status;
+        tp.n_tiles = pl.n_tc_tiles;
+        tp.n_groups = (nc + TC_N - 1) / TC_N;
+        tp.n_cond = nc;
+        tp.n_pts = a.grid.n;
+        tp.h = gp.h;
+        tp.inv_h = gp.inv_h;
+        tp.sigma = gp.sigma;
+        k_far_tc<<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
+        *launches += 2;
+    }
     pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
     if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main1, s, cudaEventRecordExternal));
     *launches += 1;
@@ -1102,11 +1502,13 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     return XC_OK;
 }
 
+bool use_tc(const BatchedArgs &a, int nc);
+
 std::string shape_key(const BatchedArgs &a, int nc) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "p%d n%zu c%d g%lld/%.17g/%.17g cut%.17g wm%.17g gh%d", a.opts.profile,
+    snprintf(buf, sizeof(buf), "p%d n%zu c%d g%lld/%.17g/%.17g cut%.17g wm%.17g gh%d f%d tc%d", a.opts.profile,
              a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff, a.opts.width_mult,
-             a.opts.n_gh);
+             a.opts.n_gh, a.opts.flags, use_tc(a, nc) ? 1 : 0);
     return buf;
 }
 
@@ -1118,6 +1520,40 @@ xc_status configure_variant(const Variant *v, int dev) {
     done[idx] = true;
     (void)dev;
     return XC_OK;
+}
+
+static int g_tc_per_sm = -1;
+static char g_tc_diag[160] = "";
+
+int tc_grid_size(int n_tiles) {
+    if (g_tc_per_sm < 0) {
+        int ps = 0;
+        cudaError_t e1 = cudaFuncSetAttribute((const void *)k_far_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)TC_SMEM);
+        cudaError_t e2 = e1 == cudaSuccess
+                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, (const void *)k_far_tc, TC_T, TC_SMEM)
+                             : e1;
+        // The occupancy query answers 1 for this kernel (it does not model tensor-memory
+        // allocation); residency is bounded by shared memory (TC_SMEM admits 4 CTAs), by
+        // registers, and by the 512 TMEM columns of an SM (4 x 128).  Extra CTAs would
+        // only wait: the work queue is shared.
+        cudaFuncAttributes fa;
+        int dev0 = 0, smem_sm = 0;
+        cudaGetDevice(&dev0);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev0);
+        int by_regs = 4, by_smem = 4;
+        if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc) == cudaSuccess && fa.numRegs > 0)
+            by_regs = 65536 / (fa.numRegs * TC_T);
+        if (smem_sm > 0) by_smem = smem_sm / (int)(TC_SMEM + 1024);
+        const int mine = std::max(1, std::min(4, std::min(by_regs, by_smem)));
+        snprintf(g_tc_diag, sizeof(g_tc_diag), "query %d (%s), registers %d, shared memory %d", ps,
+                 cudaGetErrorString(e2), by_regs, by_smem);
+        cudaGetLastError();
+        g_tc_per_sm = mine;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return std::max(1, std::min(num_sms(dev) * g_tc_per_sm, n_tiles));
 }
 
 int grid_size(const Variant *v, int dev, int n_tiles) {
@@ -1134,8 +1570,27 @@ int grid_size(const Variant *v, int dev, int n_tiles) {
 // Autotune: time each candidate variant on a probe (every tile, first 4096 lines)
 // and predict the full run from the measured time per (tile line x condition);
 // the prediction includes the wave quantisation of the tile count.
-xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out, int64_t *launches) {
+// far wings of the Voigt w4 sweep on the tensor cores: many conditions (the MMA's N is
+// 32, so a handful of conditions would waste it), one fixed cut, grids of < 2^30 points
+bool use_tc(const BatchedArgs &a, int nc) {
+    return a.allow_tc && a.opts.profile == XC_VOIGT_W4 && a.opts.width_mult <= 0.0 && nc >= 16 &&
+           !(a.opts.flags & XC_OPT_NO_TENSOR_CORES) && a.grid.n < ((int64_t)1 << 30);
+}
+
+std::string tuned_key(const BatchedState *st, const BatchedArgs &a, int nc) {
     std::string key = shape_key(a, nc);
+    if (st->force_R > 0) {
+        char fb[48];
+        snprintf(fb, sizeof(fb), " fixed R%d CG%d", st->force_R, st->force_CG);
+        key += fb;
+    }
+    return key;
+}
+
+xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out, int64_t *launches) {
+    const std::string key = tuned_key(st, a, nc);
+    const bool tc = use_tc(a, nc);
+    if (tc) tc_grid_size(1);   // kernel attributes set outside any graph capture
     auto it = st->tuned.find(key);
     if (it != st->tuned.end()) {
         *out = it->second;
@@ -1148,10 +1603,12 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
         const Variant &v = kVariants[i];
         if (v.profile != a.opts.profile) continue;
         if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
-        if (a.opts.width_mult <= 0.0) {
+        if (a.opts.width_mult <= 0.0 && st->force_R == 0) {
             if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
             if (v.CG < std::min(nc, 8)) continue;              // enough conditions share each staged line
         }
+        if (tc && v.R != 4) continue;  // spans of 128 points = the far-wing kernel's blocks
+        if (st->force_R > 0 && (v.R != st->force_R || v.CG != st->force_CG)) continue;
         cands.push_back(i);
     }
     if (cands.empty()) {
@@ -1174,7 +1631,7 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
             if (s) return s;
             Plan pl;
             int ncv = a.opts.width_mult > 0.0 ? 1 : nc;
-            if ((s = make_plan(st, a, v, ncv, &pl))) return s;
+            if ((s = make_plan(st, a, v, ncv, &pl, tc))) return s;
             int grid = grid_size(v, dev, pl.n_tiles);
             const int probe_lines = 4096;
             if ((s = enqueue(a, pl, 0, ncv, grid, probe_lines, launches, a.opts.width_mult > 0.0))) return s;
@@ -1232,6 +1689,9 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
         set_error("the FP32 path needs fewer than 2^31 grid points");
         return XC_EINVAL;
     }
+    // the status word lives in the plan's scratch, which a later plan may reallocate:
+    // it is valid only for the run that set it
+    st->tc_status = nullptr;
     if (a.n_lines == 0 || a.n_cond == 0 || a.grid.n == 0) return XC_OK;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1242,8 +1702,12 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     if ((s = configure_variant(v, dev))) return s;
     {
         char lb[256];
-        snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points; ", v->profile, v->R, v->CG, GT * v->R);
-        st->last_tuning = std::string(lb) + st->tune_log[shape_key(a, a.n_cond)];
+        if (use_tc(a, a.n_cond))
+            snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points, far wings on tensor cores (%d CTAs/SM%s%s); ",
+                     v->profile, v->R, v->CG, GT * v->R, g_tc_per_sm, g_tc_diag[0] ? ", " : "", g_tc_diag);
+        else
+            snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points; ", v->profile, v->R, v->CG, GT * v->R);
+        st->last_tuning = std::string(lb) + st->tune_log[tuned_key(st, a, a.n_cond)];
     }
     const bool per_cond = a.opts.width_mult > 0.0;
     if (per_cond) {
@@ -1251,14 +1715,14 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
         if (a.timing) cudaEventRecord(a.ev_begin, a.stream);
         for (int c = 0; c < a.n_cond; ++c) {
             Plan pl;
-            if ((s = make_plan(st, a, v, 1, &pl))) return s;
+            if ((s = make_plan(st, a, v, 1, &pl, false))) return s;
             if ((s = enqueue(a, pl, c, 1, grid_size(v, dev, pl.n_tiles), 0, launches, true))) return s;
         }
         if (a.timing) cudaEventRecord(a.ev_end, a.stream);
         return XC_OK;
     }
     Plan pl;
-    if ((s = make_plan(st, a, v, a.n_cond, &pl))) return s;
+    if ((s = make_plan(st, a, v, a.n_cond, &pl, use_tc(a, a.n_cond)))) return s;
     const int grid = grid_size(v, dev, pl.n_tiles);
     // graph cache: the sweep (geometry, constants, ranges, tile ranking, counter
     // reset, persistent kernel) is captured once per shape and buffer set, then replayed
@@ -1292,6 +1756,20 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     BT_TRY(cudaGraphLaunch(it->second.exec, a.stream));
     if (a.timing) cudaEventRecord(a.ev_end, a.stream);
     *launches += a.ghx ? 6 : 5;
+    return XC_OK;
+}
+
+xc_status batched_check(BatchedState *st) {
+    if (!st->tc_status) return XC_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, st->tc_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("reading the tensor-core kernel status failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return XC_ECUDA;
+    }
+    if (v) {
+        set_error("tensor-core far-wing kernel: an MMA completion wait ran out; results are not valid");
+        return XC_ETIMEOUT;
+    }
     return XC_OK;
 }
 

@@ -25,6 +25,7 @@ struct BatchedArgs {
     // kernel, after it, and after the centre-zone kernel
     cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr, ev_core1 = nullptr;
     const double *ghx = nullptr, *ghw = nullptr;  // device Gauss-Hermite nodes/weights
+    bool allow_tc = true;                   // far wings may use the tensor-core kernel
 };
 
 struct VjpArgs {
@@ -68,10 +69,15 @@ struct BatchedState {
     std::map<std::string, GraphEntry> graphs;   // graph cache: shape key + pointers -> graph
     std::map<std::string, std::string> tune_log; // shape key -> candidate predictions
     std::string last_tuning;                     // description of the last batched configuration
+    int *tc_status = nullptr;                    // device word: a tensor-core wait ran out
+    int force_R = 0, force_CG = 0;               // fixed CUDA-core tile shape (0: autotune)
 };
 
 xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches);
 xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches);
+// after the stream has synchronised: XC_ETIMEOUT if the tensor-core kernel reported a
+// wait that ran out (its results are then not valid), else XC_OK
+xc_status batched_check(BatchedState *st);
 void batched_invalidate(BatchedState *st);
 void batched_release(BatchedState *st);
 

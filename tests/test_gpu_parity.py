@@ -198,6 +198,79 @@ def test_batched_conditions(eng, xc, oracle_lib, precision):
     assert worst[0] < tol[0] and worst[1] < tol[1]
 
 
+@pytest.mark.parametrize("n_cond", [16, 20, 33])
+def test_batched_tensor_core_far_wings(eng, xc, oracle_lib, n_cond):
+    """FP32 Voigt w4 with >= 16 conditions sums the far wings on the tensor cores
+    (ragged last 128-point block, padded condition groups); the result must match
+    the oracle like the CUDA-core path does, and the two FP32 paths each other."""
+    L = xs.gen_lines(110, 0, 20000, 0.0, 200.0)
+    E, g = xs.gen_states(110, 5000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    W = xs.WORKLOADS["C3"]
+    base = xs.conditions_for(W)
+    conds = [base[i % 32] for i in range(n_cond)]
+    cx = [xc.make_condition(c["T"], c["P"]) for c in conds]
+    nu_A, step, n = 0.0, 0.01, 20001
+    grid = xc.make_grid(nu_A, step, n)
+    tc = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 25.0))
+    cu = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 25.0, tensor_cores=False))
+    worst = (0.0, 0.0)
+    worst_cu = 0.0
+    for i in range(n_cond):
+        ref = oracle_sigma(oracle_lib, L, E, g, conds[i]["T"], conds[i]["P"], nu_A, step, n, "voigt_w4", 25.0)
+        mr, band = metrics(tc[i], ref)
+        mr2, _ = metrics(cu[i], ref)
+        if max(mr, mr2) > 2e-5:
+            print(f"  condition {i}: tensor-core path {mr:.3g}, CUDA-core path {mr2:.3g}")
+        worst = (max(worst[0], mr), max(worst[1], band))
+        worst_cu = max(worst_cu, mr2)
+    print(f"  CUDA-core path, all conditions: {worst_cu:.3g}; tuning: {eng.tuning()}")
+    m = cu > 1e-6 * cu.max(axis=1, keepdims=True)
+    rel = (tc[m] - cu[m]) / cu[m]
+    diff = float(np.max(np.abs(rel)))
+    full = np.where(m, np.abs(tc - cu) / np.where(m, cu, 1.0), 0.0)
+    ci, ki = np.unravel_index(np.argmax(full), full.shape)
+    print(f"  largest tensor/CUDA-core difference at condition {ci}, point {ki} (block {ki // 128}, "
+          f"offset {ki % 128}): {tc[ci, ki]:.6g} vs {cu[ci, ki]:.6g}")
+    print(f"tensor-core far wings, {n_cond} conditions: vs oracle {worst[0]:.3g} band {worst[1]:.3g}; "
+          f"vs CUDA-core path max {diff:.3g}, mean {float(np.mean(rel)):.3g}")
+    assert worst[0] < TOL32 and worst[1] < TOL32_BAND
+    assert diff < 2e-5
+    assert np.all(tc >= 0)
+
+
+W4_SHAPES = [(4, 16), (2, 32), (4, 8), (8, 8), (8, 4), (8, 2), (8, 1)]
+
+
+def test_every_w4_tile_shape(eng, xc, oracle_lib):
+    """Every compiled FP32 Voigt w4 tile shape, 33 conditions (padded groups), on the
+    CUDA cores and, for the 128-point spans (R = 4), with the tensor-core far wings."""
+    L = xs.gen_lines(111, 0, 12000, 0.0, 120.0)
+    E, g = xs.gen_states(111, 3000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    base = xs.conditions_for(xs.WORKLOADS["C3"])
+    conds = [base[i % 32] for i in range(33)]
+    cx = [xc.make_condition(c["T"], c["P"]) for c in conds]
+    nu_A, step, n = 0.0, 0.01, 12001
+    grid = xc.make_grid(nu_A, step, n)
+    refs = [oracle_sigma(oracle_lib, L, E, g, c["T"], c["P"], nu_A, step, n, "voigt_w4", 25.0) for c in conds]
+    bad = []
+    try:
+        for R, CG in W4_SHAPES:
+            for tcores in ((False, True) if R == 4 else (False,)):
+                eng.set_tile_shape(R, CG)
+                got = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 25.0, tensor_cores=tcores))
+                w = max(metrics(got[i], refs[i]) for i in range(33))
+                print(f"R={R} CG={CG} tensor cores {tcores}: max rel {w[0]:.3g}, band {w[1]:.3g}")
+                if not (w[0] < TOL32 and w[1] < TOL32_BAND):
+                    bad.append((R, CG, tcores, w))
+    finally:
+        eng.set_tile_shape(0, 0)
+    assert not bad, bad
+
+
 @pytest.mark.parametrize("profile", ["voigt_w4", "voigt_gh_binned"])
 def test_width_limited_cut(eng, xc, oracle_lib, profile):
     L = xs.gen_lines(108, 0, 10000, 0.0, 100.0)
