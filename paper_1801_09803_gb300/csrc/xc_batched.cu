@@ -59,7 +59,8 @@ struct CParam {
     float log2Tr;       // log2(T_ref / T)
     float pscale;       // gamma_scale * P / P_ref
     float nshift;
-    float pad[2];
+    int row;            // output row (the caller's condition index)
+    float pad;
 };
 
 struct GeomStats {
@@ -146,10 +147,26 @@ __device__ __forceinline__ float exp2_neg(float z) {
 // ---------------------------------------------------------------------------
 // per-condition constants
 // ---------------------------------------------------------------------------
+// width of a condition's profiles at a representative line (nu = 5000 cm^-1, n = 0.6):
+// C = alpha^2 / (2 ln 2) + gamma^2, the scale of the far-wing radius
+__device__ double cond_width_key(const CondDev &d) {
+    const double al = alpha_coef(d.T, d.mass_da) * 5000.0;
+    const double ga = d.gamma_scale * (d.P / d.P_ref) * pow(d.T_ref / d.T, 0.6 + d.n_shift);
+    return al * al * (0.5 / 0.6931471805599453) + ga * ga;
+}
+
+// Per-condition constants, stored in order of increasing profile width (stable), so that
+// the conditions sharing a tile have similar far-wing radii; row keeps the caller's index.
 __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cond) return;
     const CondDev d = conds[c];
+    const double key = cond_width_key(d);
+    int rank = 0;
+    for (int j = 0; j < n_cond; ++j) {
+        const double kj = cond_width_key(conds[j]);
+        rank += (kj < key) || (kj == key && j < c);
+    }
     const double log2e = 1.4426950408889634;
     double kT = kC2 * log2e / d.T;
     float hi = (float)kT;
@@ -174,8 +191,9 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
     p.log2Tr = (float)log2(d.T_ref / d.T);
     p.pscale = (float)(d.gamma_scale * d.P / d.P_ref);
     p.nshift = (float)d.n_shift;
-    p.pad[0] = p.pad[1] = 0.f;
-    cp[c] = p;
+    p.row = c;
+    p.pad = 0.f;
+    cp[rank] = p;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,7 +202,7 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
 // ---------------------------------------------------------------------------
 __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int64_t n_pts, double cutoff,
                             double width_mult, const CondDev *cond, int *n_abs, float *f_frac, int *ka_abs,
-                            int *kb_abs, GeomStats *gs) {
+                            int *kb_abs, GeomStats *gs, float4 *tc_geo, float4 *tc_phys) {
     const double inv_h = 1.0 / step;
     float m1 = 0.f, m2 = 0.f;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
@@ -211,6 +229,12 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
         float nuf = (float)nu;
         m1 = fmaxf(m1, gA / (nuf * nuf));
         m2 = fmaxf(m2, gA / nuf);
+        if (tc_geo) {
+            // the far-wing kernel's line records: position, cut range (exact integers
+            // as floats) and the condition-independent physics
+            tc_geo[l] = make_float4((float)n_abs[l], f_frac[l], (float)ka_abs[l], (float)kb_abs[l]);
+            tc_phys[l] = make_float4(nuf, L.elower[l], gA / (nuf * nuf), L.gamma_ref[l]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
@@ -275,6 +299,45 @@ __global__ void k_nodes_to_float(const double *x, const double *w, int n, float 
 //   GHS: A = {sh, G', P, 0}
 //   GHB: A = {sh, g', G' - 1/4, P}
 // ---------------------------------------------------------------------------
+// Doppler and Lorentz half-widths in grid steps (Eqs. e:alphaD, e:gamma_L)
+__device__ __forceinline__ void line_widths(float nu, float gref, float nT, const CParam &c, float inv_h, float *ah,
+                                            float *gh) {
+    float al = c.acoef * nu;
+    float ga = c.pscale * gref * ex2_approx((nT + c.nshift) * c.log2Tr);
+    *ah = __fmul_rn(al, inv_h);
+    *gh = __fmul_rn(ga, inv_h);
+}
+
+// Voigt w4 zones of a (line, condition) from its widths in grid steps: x = a |delta|,
+// y, the region-I threshold u >= t2 (t2 < 0: region I everywhere) and the far radius D.
+// Explicitly rounded operations: every kernel that splits work by these gets the same bits.
+//   Far wing: the region-I rational P (u + C)/(u^2 + E u + F) equals its series
+//   P r (1 + c1 r + c2 r^2 + ...) in r = 1/u, c1 = C - E = 3b - g^2, c2 = E^2 - C E - F =
+//   (g^2 - 5b)^2 - 20 b^2.  u^2 + E u + F has its two roots on |u| = C, so |c_n| <=
+//   (2n + 1) C^n and the terms dropped beyond r^2 stay below 7 x^3 / (1 - 9x/7), x = C r:
+//   at u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational.
+//   D: integer radius (grid steps) beyond which every point is in that far zone and in
+//   region I; a block [t0, t1] with n - D > t1 or n + D < t0 (n = integer part of the
+//   line position) qualifies.
+struct W4Zone {
+    float a, y, t2, D;
+};
+__device__ __forceinline__ W4Zone w4_zone(float ah, float gh) {
+    W4Zone z;
+    const float rah = rcp_approx(ah);
+    z.a = __fmul_rn(kSqrtLn2f, rah);
+    z.y = __fmul_rn(z.a, gh);
+    const float thr = __fmul_rn(__fmul_rn(__fsub_rn(15.f, z.y), ah), 1.f / kSqrtLn2f);
+    z.t2 = z.y < 15.f ? __fmul_rn(thr, thr) : -1.f;
+    const float Crn = __fadd_rn(__fmul_rn(__fmul_rn(ah, ah), (float)(0.5 / 0.6931471805599453)), __fmul_rn(gh, gh));
+    // any D >= sqrt(uf) is valid: approximate square root (one MUFU op), scaled up by
+    // more than its error bound
+    float sq;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(fmaxf(__fmul_rn(Crn, kFarU), z.t2)));
+    z.D = ceilf(__fmul_rn(sq, 1.000001f)) + 1.f;
+    return z;
+}
+
 template <int PROF>
 __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
                                             float4 *A, float4 *B, float *thr2, float4 *S) {
@@ -286,8 +349,8 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     float stim = -expm1f(-c.c2T * nu);
     float I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
-    float ga = c.pscale * L.gamma_ref[l] * ex2_approx((L.n_T[l] + c.nshift) * c.log2Tr);  // Eq. e:gamma_L
-    float ah = __fmul_rn(al, inv_h), gh = __fmul_rn(ga, inv_h);   // widths in grid steps
+    float ah, gh;                                                              // widths in grid steps
+    line_widths(nu, L.gamma_ref[l], L.n_T[l], c, inv_h, &ah, &gh);
     *thr2 = -1.f;
     *S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
     if (PROF == XC_VOIGT_W4) {
@@ -297,31 +360,14 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         float P = I * kKappa * gh * inv_h;
         *A = make_float4(2.f * (g2 - b), C * C, P, P * C);
         // a, y and the region-I threshold decide which kernel evaluates a point (the
-        // main kernel: |x| + y >= 15; the centre-zone kernel: the rest); both kernels get
-        // them from this code, with explicitly rounded operations so they agree bit for bit
-        float rah = rcp_approx(ah);
-        float a = __fmul_rn(kSqrtLn2f, rah);  // x = a |delta|
-        float y = __fmul_rn(a, gh);
+        // main kernel: |x| + y >= 15; the centre-zone kernel: the rest); the far radius
+        // which points the tensor-core kernel takes (see w4_zone)
+        const W4Zone z = w4_zone(ah, gh);
         float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
-        float thr = __fmul_rn(__fmul_rn(__fsub_rn(15.f, y), ah), 1.f / kSqrtLn2f);
-        float t2 = y < 15.f ? __fmul_rn(thr, thr) : -1.f;
-        *B = make_float4(a, y, Pv, t2);
-        *thr2 = t2;
-        // far wing: the same rational as a series in r = 1/u,
-        //   P(u + C)/(u^2 + E u + F) = P r (1 + c1 r + c2 r^2 + ...),
-        //   c1 = C - E = 3b - g^2,  c2 = E^2 - C E - F = (g^2 - 5b)^2 - 20 b^2.
-        // u^2 + E u + F has its two roots on |u| = C, so |c_n| <= (2n + 1) C^n and the
-        // terms dropped beyond r^2 stay below 7 x^3 / (1 - 9x/7) with x = C r; at
-        // u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational.
-        // S.w = D: integer radius (grid steps) beyond which every point is in that far
-        // zone and in region I: a block of points [t0, t1] with n - D > t1 or n + D < t0
-        // (n = integer part of the line position) qualifies.  Integer tests, so every
-        // kernel that splits the work this way takes the same decision.
-        // (explicitly rounded: the same bits wherever this is inlined)
+        *B = make_float4(z.a, z.y, Pv, z.t2);
+        *thr2 = z.t2;
         float e5 = g2 - 5.f * b;
-        const float Crn = __fadd_rn(__fmul_rn(__fmul_rn(ah, ah), (float)(0.5 / 0.6931471805599453)), __fmul_rn(gh, gh));
-        float uf = fmaxf(__fmul_rn(Crn, kFarU), t2);
-        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), ceilf(__fsqrt_rn(uf)) + 1.f);
+        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), z.D);
     } else if (PROF == XC_LORENTZ) {
         *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
     } else if (PROF == XC_DOPPLER) {
@@ -393,7 +439,7 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
 // FP32 register partials -> FP64 output (each thread owns its points)
 template <int R, int CG>
 __device__ __forceinline__ void fold_acc(f32x2 (&acc)[R / 2][CG], const int (&ji)[R], int64_t kw, int grp,
-                                         const GatherParams &p, const double *sScale, bool first) {
+                                         const GatherParams &p, const double *sScale, const int *sRow, bool first) {
 #pragma unroll
     for (int q = 0; q < R / 2; ++q) {
 #pragma unroll
@@ -405,7 +451,7 @@ __device__ __forceinline__ void fold_acc(f32x2 (&acc)[R / 2][CG], const int (&ji
             for (int h = 0; h < 2; ++h) {
                 int64_t k = kw + ji[2 * q + h];
                 if (k < p.n_pts && cc < p.n_cond) {
-                    double *dst = p.sigma + (size_t)cc * (size_t)p.n_pts + (size_t)k;
+                    double *dst = p.sigma + (size_t)sRow[c] * (size_t)p.n_pts + (size_t)k;
                     double v = (double)v2[h] * sScale[c];
                     if (first) *dst = v; else *dst += v;
                 }
@@ -506,6 +552,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
     float *sX = reinterpret_cast<float *>(smem + Lay::kA + Lay::kB + Lay::kMetaI + Lay::kMetaF + Lay::kScale);
     float *sW = sX + 64;
     __shared__ int s_tile;
+    __shared__ int sRow[CG];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int W = p.W;
@@ -541,6 +588,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         if (tid < CG) {
             int c = grp * CG + tid;
             sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
+            sRow[tid] = c < p.n_cond ? p.cp[c].row : 0;
         }
         __syncthreads();
         f32x2 acc[R / 2][CG];
@@ -620,15 +668,76 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
             for (int ib = 0; ib < cnt; ib += 32) {
                 int i = ib + lane;
                 if (PROF == XC_VOIGT_W4 && p.tc_far) {
-                    // the far-wing kernel took every (line, condition) with span_far on this
-                    // 128-point span; the rest, region I only, as masked single lines
-                    bool nr = false;
+                    // The far-wing kernel took every (line, condition) with span_far on this
+                    // 128-point span; the rest here, region I only: pairs of lines that cover
+                    // the span with no centre-zone point (packed, shared reciprocal), the
+                    // others as masked single lines.  Per condition, a line that is far
+                    // drops out of the pair (its numerator constants are zero).
+                    bool fq = false, sq = false;
                     if (i < cnt) {
                         const int4 mi = sMi[i];
+                        const float2 mf = sMf[i];
                         const bool none = (mi.z < span0) || (mi.y > span1) || (mi.y > mi.z);
-                        nr = !none && !span_far(mi.x, (float)mi.w, span0, span1);
+                        const bool nr = !none && !span_far(mi.x, (float)mi.w, span0, span1);
+                        const bool full = (mi.y <= span0) && (mi.z >= span1);
+                        bool core = false;
+                        if (mf.y > 0.f) {
+                            const float cpos = (float)mi.x + mf.x;
+                            const float thr = sqrtf(mf.y) + 1.f;
+                            core = (cpos + thr >= (float)span0) && (cpos - thr <= (float)span1);
+                        }
+                        fq = nr && full && !core;
+                        sq = nr && !fq;
                     }
-                    unsigned nm = __ballot_sync(0xffffffffu, nr);
+                    unsigned fm = __ballot_sync(0xffffffffu, fq);
+                    unsigned nm = __ballot_sync(0xffffffffu, sq);
+                    if (__popc(fm) & 1) {  // odd count: the last fast line joins the single lines
+                        const unsigned top = 1u << (31 - __clz(fm));
+                        fm &= ~top;
+                        nm |= top;
+                    }
+                    while (fm) {
+                        const int i1 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int i2 = ib + __ffs(fm) - 1;
+                        fm &= fm - 1;
+                        const int4 m1 = sMi[i1], m2 = sMi[i2];
+                        const float f1 = sMf[i1].x, n1 = (float)m1.x, f2 = sMf[i2].x, n2 = (float)m2.x;
+                        const f32x2 nn1 = pk2(n1, n1), ff1 = pk2(f1, f1), nn2 = pk2(n2, n2), ff2 = pk2(f2, f2);
+                        f32x2 ua[R / 2], ub[R / 2];
+#pragma unroll
+                        for (int q = 0; q < R / 2; ++q) {
+                            f32x2 da = sub2(sub2(jf2[q], nn1), ff1), db = sub2(sub2(jf2[q], nn2), ff2);
+                            ua[q] = mul2(da, da);
+                            ub[q] = mul2(db, db);
+                        }
+                        bool g1 = false, g2 = false;
+                        if (lane < CG) {
+                            g1 = span_far(m1.x, sfar_radius(smem, i1 * CG + lane), span0, span1);
+                            g2 = span_far(m2.x, sfar_radius(smem, i2 * CG + lane), span0, span1);
+                        }
+                        const unsigned t1 = __ballot_sync(0xffffffffu, g1), t2 = __ballot_sync(0xffffffffu, g2);
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            const bool x1 = (t1 >> c) & 1u, x2 = (t2 >> c) & 1u;
+                            if (x1 && x2) continue;
+                            const ulonglong2 *e1 = reinterpret_cast<const ulonglong2 *>(smem + (size_t)48 * (i1 * CG + c));
+                            const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(smem + (size_t)48 * (i2 * CG + c));
+                            const ulonglong2 a0 = e1[0], b0 = e2[0];
+                            // a line that is far for c contributes nothing here: numerator 0
+                            const ulonglong2 a1 = x1 ? make_ulonglong2(0ull, 0ull) : e1[1];
+                            const ulonglong2 b1 = x2 ? make_ulonglong2(0ull, 0ull) : e2[1];
+#pragma unroll
+                            for (int q = 0; q < R / 2; ++q) {
+                                f32x2 D1 = fma2(ua[q], add2(ua[q], a0.x), a0.y);
+                                f32x2 D2 = fma2(ub[q], add2(ub[q], b0.x), b0.y);
+                                f32x2 q1 = fma2(a1.x, ua[q], a1.y);
+                                f32x2 q2 = fma2(b1.x, ub[q], b1.y);
+                                f32x2 num = fma2(q1, D2, mul2(q2, D1));
+                                acc[q][c] = fma2(num, rcp2(mul2(D1, D2)), acc[q][c]);
+                            }
+                        }
+                    }
                     while (nm) {
                         const int i1 = ib + __ffs(nm) - 1;
                         nm &= nm - 1;
@@ -873,12 +982,12 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 }
             }
             if (++chunk == FOLD_CHUNKS) {
-                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold && !p.tc_far);
+                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !p.tc_far);
                 first_fold = false;
                 chunk = 0;
             }
         }
-        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, first_fold && !p.tc_far);
+        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !p.tc_far);
     }
 }
 
@@ -886,46 +995,57 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 // Far-wing kernel on the tensor cores (Voigt w4, FP32, fixed cut, many conditions).
 //
 // For a block of 128 grid points and a line l far from all of them (integer
-// radius D(l, c), see line_consts), the region-I rational of condition c equals
-// its series r (p0 + p1 r + p2 r^2), r = 1/u, to < 2e-7.  Summed over lines,
+// radius D(l, c), see w4_zone), the region-I rational of condition c equals its
+// series r (p0 + p1 r + p2 r^2), r = 1/u, to < 2e-7.  Summed over lines,
 //   F[k, c] = sum_l sum_j r_kl^(j+1) p_j(l, c)
 // is a matrix product: A[k, (j, l)] = r_kl^(j+1) depends on the point and the
-// line only, B[(j, l), c] = p_j(l, c) on the line and the condition only.  Each
-// CTA owns one block of TC_T = 128 points (one TMEM lane each) and 32 conditions
-// (the MMA's N), walks the lines whose cut reaches the block in chunks of TC_L,
-// and per chunk: computes B in shared memory (zero where (l, c) is not far from
-// the block: the CUDA-core kernel evaluates those), writes A to tensor memory,
-// and issues tcgen05.mma kind::tf32 with M = 128, N = 32, K = 8.  FP32 inputs
-// are split x = hi + lo with hi exact in TF32, and D += Ahi Bhi + Ahi Blo +
+// line only, B[(j, l), c] = p_j(l, c) on the line and the condition only.  A CTA
+// owns TC_BLK blocks of 128 points (one TMEM lane per point, one warp quadrant
+// per 32 points) and 32 conditions (the MMA's N), walks the lines whose cut reaches
+// its points in chunks of TC_L, and per chunk: computes the series coefficients of
+// every (line, condition) once, stores per block a B operand in shared memory (zero
+// where (l, c) is not far from that block: the CUDA-core kernel evaluates those),
+// writes A to tensor memory, and per block one thread issues tcgen05.mma kind::tf32
+// (M = 128, N = 32, K = 8): a CTA keeps one MMA chain per block in flight.  FP32
+// inputs are split x = hi + lo with hi exact in TF32, and D += Ahi Bhi + Ahi Blo +
 // Alo Bhi (the dropped Alo Blo is < 2^-21 of the product).  A and B are double
 // buffered (the next chunk is built while the MMAs of this one run).  The tensor
 // core adds in FP32 with truncation, a bias that grows with the number of MMAs
-// summed into one accumulator, so D (FP32 in TMEM) is restarted every TC_FOLD
-// chunks after its value is added into compensated (Kahan) FP32 sums in shared
-// memory; the block is written (not added) to the output at the end.
+// summed into one accumulator, so D is restarted every TC_FOLD chunks after its
+// value is added into compensated (Kahan) FP32 sums in shared memory; the blocks
+// are written (not added) to the output at the end.
 // ---------------------------------------------------------------------------
-constexpr int TC_T = 128;                 // threads = points per block = MMA M
+constexpr int TC_M = 128;                 // points per block = MMA M = TMEM lanes
+constexpr int TC_BLK = 2;                 // blocks per CTA (one MMA issuer each)
+constexpr int TC_T = TC_M * TC_BLK;       // threads per CTA: one per point
 constexpr int TC_N = 32;                  // conditions per tile = MMA N
 constexpr int TC_L = 8;                   // lines per chunk
 constexpr int TC_J = 3;                   // series terms
 constexpr int TC_K = TC_L * TC_J;         // K elements per chunk (3 MMA K-steps of 8)
-constexpr int TC_FOLD = 8;                // chunks per tensor-memory accumulation period (64 lines)
-constexpr uint32_t TC_COLS = 128;         // TMEM columns: D 32 + 2 buffers x (24 hi + 24 lo)
+constexpr int TC_FOLD = 16;               // chunks per tensor-memory accumulation period
+constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x (24 hi + 24 lo)
 constexpr int TC_BFLOATS = TC_N * TC_K;   // one B operand (hi or lo): 768 floats
-constexpr size_t TC_SMEM_B = (size_t)4 * TC_BFLOATS * sizeof(float);   // 2 buffers x (hi, lo)
-constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);   // compensated FP32 sums
-constexpr size_t TC_SMEM = 50 * 1024;     // B + FP64 sums + barriers; sized so that 4 CTAs (4 x 128 TMEM
-                                          // columns) and never 5 share an SM
-static_assert(TC_SMEM_B + TC_SMEM_ACC + 64 <= TC_SMEM, "far-wing kernel shared memory");
+constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * 2 * TC_BFLOATS * sizeof(float);  // [blk][buf][hi, lo]
+constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);           // compensated FP32 sums
+constexpr size_t TC_SMEM = 100 * 1024;    // B + sums + barriers; sized so that 2 CTAs (2 x 256 TMEM
+                                          // columns) and never 3 share an SM
+static_assert(TC_SMEM_B + TC_SMEM_ACC + 128 + 4 * TC_L * 16 + 2 * TC_L * 4 + 8 <= TC_SMEM, "far-wing kernel shared memory");
+
+// a chunk line with a cut covering the whole super-block [t0, t0 + TC_T) and its centre
+// at least one step outside it: no range test and no guard against u < 1 needed
+__device__ __forceinline__ bool tc_line_plain(const float4 &g, int t0) {
+    return g.z <= (float)t0 && g.w >= (float)(t0 + TC_T - 1) &&
+           (g.x <= (float)(t0 - 2) || g.x >= (float)(t0 + TC_T + 1));
+}
+static_assert(TC_N * TC_L == TC_T, "one (line, condition) pair per thread and chunk");
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 struct TcParams {
-    LinesDev L;
-    const int *n_abs;
-    const float *f_frac;
-    const int *ka_abs, *kb_abs;
+    const float4 *geo;                 // per line: integer position n, fraction f, ka, kb (floats)
+    const float4 *phys;                // per line: nu, E'', g A / nu^2, gamma_ref (float)
+    const float *n_T;                  // per line: temperature exponent
     const CParam *cp;
-    const unsigned *blk_lo, *blk_hi;   // per 128-point block: line range
+    const unsigned *blk_lo, *blk_hi;   // per TC_T-point super-block: line range
     int *counter;
     int *status;                       // set to 1 if a wait ran out
     int n_tiles, n_groups, n_cond;
@@ -940,19 +1060,40 @@ __device__ __forceinline__ int tc_b_index(int n, int k) {
     return (((n >> 3) * (TC_K / 4) + (k >> 2)) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
 }
 
-__global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
+// series coefficients (p0, p1, p2) and far radius D of a (line, condition); D is the
+// same value line_consts gives (same inputs, same rounded operations)
+__device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, const CParam &c, float inv_h) {
+    const float nu = ph.x, E = ph.y;
+    const float z = fmaf(E, c.kT_hi, E * c.kT_lo);
+    const float I = c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
+    float ah, gh;
+    line_widths(nu, ph.w, nT, c, inv_h, &ah, &gh);
+    const W4Zone zn = w4_zone(ah, gh);
+    const float b = ah * ah * (float)(0.5 / 0.6931471805599453), g2 = gh * gh;
+    const float P = I * kKappa * gh * inv_h;
+    const float e5 = g2 - 5.f * b;
+    return make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), zn.D);
+}
+
+__global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *sB = reinterpret_cast<float *>(smem);                           // [buf][hi, lo][768]
+    float *sB = reinterpret_cast<float *>(smem);                           // [blk][buf][hi, lo][768]
     float *sSum = reinterpret_cast<float *>(smem + TC_SMEM_B);             // [c][point]
     float *sCmp = sSum + TC_N * TC_T;                                       // Kahan compensation
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_SMEM_B + TC_SMEM_ACC);
-    uint32_t *sTmem = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_SMEM_B + TC_SMEM_ACC);  // [blk][buf]
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(mbar + 2 * TC_BLK);
     int *sTile = reinterpret_cast<int *>(sTmem + 1);
+    // the chunk's line records, double buffered: loaded into registers by TC_L threads one
+    // chunk ahead and stored before the chunk's barrier, so their latency is hidden
+    float4 *sGeo = reinterpret_cast<float4 *>(smem + TC_SMEM_B + TC_SMEM_ACC + 128);   // [2][TC_L]
+    float4 *sPhys = sGeo + 2 * TC_L;                                                     // [2][TC_L]
+    float *sNT = reinterpret_cast<float *>(sPhys + 2 * TC_L);                            // [2][TC_L]
+    int *sFast = reinterpret_cast<int *>(sNT + 2 * TC_L);                                // [2]
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int blkh = tid / TC_M;                 // this thread's block within the CTA
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 2 * TC_BLK; ++i) tc::mbar_init(&mbar[i], 1);
         tc::mbar_init_fence();
     }
     if (warp == 0) tc::tmem_alloc(sTmem, TC_COLS);
@@ -961,14 +1102,22 @@ __global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *sTmem;
-    const uint32_t t_lane = tbase + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+    const uint32_t tblk = tbase + 128u * blkh;                                // this block's columns
+    const uint32_t t_lane = tblk + ((uint32_t)((warp & 3) * 32) << 16);       // this warp's lanes
     constexpr uint32_t kIdesc = tc::idesc_tf32(128, TC_N);
     const uint32_t sB_addr = tc::smem_u32(sB);
+    const bool issuer = (tid & (TC_M - 1)) == 0;  // thread 0 of each block
 
-    uint32_t uses[2] = {0u, 0u};   // commits per barrier so far (uniform over the CTA)
+    uint32_t uses[2] = {0u, 0u};   // commits per buffer (each block's barrier of it) so far
     bool ok = true;
-    // the (line, condition) pair this thread turns into B entries: line tid / 16, conditions tid % 16 (+16)
-    const int lB = tid >> 4, cB = tid & 15;
+    // The (line, condition) pair whose coefficients this thread computes each chunk, chosen
+    // so that a warp's B entries of one term fill one 8 x 4 core matrix (32 consecutive
+    // floats: conflict-free stores): conditions 8 (w % 4) .. + 7, lines 4 (w / 4) .. + 3.
+    const int lane = tid & 31;
+    const int cB = (warp & 3) * 8 + (lane >> 2), lB = (warp >> 2) * 4 + (lane & 3);
+    int bix[TC_J];
+#pragma unroll
+    for (int j = 0; j < TC_J; ++j) bix[j] = tc_b_index(cB, j * TC_L + lB);
 
     for (;;) {
         if (tid == 0) *sTile = atomicAdd(p.counter, 1);
@@ -976,76 +1125,128 @@ __global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
         const int t = *sTile;
         __syncthreads();
         if (t >= p.n_tiles) break;
-        const int blk = t / p.n_groups, grp = t % p.n_groups;
-        const int t0 = blk * TC_T, t1 = t0 + TC_T - 1;
-        const int k = t0 + tid;
-        const unsigned lo = p.blk_lo[blk], hi = p.blk_hi[blk];
-        const unsigned nl = hi - lo;
-        const int nch = (int)((nl + TC_L - 1) / TC_L);
-        CParam cpr[2];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int cc = grp * TC_N + cB + 16 * h2;
-            if (cc < p.n_cond) cpr[h2] = p.cp[cc];
+        const int sblk = t / p.n_groups, grp = t % p.n_groups;
+        const int t0 = sblk * TC_T;               // first point of the super-block
+        const float kf = (float)(t0 + tid);       // this thread's point (exact: < 2^23)
+        const unsigned lo = p.blk_lo[sblk], hi = p.blk_hi[sblk];
+        const int nl = (int)(hi - lo);
+        const int nch = (nl + TC_L - 1) / TC_L;
+        const float4 *geo = p.geo + lo;
+        const float4 *phys = p.phys + lo;
+        const float *nT = p.n_T + lo;
+        const int cc = grp * TC_N + cB;
+        CParam cpr;
+        if (cc < p.n_cond) cpr = p.cp[cc];
+        if (warp == 0 && nch > 0) {
+            bool plain = true;
+            if (tid < TC_L) {
+                const int li = tid < nl ? tid : 0;
+                const float4 g = geo[li];
+                sGeo[tid] = g;
+                sPhys[tid] = phys[li];
+                sNT[tid] = nT[li];
+                plain = tid < nl && tc_line_plain(g, t0);
+            }
+            const unsigned all = __ballot_sync(0xffffffffu, plain);
+            if (tid == 0) sFast[0] = all == 0xffffffffu;
         }
+        __syncthreads();
         int in_fold = 0;
         for (int ci = 0; ci < nch; ++ci) {
             const int b = ci & 1;
-            // buffer b is free once the MMAs of its previous chunk have completed
+            // next chunk's records: issue the loads now, store them before this chunk's barrier
+            float4 nGeo, nPhys;
+            float nNT = 0.f;
+            const bool pre = tid < TC_L && ci + 1 < nch;
+            if (pre) {
+                const int li = min((ci + 1) * TC_L + tid, nl - 1);
+                nGeo = geo[li];
+                nPhys = phys[li];
+                nNT = nT[li];
+            }
+            const bool fast = sFast[b] != 0;
+            const float4 *cGeo = sGeo + b * TC_L;
+            // buffer b of every block is free once the MMAs of its previous chunk completed
             if (uses[b] > 0u) {
-                ok &= tc::mbar_wait(&mbar[b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
+#pragma unroll
+                for (int hb = 0; hb < TC_BLK; ++hb)
+                    ok &= tc::mbar_wait(&mbar[hb * 2 + b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
                 tc::fence_after_sync();
             }
-            const unsigned base = lo + (unsigned)ci * TC_L;
-            // ---- B: series coefficients of the far (line, condition) pairs, split hi + lo
+            const int l0 = ci * TC_L;
+            // ---- B: series coefficients of this thread's (line, condition), per block zero
+            // unless far from all of that block's points, split hi + lo
             {
-                float *bh = sB + (size_t)b * 2 * TC_BFLOATS, *bl = bh + TC_BFLOATS;
-                const unsigned li = base + lB;
+                float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+                float na = 0.f;
+                bool live = false;
+                if (l0 + lB < nl && cc < p.n_cond) {
+                    const float4 g = cGeo[lB];
+                    live = g.w >= g.z;   // non-empty cut range
+                    na = g.x;
+                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h);
+                }
 #pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int c = cB + 16 * h2, cc = grp * TC_N + c;
-                    float v[TC_J] = {0.f, 0.f, 0.f};
-                    if (li < hi && cc < p.n_cond) {
-                        float4 A, B, S;
-                        float t2;
-                        line_consts<XC_VOIGT_W4>(p.L, li, cpr[h2], p.h, p.inv_h, &A, &B, &t2, &S);
-                        const int na = p.n_abs[li];
-                        if (p.kb_abs[li] >= p.ka_abs[li] && span_far(na, S.w, t0, t1)) {
-                            v[0] = S.x;
-                            v[1] = S.y;
-                            v[2] = S.z;
-                        }
-                    }
+                for (int hb = 0; hb < TC_BLK; ++hb) {
+                    const int b0 = t0 + hb * TC_M;
+                    const bool far = live && span_far((int)na, S.w, b0, b0 + TC_M - 1);
+                    float *bh = sB + (size_t)(hb * 2 + b) * 2 * TC_BFLOATS, *bl = bh + TC_BFLOATS;
+                    const float v[TC_J] = {far ? S.x : 0.f, far ? S.y : 0.f, far ? S.z : 0.f};
 #pragma unroll
                     for (int j = 0; j < TC_J; ++j) {
                         const float vh = tc::tf32_hi(v[j]);
-                        const int ix = tc_b_index(c, j * TC_L + lB);
-                        bh[ix] = vh;
-                        bl[ix] = v[j] - vh;
+                        bh[bix[j]] = vh;
+                        bl[bix[j]] = v[j] - vh;
                     }
                 }
             }
             // ---- A: r^(j+1) of this thread's point for the chunk's lines, split hi + lo
             {
                 float av[2 * TC_K];
+                if (fast) {
+                    // every line covers the super-block, no centre in it: two lines per
+                    // packed operation
+                    const f32x2 kf2 = pk2(kf, kf);
 #pragma unroll
-                for (int l8 = 0; l8 < TC_L; ++l8) {
-                    const unsigned li = base + l8;
-                    float r = 0.f;
-                    if (li < hi) {
-                        const int na = p.n_abs[li], ka = p.ka_abs[li], kb = p.kb_abs[li];
-                        const float d = (float)(k - na) - p.f_frac[li];
-                        // inside the cut; points within one step of the centre only ever meet
-                        // zero B entries (not far), r is kept finite there
-                        if (k >= ka && k <= kb) r = rcp_approx(fmaxf(d * d, 1.f));
+                    for (int l8 = 0; l8 < TC_L; l8 += 2) {
+                        const float4 g0 = cGeo[l8], g1 = cGeo[l8 + 1];
+                        const f32x2 d = sub2(sub2(kf2, pk2(g0.x, g1.x)), pk2(g0.y, g1.y));
+                        const f32x2 r = rcp2(mul2(d, d));
+                        f32x2 pw = r;
+#pragma unroll
+                        for (int j = 0; j < TC_J; ++j) {
+                            float x0, x1;
+                            upk2(pw, x0, x1);
+                            const f32x2 vh = pk2(tc::tf32_hi(x0), tc::tf32_hi(x1));
+                            float h0, h1, e0, e1;
+                            upk2(vh, h0, h1);
+                            upk2(sub2(pw, vh), e0, e1);
+                            av[j * TC_L + l8] = h0;
+                            av[j * TC_L + l8 + 1] = h1;
+                            av[TC_K + j * TC_L + l8] = e0;
+                            av[TC_K + j * TC_L + l8 + 1] = e1;
+                            pw = mul2(pw, r);
+                        }
                     }
-                    float pw = r;
+                } else {
 #pragma unroll
-                    for (int j = 0; j < TC_J; ++j) {
-                        const float vh = tc::tf32_hi(pw);
-                        av[j * TC_L + l8] = vh;
-                        av[TC_K + j * TC_L + l8] = pw - vh;
-                        pw *= r;
+                    for (int l8 = 0; l8 < TC_L; ++l8) {
+                        float r = 0.f;
+                        if (l0 + l8 < nl) {
+                            const float4 g = cGeo[l8];
+                            const float d = (kf - g.x) - g.y;
+                            // inside the cut; points within one step of the centre only ever
+                            // meet zero B entries (not far), r is kept finite there
+                            if (kf >= g.z && kf <= g.w) r = rcp_approx(fmaxf(d * d, 1.f));
+                        }
+                        float pw = r;
+#pragma unroll
+                        for (int j = 0; j < TC_J; ++j) {
+                            const float vh = tc::tf32_hi(pw);
+                            av[j * TC_L + l8] = vh;
+                            av[TC_K + j * TC_L + l8] = pw - vh;
+                            pw *= r;
+                        }
                     }
                 }
                 const uint32_t ta = t_lane + 32u + (uint32_t)b * (2u * TC_K);
@@ -1058,29 +1259,41 @@ __global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
                 }
                 tc::tmem_st_wait();
             }
+            if (warp == 0 && ci + 1 < nch) {
+                bool plain = true;
+                if (pre) {
+                    const int nb = (b ^ 1) * TC_L;
+                    sGeo[nb + tid] = nGeo;
+                    sPhys[nb + tid] = nPhys;
+                    sNT[nb + tid] = nNT;
+                    plain = (ci + 1) * TC_L + tid < nl && tc_line_plain(nGeo, t0);
+                }
+                const unsigned all = __ballot_sync(0xffffffffu, plain);
+                if (tid == 0) sFast[b ^ 1] = all == 0xffffffffu;
+            }
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
-            if (tid == 0) {
+            if (issuer) {
                 tc::fence_after_sync();
-                const uint32_t a_hi = tbase + 32u + (uint32_t)b * (2u * TC_K), a_lo = a_hi + TC_K;
-                const uint32_t bh_addr = sB_addr + (uint32_t)(b * 2 * TC_BFLOATS * 4);
+                const uint32_t a_hi = tblk + 32u + (uint32_t)b * (2u * TC_K), a_lo = a_hi + TC_K;
+                const uint32_t bh_addr = sB_addr + (uint32_t)((blkh * 2 + b) * 2 * TC_BFLOATS * 4);
                 const uint32_t bl_addr = bh_addr + (uint32_t)(TC_BFLOATS * 4);
 #pragma unroll
                 for (int s = 0; s < TC_K / 8; ++s) {
                     // K-step s: two core matrices along K (256 bytes), LBO 128, SBO 6 x 128
                     const uint64_t dh = tc::smem_desc(bh_addr + 256u * s, 128u, 128u * (TC_K / 4));
                     const uint64_t dl = tc::smem_desc(bl_addr + 256u * s, 128u, 128u * (TC_K / 4));
-                    tc::mma_tf32_ts(tbase, a_hi + 8u * s, dh, kIdesc, (in_fold > 0 || s > 0) ? 1u : 0u);
-                    tc::mma_tf32_ts(tbase, a_hi + 8u * s, dl, kIdesc, 1u);
-                    tc::mma_tf32_ts(tbase, a_lo + 8u * s, dh, kIdesc, 1u);
+                    tc::mma_tf32_ts(tblk, a_hi + 8u * s, dh, kIdesc, (in_fold > 0 || s > 0) ? 1u : 0u);
+                    tc::mma_tf32_ts(tblk, a_hi + 8u * s, dl, kIdesc, 1u);
+                    tc::mma_tf32_ts(tblk, a_lo + 8u * s, dh, kIdesc, 1u);
                 }
-                tc::mma_commit(&mbar[b]);
+                tc::mma_commit(&mbar[blkh * 2 + b]);
             }
             ++uses[b];
             if (++in_fold == TC_FOLD || ci == nch - 1) {
-                // tensor-memory sums -> compensated FP32 sums (each thread owns its point's row)
-                ok &= tc::mbar_wait(&mbar[b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
+                // this block's tensor-memory sums -> compensated FP32 sums (one row per thread)
+                ok &= tc::mbar_wait(&mbar[blkh * 2 + b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
                 tc::fence_after_sync();
                 float v[32];
                 tc::tmem_ld32(t_lane, v);
@@ -1096,12 +1309,13 @@ __global__ void __launch_bounds__(TC_T, 4) k_far_tc(TcParams p) {
                 in_fold = 0;
             }
         }
-        // ---- the block's far-wing sums: first writer of these outputs
+        // ---- the super-block's far-wing sums: first writer of these outputs
+        const int64_t k = (int64_t)t0 + tid;
         for (int c = 0; c < TC_N; ++c) {
-            const int cc = grp * TC_N + c;
-            if ((int64_t)k < p.n_pts && cc < p.n_cond)
-                p.sigma[(size_t)cc * (size_t)p.n_pts + (size_t)k] =
-                    ((double)sSum[c * TC_T + tid] - (double)sCmp[c * TC_T + tid]) * p.cp[cc].inv_scale;
+            const int c2 = grp * TC_N + c;
+            if (k < p.n_pts && c2 < p.n_cond)
+                p.sigma[(size_t)p.cp[c2].row * (size_t)p.n_pts + (size_t)k] =
+                    ((double)sSum[c * TC_T + tid] - (double)sCmp[c * TC_T + tid]) * p.cp[c2].inv_scale;
             sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
         }
     }
@@ -1159,9 +1373,11 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
     const int64_t kw = (int64_t)blockIdx.x * CORE_T;
     const int grp = blockIdx.y;
     const float jf = (float)tid;
+    __shared__ int sRow[CORE_CG];
     if (tid < CORE_CG) {
         int c = grp * CORE_CG + tid;
         sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
+        sRow[tid] = c < p.n_cond ? p.cp[c].row : 0;
     }
 #pragma unroll
     for (int c = 0; c < CORE_CG; ++c) sAcc[c][tid] = 0.f;
@@ -1246,7 +1462,7 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             int cc = grp * CORE_CG + c;
             float a = sAcc[c][tid];
             if (cc < p.n_cond && a != 0.f)
-                p.sigma[(size_t)cc * (size_t)p.n_pts + (size_t)k] += (double)a * sScale[c];
+                p.sigma[(size_t)sRow[c] * (size_t)p.n_pts + (size_t)k] += (double)a * sScale[c];
         }
     }
 }
@@ -1334,9 +1550,10 @@ struct Plan {
     int n_win_core = 0;                         // centre-zone kernel windows (Voigt w4)
     unsigned *core_lo = nullptr, *core_hi = nullptr;
     bool tc = false;                            // far wings on the tensor cores (Voigt w4)
-    int n_blk = 0, n_tc_tiles = 0;              // 128-point blocks, (block, 32-condition group) tiles
+    int n_blk = 0, n_tc_tiles = 0;              // TC_T-point super-blocks, (super-block, group) tiles
     unsigned *blk_lo = nullptr, *blk_hi = nullptr;
     int *tc_counter = nullptr, *tc_status = nullptr;
+    float4 *tc_geo = nullptr, *tc_phys = nullptr;
 };
 
 xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl,
@@ -1356,13 +1573,15 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
     pl->n_win_core = (int)((a.grid.n + CORE_T - 1) / CORE_T);
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
-    size_t o_blo = 0, o_bhi = 0, o_tcc = 0;
+    size_t o_blo = 0, o_bhi = 0, o_tcc = 0, o_geo = 0, o_phys = 0;
     if (tc) {
         pl->n_blk = (int)((a.grid.n + TC_T - 1) / TC_T);
         pl->n_tc_tiles = pl->n_blk * ((n_cond_call + TC_N - 1) / TC_N);
         o_blo = carve((size_t)pl->n_blk * 4);
         o_bhi = carve((size_t)pl->n_blk * 4);
         o_tcc = carve(64);
+        o_geo = carve(n * sizeof(float4));
+        o_phys = carve(n * sizeof(float4));
     }
     BT_TRY(st->tiles.ensure(off));
     char *b = st->tiles.as<char>();
@@ -1385,6 +1604,8 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->blk_hi = (unsigned *)(b + o_bhi);
         pl->tc_counter = (int *)(b + o_tcc);
         pl->tc_status = pl->tc_counter + 1;
+        pl->tc_geo = (float4 *)(b + o_geo);
+        pl->tc_phys = (float4 *)(b + o_phys);
         st->tc_status = pl->tc_status;
     }
     return XC_OK;
@@ -1403,7 +1624,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     k_line_geom<<<gblocks, 256, 0, s>>>(a.L, n, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
                                         per_cond_cut ? a.opts.width_mult : 0.0,
                                         per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
-                                        pl.gs);
+                                        pl.gs, pl.tc ? pl.tc_geo : nullptr, pl.tc ? pl.tc_phys : nullptr);
     k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp);
     k_win_ranges32<<<(pl.n_win + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
                                                            pl.W, a.opts.cutoff, pl.n_win, pl.lo, pl.hi);
@@ -1447,11 +1668,9 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
                                                               TC_T, a.opts.cutoff, pl.n_blk, pl.blk_lo, pl.blk_hi);
         BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 2 * sizeof(int), s));
         TcParams tp;
-        tp.L = a.L;
-        tp.n_abs = pl.n_abs;
-        tp.f_frac = pl.f;
-        tp.ka_abs = pl.ka;
-        tp.kb_abs = pl.kb;
+        tp.geo = pl.tc_geo;
+        tp.phys = pl.tc_phys;
+        tp.n_T = a.L.n_T;
         tp.cp = pl.cp;
         tp.blk_lo = pl.blk_lo;
         tp.blk_hi = pl.blk_hi;
@@ -1534,18 +1753,18 @@ int tc_grid_size(int n_tiles) {
                              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, (const void *)k_far_tc, TC_T, TC_SMEM)
                              : e1;
         // The occupancy query answers 1 for this kernel (it does not model tensor-memory
-        // allocation); residency is bounded by shared memory (TC_SMEM admits 4 CTAs), by
-        // registers, and by the 512 TMEM columns of an SM (4 x 128).  Extra CTAs would
+        // allocation); residency is bounded by shared memory (TC_SMEM admits 2 CTAs), by
+        // registers, and by the 512 TMEM columns of an SM (2 x 256).  Extra CTAs would
         // only wait: the work queue is shared.
         cudaFuncAttributes fa;
         int dev0 = 0, smem_sm = 0;
         cudaGetDevice(&dev0);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev0);
-        int by_regs = 4, by_smem = 4;
+        int by_regs = 1, by_smem = 1;
         if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc) == cudaSuccess && fa.numRegs > 0)
             by_regs = 65536 / (fa.numRegs * TC_T);
         if (smem_sm > 0) by_smem = smem_sm / (int)(TC_SMEM + 1024);
-        const int mine = std::max(1, std::min(4, std::min(by_regs, by_smem)));
+        const int mine = std::max(1, std::min((int)(512 / TC_COLS), std::min(by_regs, by_smem)));
         snprintf(g_tc_diag, sizeof(g_tc_diag), "query %d (%s), registers %d, shared memory %d", ps,
                  cudaGetErrorString(e2), by_regs, by_smem);
         cudaGetLastError();
@@ -1574,7 +1793,7 @@ int grid_size(const Variant *v, int dev, int n_tiles) {
 // 32, so a handful of conditions would waste it), one fixed cut, grids of < 2^30 points
 bool use_tc(const BatchedArgs &a, int nc) {
     return a.allow_tc && a.opts.profile == XC_VOIGT_W4 && a.opts.width_mult <= 0.0 && nc >= 16 &&
-           !(a.opts.flags & XC_OPT_NO_TENSOR_CORES) && a.grid.n < ((int64_t)1 << 30);
+           !(a.opts.flags & XC_OPT_NO_TENSOR_CORES) && a.grid.n < ((int64_t)1 << 23);
 }
 
 std::string tuned_key(const BatchedState *st, const BatchedArgs &a, int nc) {
