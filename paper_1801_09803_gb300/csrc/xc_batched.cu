@@ -1006,10 +1006,14 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 // every (line, condition) once, stores per block a B operand in shared memory (zero
 // where (l, c) is not far from that block: the CUDA-core kernel evaluates those),
 // writes A to tensor memory, and per block one thread issues tcgen05.mma kind::tf32
-// (M = 128, N = 32, K = 8): a CTA keeps one MMA chain per block in flight.  FP32
-// inputs are split x = hi + lo with hi exact in TF32, and D += Ahi Bhi + Ahi Blo +
-// Alo Bhi (the dropped Alo Blo is < 2^-21 of the product).  A and B are double
-// buffered (the next chunk is built while the MMAs of this one run).  The tensor
+// (M = 128, N = 32, K = 8): a CTA keeps one MMA chain per block in flight.  Operand
+// precision follows each term's weight: for j = 0 (the value itself) r and p0 are
+// split x = hi + lo with hi exact in TF32 and D += rhi p0hi + rhi p0lo + rlo p0hi (the
+// dropped rlo p0lo is < 2^-21 of the product); the j = 1 term is at most 3x = 0.009
+// of the value (x = C r <= 0.003), so r^2 rounded to TF32 (relative error <= 2^-11,
+// unbiased) with p1 split costs < 5e-6; the j = 2 term (<= 5x^2 = 5e-5 of the value)
+// takes r^3 and p2 as the MMA reads them.  Six MMAs per chunk and block.  A and B
+// are double buffered (the next chunk is built while the MMAs of this one run).  The tensor
 // core adds in FP32 with truncation, a bias that grows with the number of MMAs
 // summed into one accumulator, so D is restarted every TC_FOLD chunks after its
 // value is added into compensated (Kahan) FP32 sums in shared memory; the blocks
@@ -1021,11 +1025,12 @@ constexpr int TC_T = TC_M * TC_BLK;       // threads per CTA: one per point
 constexpr int TC_N = 32;                  // conditions per tile = MMA N
 constexpr int TC_L = 8;                   // lines per chunk
 constexpr int TC_J = 3;                   // series terms
-constexpr int TC_K = TC_L * TC_J;         // K elements per chunk (3 MMA K-steps of 8)
+constexpr int TC_ACOLS = 4 * TC_L;        // A columns per chunk: r hi, r lo, r^2 (TF32), r^3
+constexpr int TC_BT = 5;                  // B tiles (K = 8 each): p0 hi, p0 lo, p1 hi, p1 lo, p2
 constexpr int TC_FOLD = 16;               // chunks per tensor-memory accumulation period
-constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x (24 hi + 24 lo)
-constexpr int TC_BFLOATS = TC_N * TC_K;   // one B operand (hi or lo): 768 floats
-constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * 2 * TC_BFLOATS * sizeof(float);  // [blk][buf][hi, lo]
+constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x 32 (+ 32 spare)
+constexpr int TC_BTILE = TC_N * TC_L;     // one B tile: 8 K x 32 N = 256 floats (1 KB)
+constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * TC_BT * TC_BTILE * sizeof(float);  // [blk][buf][tile]
 constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);           // compensated FP32 sums
 constexpr size_t TC_SMEM = 100 * 1024;    // B + sums + barriers; sized so that 2 CTAs (2 x 256 TMEM
                                           // columns) and never 3 share an SM
@@ -1054,10 +1059,10 @@ struct TcParams {
     double *sigma;
 };
 
-// B element (n, k) of a K-major operand with 8 x 16-byte core matrices:
-// core (n / 8, k / 4) at ((n / 8) * (TC_K / 4) + k / 4) * 128 bytes
+// element (n, k) of an 8 (K) x 32 (N) B tile, K-major with 8 x 16-byte core matrices:
+// core (n / 8, k / 4) at ((n / 8) * 2 + k / 4) * 128 bytes (LBO 128, SBO 256)
 __device__ __forceinline__ int tc_b_index(int n, int k) {
-    return (((n >> 3) * (TC_K / 4) + (k >> 2)) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
+    return (((n >> 3) * 2 + (k >> 2)) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
 }
 
 // series coefficients (p0, p1, p2) and far radius D of a (line, condition); D is the
@@ -1107,6 +1112,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     constexpr uint32_t kIdesc = tc::idesc_tf32(128, TC_N);
     const uint32_t sB_addr = tc::smem_u32(sB);
     const bool issuer = (tid & (TC_M - 1)) == 0;  // thread 0 of each block
+    // descriptor of this block's B operand (buffer 0, hi); the whole region lies below
+    // 256 KB, so the start field never carries into the next one
+    const uint64_t desc_b0 = tc::smem_desc(sB_addr + (uint32_t)(blkh * 2 * TC_BT * TC_BTILE * 4), 128u, 256u);
 
     uint32_t uses[2] = {0u, 0u};   // commits per buffer (each block's barrier of it) so far
     bool ok = true;
@@ -1115,9 +1123,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     // floats: conflict-free stores): conditions 8 (w % 4) .. + 7, lines 4 (w / 4) .. + 3.
     const int lane = tid & 31;
     const int cB = (warp & 3) * 8 + (lane >> 2), lB = (warp >> 2) * 4 + (lane & 3);
-    int bix[TC_J];
-#pragma unroll
-    for (int j = 0; j < TC_J; ++j) bix[j] = tc_b_index(cB, j * TC_L + lB);
+    const int bix = tc_b_index(cB, lB);   // the same slot in each of the five B tiles
 
     for (;;) {
         if (tid == 0) *sTile = atomicAdd(p.counter, 1);
@@ -1186,73 +1192,46 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     na = g.x;
                     S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h);
                 }
+                const float p0h = tc::tf32_hi(S.x), p1h = tc::tf32_hi(S.y);
+                const float p0l = S.x - p0h, p1l = S.y - p1h;
 #pragma unroll
                 for (int hb = 0; hb < TC_BLK; ++hb) {
                     const int b0 = t0 + hb * TC_M;
                     const bool far = live && span_far((int)na, S.w, b0, b0 + TC_M - 1);
-                    float *bh = sB + (size_t)(hb * 2 + b) * 2 * TC_BFLOATS, *bl = bh + TC_BFLOATS;
-                    const float v[TC_J] = {far ? S.x : 0.f, far ? S.y : 0.f, far ? S.z : 0.f};
-#pragma unroll
-                    for (int j = 0; j < TC_J; ++j) {
-                        const float vh = tc::tf32_hi(v[j]);
-                        bh[bix[j]] = vh;
-                        bl[bix[j]] = v[j] - vh;
-                    }
+                    float *bt = sB + (size_t)(hb * 2 + b) * TC_BT * TC_BTILE + bix;
+                    bt[0 * TC_BTILE] = far ? p0h : 0.f;
+                    bt[1 * TC_BTILE] = far ? p0l : 0.f;
+                    bt[2 * TC_BTILE] = far ? p1h : 0.f;
+                    bt[3 * TC_BTILE] = far ? p1l : 0.f;
+                    bt[4 * TC_BTILE] = far ? S.z : 0.f;
                 }
             }
             // ---- A: r^(j+1) of this thread's point for the chunk's lines, split hi + lo
             {
-                float av[2 * TC_K];
-                if (fast) {
-                    // every line covers the super-block, no centre in it: two lines per
-                    // packed operation
-                    const f32x2 kf2 = pk2(kf, kf);
+                float av[TC_ACOLS];   // [r hi | r lo | r^2 | r^3], TC_L lines each
 #pragma unroll
-                    for (int l8 = 0; l8 < TC_L; l8 += 2) {
-                        const float4 g0 = cGeo[l8], g1 = cGeo[l8 + 1];
-                        const f32x2 d = sub2(sub2(kf2, pk2(g0.x, g1.x)), pk2(g0.y, g1.y));
-                        const f32x2 r = rcp2(mul2(d, d));
-                        f32x2 pw = r;
-#pragma unroll
-                        for (int j = 0; j < TC_J; ++j) {
-                            float x0, x1;
-                            upk2(pw, x0, x1);
-                            const f32x2 vh = pk2(tc::tf32_hi(x0), tc::tf32_hi(x1));
-                            float h0, h1, e0, e1;
-                            upk2(vh, h0, h1);
-                            upk2(sub2(pw, vh), e0, e1);
-                            av[j * TC_L + l8] = h0;
-                            av[j * TC_L + l8 + 1] = h1;
-                            av[TC_K + j * TC_L + l8] = e0;
-                            av[TC_K + j * TC_L + l8 + 1] = e1;
-                            pw = mul2(pw, r);
-                        }
+                for (int l8 = 0; l8 < TC_L; ++l8) {
+                    float r;
+                    const float4 g = cGeo[l8];
+                    const float d = (kf - g.x) - g.y;
+                    if (fast) {
+                        // every line covers the super-block, no centre in it
+                        r = rcp_approx(d * d);
+                    } else {
+                        // inside the cut; points within one step of the centre only ever
+                        // meet zero B entries (not far), r is kept finite there
+                        r = (l0 + l8 < nl && kf >= g.z && kf <= g.w) ? rcp_approx(fmaxf(d * d, 1.f)) : 0.f;
                     }
-                } else {
-#pragma unroll
-                    for (int l8 = 0; l8 < TC_L; ++l8) {
-                        float r = 0.f;
-                        if (l0 + l8 < nl) {
-                            const float4 g = cGeo[l8];
-                            const float d = (kf - g.x) - g.y;
-                            // inside the cut; points within one step of the centre only ever
-                            // meet zero B entries (not far), r is kept finite there
-                            if (kf >= g.z && kf <= g.w) r = rcp_approx(fmaxf(d * d, 1.f));
-                        }
-                        float pw = r;
-#pragma unroll
-                        for (int j = 0; j < TC_J; ++j) {
-                            const float vh = tc::tf32_hi(pw);
-                            av[j * TC_L + l8] = vh;
-                            av[TC_K + j * TC_L + l8] = pw - vh;
-                            pw *= r;
-                        }
-                    }
+                    const float rh = tc::tf32_hi(r), r2 = r * r;
+                    av[l8] = rh;
+                    av[TC_L + l8] = r - rh;
+                    av[2 * TC_L + l8] = tc::tf32_hi(r2);
+                    av[3 * TC_L + l8] = r2 * r;
                 }
-                const uint32_t ta = t_lane + 32u + (uint32_t)b * (2u * TC_K);
+                const uint32_t ta = t_lane + 32u + (uint32_t)b * TC_ACOLS;
                 float v16[16];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < 2; ++q) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v16[i] = av[16 * q + i];
                     tc::tmem_st16(ta + 16u * q, v16);
@@ -1276,18 +1255,17 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             __syncthreads();
             if (issuer) {
                 tc::fence_after_sync();
-                const uint32_t a_hi = tblk + 32u + (uint32_t)b * (2u * TC_K), a_lo = a_hi + TC_K;
-                const uint32_t bh_addr = sB_addr + (uint32_t)((blkh * 2 + b) * 2 * TC_BFLOATS * 4);
-                const uint32_t bl_addr = bh_addr + (uint32_t)(TC_BFLOATS * 4);
-#pragma unroll
-                for (int s = 0; s < TC_K / 8; ++s) {
-                    // K-step s: two core matrices along K (256 bytes), LBO 128, SBO 6 x 128
-                    const uint64_t dh = tc::smem_desc(bh_addr + 256u * s, 128u, 128u * (TC_K / 4));
-                    const uint64_t dl = tc::smem_desc(bl_addr + 256u * s, 128u, 128u * (TC_K / 4));
-                    tc::mma_tf32_ts(tblk, a_hi + 8u * s, dh, kIdesc, (in_fold > 0 || s > 0) ? 1u : 0u);
-                    tc::mma_tf32_ts(tblk, a_hi + 8u * s, dl, kIdesc, 1u);
-                    tc::mma_tf32_ts(tblk, a_lo + 8u * s, dh, kIdesc, 1u);
-                }
+                const uint32_t a0 = tblk + 32u + (uint32_t)b * TC_ACOLS;
+                // descriptors differ only in the start address field (bits 0-13, 16-byte units):
+                // tile t of buffer b at + (b * TC_BT + t) KB
+                const uint64_t d0 = desc_b0 + (uint64_t)(b * TC_BT * (TC_BTILE * 4 / 16));
+                constexpr uint64_t kT = TC_BTILE * 4 / 16;
+                tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 0 * kT, kIdesc, in_fold > 0 ? 1u : 0u);  // rhi p0hi
+                tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 1 * kT, kIdesc, 1u);                    // rhi p0lo
+                tc::mma_tf32_ts(tblk, a0 + 1u * TC_L, d0 + 0 * kT, kIdesc, 1u);                    // rlo p0hi
+                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r^2 p1hi
+                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 3 * kT, kIdesc, 1u);                    // r^2 p1lo
+                tc::mma_tf32_ts(tblk, a0 + 3u * TC_L, d0 + 4 * kT, kIdesc, 1u);                    // r^3 p2
                 tc::mma_commit(&mbar[blkh * 2 + b]);
             }
             ++uses[b];

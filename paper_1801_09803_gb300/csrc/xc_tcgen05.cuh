@@ -112,5 +112,13 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(r);
 }
 
+// the same split on the FMA pipe (Veltkamp): hi keeps the leading 11 significant bits
+// (exact in TF32), lo = x - hi exactly; for |x| < 2^100
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    const float c = __fmul_rn(x, 8193.0f);   // 2^13 + 1
+    hi = __fsub_rn(c, __fsub_rn(c, x));
+    lo = __fsub_rn(x, hi);
+}
+
 }  // namespace tc
 }  // namespace xc
