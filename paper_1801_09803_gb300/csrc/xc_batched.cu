@@ -48,7 +48,8 @@ constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 regio
 constexpr float kSqrtLn2f = 0.8325546111576977f;
 constexpr float kSqrtLn2OverPi = 0.46971863934982566f;  // sqrt(ln2/pi)
 constexpr float kPiM32 = 0.17958712212516656f;          // pi^(-3/2)
-constexpr float kFarU = 1.f / 0.003f;                    // far-wing series from u >= C / 0.003
+constexpr float kFarU3 = 1.f / 0.003f;                   // 3-term far-wing series from u >= C / 0.003
+constexpr float kFarU4 = 1.f / 0.012f;                   // 4-term far-wing series from u >= C / 0.012
 
 struct CParam {
     double inv_scale;   // 1 / scale (power of two)
@@ -315,12 +316,14 @@ __device__ __forceinline__ void line_widths(float nu, float gref, float nT, cons
 //   P r (1 + c1 r + c2 r^2 + ...) in r = 1/u, c1 = C - E = 3b - g^2, c2 = E^2 - C E - F =
 //   (g^2 - 5b)^2 - 20 b^2.  u^2 + E u + F has its two roots on |u| = C, so |c_n| <=
 //   (2n + 1) C^n and the terms dropped beyond r^2 stay below 7 x^3 / (1 - 9x/7), x = C r:
-//   at u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational.
-//   D: integer radius (grid steps) beyond which every point is in that far zone and in
-//   region I; a block [t0, t1] with n - D > t1 or n + D < t0 (n = integer part of the
-//   line position) qualifies.
+//   at u >= C / 0.003 that is < 2e-7 of the value, below FP32 rounding of the rational;
+//   with four terms (c3 = -E c2 - F c1) the bound is 9 x^4 / (1 - 11x/9) < 2e-7 from
+//   u >= C / 0.012.
+//   D3, D4: integer radii (grid steps) beyond which every point is in the 3- or 4-term
+//   far zone and in region I; a block [t0, t1] with n - D > t1 or n + D < t0 (n =
+//   integer part of the line position) qualifies.
 struct W4Zone {
-    float a, y, t2, D;
+    float a, y, t2, D3, D4;
 };
 __device__ __forceinline__ W4Zone w4_zone(float ah, float gh) {
     W4Zone z;
@@ -332,15 +335,19 @@ __device__ __forceinline__ W4Zone w4_zone(float ah, float gh) {
     const float Crn = __fadd_rn(__fmul_rn(__fmul_rn(ah, ah), (float)(0.5 / 0.6931471805599453)), __fmul_rn(gh, gh));
     // any D >= sqrt(uf) is valid: approximate square root (one MUFU op), scaled up by
     // more than its error bound
-    float sq;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq) : "f"(fmaxf(__fmul_rn(Crn, kFarU), z.t2)));
-    z.D = ceilf(__fmul_rn(sq, 1.000001f)) + 1.f;
+    float sq3, sq4;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq3) : "f"(fmaxf(__fmul_rn(Crn, kFarU3), z.t2)));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sq4) : "f"(fmaxf(__fmul_rn(Crn, kFarU4), z.t2)));
+    z.D3 = ceilf(__fmul_rn(sq3, 1.000001f)) + 1.f;
+    z.D4 = ceilf(__fmul_rn(sq4, 1.000001f)) + 1.f;
     return z;
 }
 
+// S = (p0, p1, p2, D) of the 3-term far-wing series; D = D4 (the tensor-core kernel's
+// radius) when that kernel takes the far wings (d4), else D3
 template <int PROF>
 __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
-                                            float4 *A, float4 *B, float *thr2, float4 *S) {
+                                            float4 *A, float4 *B, float *thr2, float4 *S, bool d4 = false) {
     const float nu = (float)L.nu[l];
     const float E = L.elower[l];
     // Boltzmann factor exp(-c2 E/T) = 2^-(E c2 log2e / T), product kept to ~1 ulp
@@ -367,7 +374,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         *B = make_float4(z.a, z.y, Pv, z.t2);
         *thr2 = z.t2;
         float e5 = g2 - 5.f * b;
-        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), z.D);
+        *S = make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), d4 ? z.D4 : z.D3);
     } else if (PROF == XC_LORENTZ) {
         *A = make_float4(fmaxf(gh * gh, 1e-30f), I * gh * inv_h * (float)(1.0 / 3.141592653589793), 0.f, 0.f);
     } else if (PROF == XC_DOPPLER) {
@@ -638,7 +645,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                     if (cc < p.n_cond) {
                         line_consts<PROF>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
-                                          &t2, &S);
+                                          &t2, &S, p.tc_far != 0);
                     } else {  // padding condition: contributes exactly 0
                         if (PROF == XC_VOIGT_W4) A = make_float4(1.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
@@ -995,8 +1002,8 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 // Far-wing kernel on the tensor cores (Voigt w4, FP32, fixed cut, many conditions).
 //
 // For a block of 128 grid points and a line l far from all of them (integer
-// radius D(l, c), see w4_zone), the region-I rational of condition c equals its
-// series r (p0 + p1 r + p2 r^2), r = 1/u, to < 2e-7.  Summed over lines,
+// radius D4(l, c), see w4_zone), the region-I rational of condition c equals its
+// series r (p0 + p1 r + p2 r^2 + p3 r^3), r = 1/u, to < 2e-7.  Summed over lines,
 //   F[k, c] = sum_l sum_j r_kl^(j+1) p_j(l, c)
 // is a matrix product: A[k, (j, l)] = r_kl^(j+1) depends on the point and the
 // line only, B[(j, l), c] = p_j(l, c) on the line and the condition only.  A CTA
@@ -1007,13 +1014,13 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 // where (l, c) is not far from that block: the CUDA-core kernel evaluates those),
 // writes A to tensor memory, and per block one thread issues tcgen05.mma kind::tf32
 // (M = 128, N = 32, K = 8): a CTA keeps one MMA chain per block in flight.  Operand
-// precision follows each term's weight: for j = 0 (the value itself) r and p0 are
-// split x = hi + lo with hi exact in TF32 and D += rhi p0hi + rhi p0lo + rlo p0hi (the
-// dropped rlo p0lo is < 2^-21 of the product); the j = 1 term is at most 3x = 0.009
-// of the value (x = C r <= 0.003), so r^2 rounded to TF32 (relative error <= 2^-11,
-// unbiased) with p1 split costs < 5e-6; the j = 2 term (<= 5x^2 = 5e-5 of the value)
-// takes r^3 and p2 as the MMA reads them.  Six MMAs per chunk and block.  A and B
-// are double buffered (the next chunk is built while the MMAs of this one run).  The tensor
+// precision follows each term's weight (four terms, x = C r <= 0.012): for j = 0 (the
+// value itself) and j = 1 (<= 3x = 0.036 of it) r^(j+1) and p_j are split x = hi + lo
+// with hi exact in TF32, D += Ahi Bhi + Ahi Blo + Alo Bhi (the dropped Alo Blo is
+// < 2^-21 of the product); the j = 2 term (<= 5x^2 = 7e-4 of the value) takes r^3 and
+// p2 rounded to TF32 (< 2e-7), the j = 3 term (<= 7x^3 = 1.3e-5) r^4 and p3 as the MMA
+// reads them.  Eight MMAs per chunk and block.  A and B are double buffered (the next
+// chunk is built while the MMAs of this one run).  The tensor
 // core adds in FP32 with truncation, a bias that grows with the number of MMAs
 // summed into one accumulator, so D is restarted every TC_FOLD chunks after its
 // value is added into compensated (Kahan) FP32 sums in shared memory; the blocks
@@ -1024,11 +1031,11 @@ constexpr int TC_BLK = 2;                 // blocks per CTA (one MMA issuer each
 constexpr int TC_T = TC_M * TC_BLK;       // threads per CTA: one per point
 constexpr int TC_N = 32;                  // conditions per tile = MMA N
 constexpr int TC_L = 8;                   // lines per chunk
-constexpr int TC_J = 3;                   // series terms
-constexpr int TC_ACOLS = 4 * TC_L;        // A columns per chunk: r hi, r lo, r^2 (TF32), r^3
-constexpr int TC_BT = 5;                  // B tiles (K = 8 each): p0 hi, p0 lo, p1 hi, p1 lo, p2
+constexpr int TC_J = 4;                   // series terms
+constexpr int TC_ACOLS = 6 * TC_L;        // A columns per chunk: r hi, r lo, r^2 hi, r^2 lo, r^3, r^4
+constexpr int TC_BT = 6;                  // B tiles (K = 8 each): p0 hi, p0 lo, p1 hi, p1 lo, p2, p3
 constexpr int TC_FOLD = 16;               // chunks per tensor-memory accumulation period
-constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x 32 (+ 32 spare)
+constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x 48
 constexpr int TC_BTILE = TC_N * TC_L;     // one B tile: 8 K x 32 N = 256 floats (1 KB)
 constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * TC_BT * TC_BTILE * sizeof(float);  // [blk][buf][tile]
 constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);           // compensated FP32 sums
@@ -1065,9 +1072,10 @@ __device__ __forceinline__ int tc_b_index(int n, int k) {
     return (((n >> 3) * 2 + (k >> 2)) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
 }
 
-// series coefficients (p0, p1, p2) and far radius D of a (line, condition); D is the
-// same value line_consts gives (same inputs, same rounded operations)
-__device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, const CParam &c, float inv_h) {
+// series coefficients (p0, p1, p2) and far radius D4 of a (line, condition), p3 in *p3;
+// D4 is the same value line_consts gives (same inputs, same rounded operations)
+__device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, const CParam &c, float inv_h,
+                                                   float *p3) {
     const float nu = ph.x, E = ph.y;
     const float z = fmaf(E, c.kT_hi, E * c.kT_lo);
     const float I = c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
@@ -1077,7 +1085,10 @@ __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, c
     const float b = ah * ah * (float)(0.5 / 0.6931471805599453), g2 = gh * gh;
     const float P = I * kKappa * gh * inv_h;
     const float e5 = g2 - 5.f * b;
-    return make_float4(P, P * (3.f * b - g2), P * fmaf(e5, e5, -20.f * b * b), zn.D);
+    const float c1 = 3.f * b - g2, c2 = fmaf(e5, e5, -20.f * b * b);
+    const float Cw = b + g2, Ew = 2.f * (g2 - b);
+    *p3 = P * -fmaf(Ew, c2, Cw * Cw * c1);   // c3 = -E c2 - F c1
+    return make_float4(P, P * c1, P * c2, zn.D4);
 }
 
 __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
@@ -1184,15 +1195,16 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             // unless far from all of that block's points, split hi + lo
             {
                 float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+                float p3 = 0.f;
                 float na = 0.f;
                 bool live = false;
                 if (l0 + lB < nl && cc < p.n_cond) {
                     const float4 g = cGeo[lB];
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
-                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h);
+                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3);
                 }
-                const float p0h = tc::tf32_hi(S.x), p1h = tc::tf32_hi(S.y);
+                const float p0h = tc::tf32_hi(S.x), p1h = tc::tf32_hi(S.y), p2h = tc::tf32_hi(S.z);
                 const float p0l = S.x - p0h, p1l = S.y - p1h;
 #pragma unroll
                 for (int hb = 0; hb < TC_BLK; ++hb) {
@@ -1203,12 +1215,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     bt[1 * TC_BTILE] = far ? p0l : 0.f;
                     bt[2 * TC_BTILE] = far ? p1h : 0.f;
                     bt[3 * TC_BTILE] = far ? p1l : 0.f;
-                    bt[4 * TC_BTILE] = far ? S.z : 0.f;
+                    bt[4 * TC_BTILE] = far ? p2h : 0.f;
+                    bt[5 * TC_BTILE] = far ? p3 : 0.f;
                 }
             }
             // ---- A: r^(j+1) of this thread's point for the chunk's lines, split hi + lo
             {
-                float av[TC_ACOLS];   // [r hi | r lo | r^2 | r^3], TC_L lines each
+                float av[TC_ACOLS];   // [r hi | r lo | r^2 hi | r^2 lo | r^3 | r^4], TC_L lines each
 #pragma unroll
                 for (int l8 = 0; l8 < TC_L; ++l8) {
                     float r;
@@ -1222,16 +1235,19 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                         // meet zero B entries (not far), r is kept finite there
                         r = (l0 + l8 < nl && kf >= g.z && kf <= g.w) ? rcp_approx(fmaxf(d * d, 1.f)) : 0.f;
                     }
-                    const float rh = tc::tf32_hi(r), r2 = r * r;
+                    const float r2 = r * r, r3 = r2 * r;
+                    const float rh = tc::tf32_hi(r), r2h = tc::tf32_hi(r2);
                     av[l8] = rh;
                     av[TC_L + l8] = r - rh;
-                    av[2 * TC_L + l8] = tc::tf32_hi(r2);
-                    av[3 * TC_L + l8] = r2 * r;
+                    av[2 * TC_L + l8] = r2h;
+                    av[3 * TC_L + l8] = r2 - r2h;
+                    av[4 * TC_L + l8] = tc::tf32_hi(r3);
+                    av[5 * TC_L + l8] = r2 * r2;
                 }
                 const uint32_t ta = t_lane + 32u + (uint32_t)b * TC_ACOLS;
                 float v16[16];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < TC_ACOLS / 16; ++q) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v16[i] = av[16 * q + i];
                     tc::tmem_st16(ta + 16u * q, v16);
@@ -1263,9 +1279,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                 tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 0 * kT, kIdesc, in_fold > 0 ? 1u : 0u);  // rhi p0hi
                 tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 1 * kT, kIdesc, 1u);                    // rhi p0lo
                 tc::mma_tf32_ts(tblk, a0 + 1u * TC_L, d0 + 0 * kT, kIdesc, 1u);                    // rlo p0hi
-                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r^2 p1hi
-                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 3 * kT, kIdesc, 1u);                    // r^2 p1lo
-                tc::mma_tf32_ts(tblk, a0 + 3u * TC_L, d0 + 4 * kT, kIdesc, 1u);                    // r^3 p2
+                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r2hi p1hi
+                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 3 * kT, kIdesc, 1u);                    // r2hi p1lo
+                tc::mma_tf32_ts(tblk, a0 + 3u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r2lo p1hi
+                tc::mma_tf32_ts(tblk, a0 + 4u * TC_L, d0 + 4 * kT, kIdesc, 1u);                    // r^3 p2
+                tc::mma_tf32_ts(tblk, a0 + 5u * TC_L, d0 + 5 * kT, kIdesc, 1u);                    // r^4 p3
                 tc::mma_commit(&mbar[blkh * 2 + b]);
             }
             ++uses[b];
