@@ -35,6 +35,10 @@ UNIT = "evals/s"
 # t = u + E (1), D = u t + F (2), q = P u + PC (2), q / D (1), accumulate (2).
 # At the FMA/MUFU bound of 32 evals/clk/SM this is exactly the FP32 peak of 256 flops/clk/SM.
 ALG_FLOPS_PER_EVAL = 8
+# One tcgen05.mma of the far-wing kernel: M = 128 points, N = 32 conditions, K = 8.
+MMA_FLOPS = 2 * 128 * 32 * 8
+# TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU).
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def parse():
@@ -293,6 +297,7 @@ def run_xc(args, dist, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     prof_ms, core_ms, sweep_ms, launches = [], [], [], 0
+    kern = []   # per step: (far-wing tensor ms, CUDA-core ms, centre-zone ms, MMA count)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -302,6 +307,7 @@ def run_xc(args, dist, rank, world, local):
             prof_ms.append(t["profile"])
             core_ms.append(t["ranges_or_core"])
             sweep_ms.append(t["params_or_sweep"])
+            kern.append(eng.sweep_kernels())
             launches += eng.last_launch_count()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -371,14 +377,32 @@ def run_xc(args, dist, rank, world, local):
     # the algorithmic eval count covers both
     prof = (statistics.mean(prof_ms) + (statistics.mean(core_ms) if core_ms else 0.0)) if prof_ms else None
     peak_max = nsm * 128 * 2 * 2070e6 / 1e12
-    rl = None
+    rl = sweep_rl = None
     if prof:
         ach = evals * ALG_FLOPS_PER_EVAL / (prof / 1e3) / 1e12
-        rl = {"bound": "alu", "achieved": ach, "peak": peak_max, "unit": "TFLOP/s", "frac": ach / peak_max,
-              "traffic": None, "kernel": "k_gather_f32 + k_core_w4_f32 (FP32 profile kernels; CUDA events inside the graph)",
-              "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-              "frac_at_sampled_clock": (ach / (nsm * 128 * 2 * sm_mhz * 1e6 / 1e12)) if sm_mhz else None,
-              "flops_per_eval": ALG_FLOPS_PER_EVAL, "kernel_ms": prof}
+        sweep_rl = {"bound": "alu", "achieved": ach, "peak": peak_max, "unit": "TFLOP/s", "frac": ach / peak_max,
+                    "traffic": None,
+                    "kernel": "all profile kernels of the sweep (CUDA events inside the graph), algorithmic flops",
+                    "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                    "frac_at_sampled_clock": (ach / (nsm * 128 * 2 * sm_mhz * 1e6 / 1e12)) if sm_mhz else None,
+                    "flops_per_eval": ALG_FLOPS_PER_EVAL, "kernel_ms": prof}
+        rl = sweep_rl
+    per_kernel = None
+    if kern and kern[0][3] > 0:
+        far_ms = statistics.mean(k[0] for k in kern)
+        main_ms = statistics.mean(k[1] for k in kern)
+        cz_ms = statistics.mean(k[2] for k in kern)
+        mma = kern[-1][3]
+        per_kernel = {"k_far_tc": far_ms, "k_gather_f32": main_ms, "k_core_w4_f32": cz_ms, "mma_per_launch": mma}
+        pk, basis = peaks()
+        tf32_peak = pk["bf16_tflops"] * TF32_PER_BF16
+        ach = mma * MMA_FLOPS / (far_ms / 1e3) / 1e12
+        dominant = max(per_kernel, key=lambda k: per_kernel[k] if k != "mma_per_launch" else -1)
+        rl = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
+              "traffic": None, "kernel": "k_far_tc (tcgen05.mma kind::tf32, far wings)",
+              "peak_basis": f"TF32 dense = {basis} BF16 burst {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal ratio)",
+              "flops": "executed MMA flops: MMAs per launch x 2 x 128 x 32 x 8", "kernel_ms": far_ms,
+              "dominant_kernel_of_sweep": dominant}
     cpu = None
     if not args.no_cpu:
         cpu = cpu_oracle_rate(W, lines, E, g, conds_py)
@@ -387,12 +411,14 @@ def run_xc(args, dist, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(W, n, nc), evals_per_step=evals, generation_s=round(t_gen, 1)),
-        "e2e": e2e, "roofline": rl, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
+        "e2e": e2e, "roofline": rl, "roofline_sweep_alu": sweep_rl if rl is not sweep_rl else None,
+        "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "stage_ms": {"sort": sort_t["sort"], "gather": sort_t["gather"],
                      "main_kernel_mean": statistics.mean(prof_ms) if prof_ms else None,
                      "centre_zone_kernel_mean": statistics.mean(core_ms) if core_ms else None,
                      "profile_kernels_mean": prof,
-                     "sweep_mean": statistics.mean(sweep_ms) if sweep_ms else None},
+                     "sweep_mean": statistics.mean(sweep_ms) if sweep_ms else None,
+                     "per_kernel_mean": per_kernel},
         "tuning": eng.tuning(),
     }
     if extras:

@@ -261,6 +261,13 @@ xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len);
 /* Kernel launches issued by the last call (for launch accounting). */
 xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out);
 
+/* Per-kernel times (ms, CUDA events; needs xc_set_timing(h, 1)) of the last FP32
+ * batched call with a fixed cut: ms_out[0] the tensor-core far-wing kernel, ms_out[1]
+ * the CUDA-core profile kernel, ms_out[2] the Voigt w4 centre-zone kernel; -1 where a
+ * kernel did not run or was not timed.  *mma_out: tcgen05.mma instructions (M = 128,
+ * N = 32, K = 8, kind::tf32) the tensor-core kernel issued, 0 if it did not run. */
+xc_status xc_last_sweep_kernels(xc_handle *h, double *ms_out, int64_t *mma_out);
+
 /* Fix the tile shape of the FP32 CUDA-core kernel for later batched calls on this
  * handle: R grid points per thread and CG conditions per tile, one of the compiled
  * shapes of the profile (R in {2, 4, 8}; CG in {1, 2, 4, 8, 16, 32}); (0, 0) restores

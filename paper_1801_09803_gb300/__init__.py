@@ -31,6 +31,7 @@ EXPORTED_SYMBOLS = [
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
     "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static", "xc_set_tile_shape",
+    "xc_last_sweep_kernels",
 ]
 
 
@@ -96,6 +97,7 @@ def lib(build_if_missing: bool = False):
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
         "xc_get_tuning": ([vp, C.c_char_p, st], i),
         "xc_set_tile_shape": ([vp, i, i], i),
+        "xc_last_sweep_kernels": ([vp, vp, C.POINTER(C.c_int64)], i),
         "xc_cross_section_batched_static": ([C.POINTER(XcLines), st, vp, vp, st, C.POINTER(XcCondition), st,
                                              C.POINTER(XcGrid), C.POINTER(XcOpts), vp, vp], i),
     }
@@ -327,6 +329,14 @@ class Engine:
         """Fix the FP32 CUDA-core kernel's tile shape (R points per thread, CG conditions
         per tile); (0, 0) returns to the autotuner."""
         _check(lib().xc_set_tile_shape(self._h, int(R), int(CG)))
+
+    def sweep_kernels(self):
+        """(far-wing tensor-core ms, CUDA-core kernel ms, centre-zone ms, MMA count) of the
+        last timed FP32 batched call; -1 for a kernel that did not run."""
+        ms = (C.c_double * 3)()
+        mma = C.c_int64()
+        _check(lib().xc_last_sweep_kernels(self._h, ms, C.byref(mma)))
+        return ms[0], ms[1], ms[2], int(mma.value)
 
     def tuning(self) -> str:
         buf = C.create_string_buffer(4096)

@@ -63,6 +63,8 @@ struct xc_handle {
     bool timing = false;
     cudaEvent_t ev[2 * ST_COUNT + 4] = {};
     float last_ms[ST_COUNT] = {};
+    double kernel_ms[3] = {-1.0, -1.0, -1.0};   // last FP32 sweep: far-wing (tensor), main, centre zone
+    int64_t tc_mma = 0;
     int64_t launches = 0;
     BatchedState batched;
 };
@@ -660,6 +662,7 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         a.ev_main0 = h->ev[2 * ST_PROFILE];         // main kernel
         a.ev_main1 = h->ev[2 * ST_PROFILE + 1];
         a.ev_core1 = h->ev[2 * ST_RANGES + 1];      // centre-zone kernel: main end -> core end
+        a.ev_tc1 = h->ev[2 * ST_COUNT];             // tensor-core far-wing kernel: main start -> here
         if (opts->profile == XC_VOIGT_GH_BINNED || opts->profile == XC_VOIGT_GH_SAMPLED) {
             if ((st = ensure_gh(h, opts->n_gh, s))) return st;
             a.ghx = h->gh.as<double>();
@@ -686,6 +689,18 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         if (opts->profile == XC_VOIGT_W4 &&
             cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE + 1], h->ev[2 * ST_RANGES + 1]) == cudaSuccess)
             h->last_ms[ST_RANGES] = ms;
+        // per kernel: far wings on the tensor cores (if they ran), CUDA-core kernel, centre zone
+        h->tc_mma = batched_tc_mma_count(&h->batched);
+        h->kernel_ms[0] = h->kernel_ms[1] = h->kernel_ms[2] = -1.0;
+        if (h->tc_mma > 0) {
+            if (cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE], h->ev[2 * ST_COUNT]) == cudaSuccess)
+                h->kernel_ms[0] = ms;
+            if (cudaEventElapsedTime(&ms, h->ev[2 * ST_COUNT], h->ev[2 * ST_PROFILE + 1]) == cudaSuccess)
+                h->kernel_ms[1] = ms;
+        } else {
+            h->kernel_ms[1] = h->last_ms[ST_PROFILE];
+        }
+        if (opts->profile == XC_VOIGT_W4) h->kernel_ms[2] = h->last_ms[ST_RANGES];
         cudaGetLastError();
     }
     return XC_OK;
@@ -760,6 +775,15 @@ xc_status xc_get_tuning(xc_handle *h, char *buf, size_t len) {
     if (st) return st;
     if (!buf || !len) { set_error("NULL buffer"); return XC_EINVAL; }
     snprintf(buf, len, "%s", h->batched.last_tuning.c_str());
+    return XC_OK;
+}
+
+xc_status xc_last_sweep_kernels(xc_handle *h, double *ms_out, int64_t *mma_out) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (!ms_out || !mma_out) { set_error("NULL out"); return XC_EINVAL; }
+    for (int i = 0; i < 3; ++i) ms_out[i] = h->kernel_ms[i];
+    *mma_out = h->tc_mma;
     return XC_OK;
 }
 

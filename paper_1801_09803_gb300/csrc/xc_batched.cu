@@ -1600,6 +1600,10 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->blk_hi = (unsigned *)(b + o_bhi);
         pl->tc_counter = (int *)(b + o_tcc);
         pl->tc_status = pl->tc_counter + 1;
+        st->tc_blk_lo = pl->blk_lo;
+        st->tc_blk_hi = pl->blk_hi;
+        st->tc_n_blk = pl->n_blk;
+        st->tc_groups = (n_cond_call + TC_N - 1) / TC_N;
         pl->tc_geo = (float4 *)(b + o_geo);
         pl->tc_phys = (float4 *)(b + o_phys);
         st->tc_status = pl->tc_status;
@@ -1680,6 +1684,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.inv_h = gp.inv_h;
         tp.sigma = gp.sigma;
         k_far_tc<<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
+        if (ev && a.ev_tc1) BT_TRY(cudaEventRecordWithFlags(a.ev_tc1, s, cudaEventRecordExternal));
         *launches += 2;
     }
     pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
@@ -1907,6 +1912,8 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     // the status word lives in the plan's scratch, which a later plan may reallocate:
     // it is valid only for the run that set it
     st->tc_status = nullptr;
+    st->tc_blk_lo = st->tc_blk_hi = nullptr;
+    st->tc_n_blk = st->tc_groups = 0;
     if (a.n_lines == 0 || a.n_cond == 0 || a.grid.n == 0) return XC_OK;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1986,6 +1993,20 @@ xc_status batched_check(BatchedState *st) {
         return XC_ETIMEOUT;
     }
     return XC_OK;
+}
+
+int64_t batched_tc_mma_count(BatchedState *st) {
+    if (!st->tc_blk_lo || st->tc_n_blk <= 0) return 0;
+    std::vector<unsigned> lo(st->tc_n_blk), hi(st->tc_n_blk);
+    if (cudaMemcpy(lo.data(), st->tc_blk_lo, lo.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hi.data(), st->tc_blk_hi, hi.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    int64_t chunks = 0;
+    for (int i = 0; i < st->tc_n_blk; ++i) chunks += (int64_t)((hi[i] - lo[i] + TC_L - 1) / TC_L);
+    // per chunk and 128-point block: 8 MMAs (M = 128, N = 32, K = 8)
+    return chunks * st->tc_groups * TC_BLK * 8;
 }
 
 void batched_invalidate(BatchedState *st) {

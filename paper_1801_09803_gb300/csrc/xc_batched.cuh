@@ -24,6 +24,7 @@ struct BatchedArgs {
     // with timing: events recorded (as graph event nodes when captured) before the main
     // kernel, after it, and after the centre-zone kernel
     cudaEvent_t ev_main0 = nullptr, ev_main1 = nullptr, ev_core1 = nullptr;
+    cudaEvent_t ev_tc1 = nullptr;            // after the tensor-core far-wing kernel (when it runs)
     const double *ghx = nullptr, *ghw = nullptr;  // device Gauss-Hermite nodes/weights
     bool allow_tc = true;                   // far wings may use the tensor-core kernel
 };
@@ -70,6 +71,9 @@ struct BatchedState {
     std::map<std::string, std::string> tune_log; // shape key -> candidate predictions
     std::string last_tuning;                     // description of the last batched configuration
     int *tc_status = nullptr;                    // device word: a tensor-core wait ran out
+    // the last run's tensor-core work: super-block line ranges (device) and shape
+    const unsigned *tc_blk_lo = nullptr, *tc_blk_hi = nullptr;
+    int tc_n_blk = 0, tc_groups = 0;
     int force_R = 0, force_CG = 0;               // fixed CUDA-core tile shape (0: autotune)
 };
 
@@ -78,6 +82,9 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches);
 // after the stream has synchronised: XC_ETIMEOUT if the tensor-core kernel reported a
 // wait that ran out (its results are then not valid), else XC_OK
 xc_status batched_check(BatchedState *st);
+// after the stream has synchronised: tcgen05.mma instructions the last run's tensor-core
+// kernel issued (0 if it did not run), from its super-block line ranges
+int64_t batched_tc_mma_count(BatchedState *st);
 void batched_invalidate(BatchedState *st);
 void batched_release(BatchedState *st);
 
