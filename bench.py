@@ -39,6 +39,11 @@ ALG_FLOPS_PER_EVAL = 8
 MMA_FLOPS = 2 * 128 * 32 * 8
 # TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU).
 TF32_PER_BF16 = 1.1 / 2.25
+# DRAM bytes of one k_far_tc launch from one ncu capture on the C3 generator at 1e6
+# lines (profiles/k_far_tc_c3_1e6lines_32cond.md): reads grow with the line count,
+# writes are the 32-condition output; scaled to the bench's line count.
+TC_DRAM_READ_PER_LINE = 36.65e6 / 1e6
+TC_DRAM_WRITE_1M_PTS_32C = 197.6e6
 
 
 def parse():
@@ -398,8 +403,14 @@ def run_xc(args, dist, rank, world, local):
         tf32_peak = pk["bf16_tflops"] * TF32_PER_BF16
         ach = mma * MMA_FLOPS / (far_ms / 1e3) / 1e12
         dominant = max(per_kernel, key=lambda k: per_kernel[k] if k != "mma_per_launch" else -1)
+        traffic = None
+        if args.workload == "C3" and not args.profile:
+            traffic = TC_DRAM_READ_PER_LINE * n + TC_DRAM_WRITE_1M_PTS_32C * (nc / 32) * (W.n_points / 1e6)
         rl = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-              "traffic": None, "kernel": "k_far_tc (tcgen05.mma kind::tf32, far wings)",
+              "traffic": traffic,
+              "traffic_basis": "dram read + write bytes per launch from one ncu capture at 1e6 lines, read part "
+                               "scaled by the line count (profiles/k_far_tc_c3_1e6lines_32cond.md)",
+              "kernel": "k_far_tc (tcgen05.mma kind::tf32, far wings)",
               "peak_basis": f"TF32 dense = {basis} BF16 burst {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal ratio)",
               "flops": "executed MMA flops: MMAs per launch x 2 x 128 x 32 x 8", "kernel_ms": far_ms,
               "dominant_kernel_of_sweep": dominant}
