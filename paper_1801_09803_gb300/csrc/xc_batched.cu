@@ -61,12 +61,15 @@ struct CParam {
     float pscale;       // gamma_scale * P / P_ref
     float nshift;
     int row;            // output row (the caller's condition index)
-    float pad;
+    float dbound;       // upper bound of the far radius D4 over all lines (grid steps)
 };
 
 struct GeomStats {
     unsigned int gA_nu2_bits;  // max g A / nu^2 (float bits; values >= 0)
     unsigned int gA_nu_bits;   // max g A / nu
+    unsigned int nu_bits;      // max nu (float, rounded up)
+    unsigned int gref_bits;    // max |gamma_ref|
+    unsigned int nT_bits;      // max |n_T|
 };
 
 struct GatherParams {
@@ -158,7 +161,7 @@ __device__ double cond_width_key(const CondDev &d) {
 
 // Per-condition constants, stored in order of increasing profile width (stable), so that
 // the conditions sharing a tile have similar far-wing radii; row keeps the caller's index.
-__global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp) {
+__global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp, double step) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cond) return;
     const CondDev d = conds[c];
@@ -193,8 +196,49 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
     p.pscale = (float)(d.gamma_scale * d.P / d.P_ref);
     p.nshift = (float)d.n_shift;
     p.row = c;
-    p.pad = 0.f;
+    {
+        // D4 <= ceil(sqrt(max(C k4, t2))) + 1 grows with both widths; t2 <= (15 a_h / sqrt ln2)^2.
+        // Upper bounds of the widths from the line statistics (|n| <= nT_max), with margin.
+        const double num = (double)__uint_as_float(gs->nu_bits);
+        const double grm = (double)__uint_as_float(gs->gref_bits);
+        const double ntm = (double)__uint_as_float(gs->nT_bits);
+        const double lr = log(d.T_ref / d.T);
+        const double tf = fmax(exp((ntm + d.n_shift) * lr), exp((-ntm + d.n_shift) * lr));
+        const double ah = alpha_coef(d.T, d.mass_da) * num / step;
+        const double gh = fabs(d.gamma_scale * d.P / d.P_ref) * grm * tf / step;
+        const double C = ah * ah * (0.5 / 0.6931471805599453) + gh * gh;
+        const double t2 = 225.0 * ah * ah / 0.6931471805599453;
+        const double uf = fmax(C * (1.0 / 0.012), t2);
+        const double db = ceil(sqrt(uf) * 1.001) + 3.0;
+        p.dbound = (isfinite(db) && db < 1e9) ? (float)db : 1e9f;
+    }
     cp[rank] = p;
+}
+
+// (window, condition-group) tile -> line range for the CUDA-core kernel when the
+// tensor-core kernel takes the far wings: only lines within the group's largest far
+// radius of the window (or within the cut, if that is smaller) have work there
+__global__ void k_win_ranges_near(const double *__restrict__ nu, int64_t n, double nu_A, double step,
+                                  int64_t n_pts, int W, double cutoff, int n_win, int n_groups, int CG,
+                                  const CParam *cp, int n_cond, unsigned *lo, unsigned *hi) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_win * n_groups) return;
+    const int w = t / n_groups, g = t % n_groups;
+    float db = 0.f;
+    for (int c = g * CG; c < min(n_cond, (g + 1) * CG); ++c) db = fmaxf(db, cp[c].dbound);
+    const double cutmax = fmin(cutoff, ((double)db + 2.0) * step);
+    int64_t k0 = (int64_t)w * W;
+    int64_t k1 = i64min(k0 + W, n_pts) - 1;
+    double x0 = grid_x(nu_A, step, k0), x1 = grid_x(nu_A, step, k1);
+    double margin = cutmax * (1.0 + 1e-12) + 1e-12 * (fabs(x0) + fabs(x1)) + 1e-300;
+    int64_t a = 0, b = n;
+    double x = x0 - margin;
+    while (a < b) { int64_t m = a + ((b - a) >> 1); if (nu[m] < x) a = m + 1; else b = m; }
+    lo[t] = (unsigned)a;
+    int64_t a2 = a, b2 = n;
+    x = x1 + margin;
+    while (a2 < b2) { int64_t m = a2 + ((b2 - a2) >> 1); if (nu[m] <= x) a2 = m + 1; else b2 = m; }
+    hi[t] = (unsigned)a2;
 }
 
 // ---------------------------------------------------------------------------
@@ -205,9 +249,12 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
                             double width_mult, const CondDev *cond, int *n_abs, float *f_frac, int *ka_abs,
                             int *kb_abs, GeomStats *gs, float4 *tc_geo, float4 *tc_phys) {
     const double inv_h = 1.0 / step;
-    float m1 = 0.f, m2 = 0.f;
+    float m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
         double nu = L.nu[l];
+        m3 = fmaxf(m3, __double2float_ru(fabs(nu)));
+        m4 = fmaxf(m4, fabsf(L.gamma_ref[l]));
+        m5 = fmaxf(m5, fabsf(L.n_T[l]));
         double cut = cutoff;
         if (width_mult > 0.0 && cond) {
             const CondDev c = *cond;
@@ -240,10 +287,16 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
         m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, o));
+        m4 = fmaxf(m4, __shfl_xor_sync(0xffffffffu, m4, o));
+        m5 = fmaxf(m5, __shfl_xor_sync(0xffffffffu, m5, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (isfinite(m1)) atomicMax(&gs->gA_nu2_bits, __float_as_uint(m1));
         if (isfinite(m2)) atomicMax(&gs->gA_nu_bits, __float_as_uint(m2));
+        atomicMax(&gs->nu_bits, __float_as_uint(m3));   // non-negative floats: integer order
+        atomicMax(&gs->gref_bits, __float_as_uint(m4));
+        atomicMax(&gs->nT_bits, __float_as_uint(m5));
     }
 }
 
@@ -268,17 +321,19 @@ __global__ void k_win_ranges32(const double *__restrict__ nu, int64_t n, double 
 
 // rank tiles by decreasing cost (ties by index): order[rank] = tile
 __global__ void k_rank_tiles(const unsigned *lo, const unsigned *hi, int n_win, int n_groups, int n_tiles,
-                             int *order, bool do_rank) {
+                             int *order, bool do_rank, bool per_tile) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     if (!do_rank) {  // very many tiles: keep index order
         order[t] = t;
         return;
     }
-    unsigned ct = hi[t / n_groups] - lo[t / n_groups];
+    const int rt = per_tile ? t : t / n_groups;
+    unsigned ct = hi[rt] - lo[rt];
     int rank = 0;
     for (int u = 0; u < n_tiles; ++u) {
-        unsigned cu = hi[u / n_groups] - lo[u / n_groups];
+        const int ru = per_tile ? u : u / n_groups;
+        unsigned cu = hi[ru] - lo[ru];
         rank += (cu > ct) || (cu == ct && u < t);
     }
     order[rank] = t;
@@ -590,8 +645,8 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
         const int tile = p.tile_order[t];
         const int win = tile / p.n_groups, grp = tile % p.n_groups;
         const int64_t kw = (int64_t)win * W;
-        const unsigned lo = p.win_lo[win];
-        const unsigned hi = p.win_hi[win];
+        const unsigned lo = p.win_lo[p.tc_far ? tile : win];   // near mode: a range per tile
+        const unsigned hi = p.win_hi[p.tc_far ? tile : win];
         if (tid < CG) {
             int c = grp * CG + tid;
             sScale[tid] = c < p.n_cond ? p.cp[c].inv_scale : 0.0;
@@ -1535,7 +1590,7 @@ int num_sms(int dev) {
 // Everything the persistent kernel needs, carved out of the state's buffers.
 struct Plan {
     const Variant *v = nullptr;
-    int W = 0, n_win = 0, n_groups = 0, n_tiles = 0, grid = 0;
+    int W = 0, n_win = 0, n_groups = 0, n_tiles = 0, grid = 0, n_ranges = 0;
     int *n_abs = nullptr, *ka = nullptr, *kb = nullptr;
     float *f = nullptr;
     CParam *cp = nullptr;
@@ -1565,7 +1620,8 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     size_t o_n = carve(n * 4), o_f = carve(n * 4), o_ka = carve(n * 4), o_kb = carve(n * 4);
     size_t o_cp = carve((size_t)n_cond_call * sizeof(CParam));
-    size_t o_lo = carve((size_t)pl->n_win * 4), o_hi = carve((size_t)pl->n_win * 4);
+    pl->n_ranges = tc ? pl->n_tiles : pl->n_win;   // near mode: one line range per tile
+    size_t o_lo = carve((size_t)pl->n_ranges * 4), o_hi = carve((size_t)pl->n_ranges * 4);
     size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
     pl->n_win_core = (int)((a.grid.n + CORE_T - 1) / CORE_T);
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
@@ -1625,11 +1681,16 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
                                         per_cond_cut ? a.opts.width_mult : 0.0,
                                         per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
                                         pl.gs, pl.tc ? pl.tc_geo : nullptr, pl.tc ? pl.tc_phys : nullptr);
-    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp);
-    k_win_ranges32<<<(pl.n_win + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
-                                                           pl.W, a.opts.cutoff, pl.n_win, pl.lo, pl.hi);
+    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step);
+    if (pl.tc)
+        k_win_ranges_near<<<(pl.n_tiles + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step,
+                                                                  a.grid.n, pl.W, a.opts.cutoff, pl.n_win,
+                                                                  pl.n_groups, pl.v->CG, pl.cp, nc, pl.lo, pl.hi);
+    else
+        k_win_ranges32<<<(pl.n_win + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step,
+                                                               a.grid.n, pl.W, a.opts.cutoff, pl.n_win, pl.lo, pl.hi);
     k_rank_tiles<<<(pl.n_tiles + 127) / 128, 128, 0, s>>>(pl.lo, pl.hi, pl.n_win, pl.n_groups, pl.n_tiles,
-                                                          pl.order, pl.n_tiles <= 16384);
+                                                          pl.order, pl.n_tiles <= 16384, pl.tc);
     *launches += 4;
     if (a.ghx) {
         k_nodes_to_float<<<1, 64, 0, s>>>(a.ghx, a.ghw, a.opts.n_gh, pl.gx, pl.gw);
@@ -1862,11 +1923,11 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
             float ms = 0.f;
             BT_TRY(cudaEventElapsedTime(&ms, e0, e1));
             // measured: all tiles, <= probe_lines lines each. Predict for the full line count:
-            std::vector<unsigned> lo(pl.n_win), hi(pl.n_win);
-            BT_TRY(cudaMemcpy(lo.data(), pl.lo, pl.n_win * 4, cudaMemcpyDeviceToHost));
-            BT_TRY(cudaMemcpy(hi.data(), pl.hi, pl.n_win * 4, cudaMemcpyDeviceToHost));
+            std::vector<unsigned> lo(pl.n_ranges), hi(pl.n_ranges);
+            BT_TRY(cudaMemcpy(lo.data(), pl.lo, pl.n_ranges * 4, cudaMemcpyDeviceToHost));
+            BT_TRY(cudaMemcpy(hi.data(), pl.hi, pl.n_ranges * 4, cudaMemcpyDeviceToHost));
             double probe_max = 0.0, full_work = 0.0, max_tile = 0.0, probe_sum = 0.0;
-            for (int w = 0; w < pl.n_win; ++w) {
+            for (int w = 0; w < pl.n_ranges; ++w) {
                 double cntl = (double)(hi[w] - lo[w]);
                 double pc = std::min(cntl, (double)probe_lines);
                 probe_sum += pc;
@@ -1876,9 +1937,9 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
             }
             // time per tile-line for one slot, from waves x mean probe tile
             double waves = std::ceil((double)pl.n_tiles / grid);
-            double probe_avg = probe_sum / pl.n_win;
+            double probe_avg = probe_sum / pl.n_ranges;
             double t_line = (probe_avg > 0 && waves > 0) ? ms / (waves * probe_avg) : 0.0;
-            double avg_tile = full_work / pl.n_win;
+            double avg_tile = full_work / pl.n_ranges;
             double pred = t_line * std::max(waves * avg_tile, max_tile);
             {
                 char lb[160];
