@@ -1177,7 +1177,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     const uint32_t t_lane = tblk + ((uint32_t)((warp & 3) * 32) << 16);       // this warp's lanes
     constexpr uint32_t kIdesc = tc::idesc_tf32(128, TC_N);
     const uint32_t sB_addr = tc::smem_u32(sB);
-    const bool issuer = (tid & (TC_M - 1)) == 0;  // thread 0 of each block
+    // One MMA-issuing thread per block, in a warp of that block.  MMA issue from one
+    // SM sub-partition is serialised, so the two issuers sit on different sub-partitions
+    // (warp % 4), and CTAs of odd index use the other two (two CTAs share an SM).
+    const bool odd_cta = (blockIdx.x & 1) != 0;
+    const bool issuer = (tid & 31) == 0 && (warp == (odd_cta ? 2 : 0) || warp == (odd_cta ? 7 : 5));
     // descriptor of this block's B operand (buffer 0, hi); the whole region lies below
     // 256 KB, so the start field never carries into the next one
     const uint64_t desc_b0 = tc::smem_desc(sB_addr + (uint32_t)(blkh * 2 * TC_BT * TC_BTILE * 4), 128u, 256u);
