@@ -187,6 +187,36 @@ def cpu_oracle_rate(W, lines, E, g, conds, budget_s=12.0, threads=None):
                       f"full grid ({best[2]:.3g} evals in {best[3]:.1f} s)"}
 
 
+# Modelled HBM traffic of the line-list sort (bytes per line): key making (read nu 8 B,
+# write key 8 + index 4), one histogram pass over the keys (8), 8 LSD digit passes
+# (tile histogram 8 + scatter read 12 + write 12), gather (index 4 + 28 read + 28 write).
+SORT_BYTES_PER_LINE = 20 + 8 + 8 * 32 + 60
+# Standalone FP64 line parameters: read nu, E'', A, g', gamma_ref, n (26 B), write I, alpha, gamma (24 B).
+PARAMS_BYTES_PER_LINE = 26 + 24
+
+
+def hbm_stages(eng, xc, torch, dev, n, cond, sort_ms, gather_ms):
+    """The HBM-bound steps with their achieved bandwidth against the measured copy
+    peak: the device sort + gather of the line list (CUDA events of the load) and a
+    standalone FP64 line-parameter pass over the whole sorted list."""
+    pk, basis = peaks()
+    out = {"peak_gbs": pk["hbm_gbs"], "peak_basis": basis}
+    sb = SORT_BYTES_PER_LINE * n
+    out["sort_gather"] = {"ms": sort_ms + gather_ms, "modelled_bytes": sb,
+                          "gbs": sb / ((sort_ms + gather_ms) / 1e3) / 1e9,
+                          "frac": sb / ((sort_ms + gather_ms) / 1e3) / 1e9 / pk["hbm_gbs"],
+                          "model": "20 + 8 + 8 x 32 + 60 B per line (keys, histogram, 8 digit passes, gather)"}
+    I = torch.empty(n, dtype=torch.float64, device=dev)
+    a = torch.empty_like(I)
+    g = torch.empty_like(I)
+    ms = _timed(torch, lambda: eng.line_params_device(cond, I, a, g))
+    pb = PARAMS_BYTES_PER_LINE * n
+    out["line_params_fp64"] = {"ms": ms, "bytes": pb, "gbs": pb / (ms / 1e3) / 1e9,
+                               "frac": pb / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    del I, a, g
+    return out
+
+
 def run_reference(args, dist, rank, world):
     if rank != 0:
         return
@@ -417,12 +447,19 @@ def run_xc(args, dist, rank, world, local):
     cpu = None
     if not args.no_cpu:
         cpu = cpu_oracle_rate(W, lines, E, g, conds_py)
+        one = cpu_oracle_rate(W, lines, E, g, conds_py, budget_s=4.0, threads=1)
+        cpu["single_thread"] = {"value": one["value"], "unit": UNIT, "sample": one["sample"]}
+    hbm = None
+    if not args.no_extras:
+        eng.load_lines(dlines)
+        hbm = hbm_stages(eng, xc, torch, dev, n, conds[len(conds) // 2], sort_t["sort"], sort_t["gather"])
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(W, n, nc), evals_per_step=evals, generation_s=round(t_gen, 1)),
         "e2e": e2e, "roofline": rl, "roofline_sweep_alu": sweep_rl if rl is not sweep_rl else None,
+        "hbm_stages": hbm,
         "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches),
         "stage_ms": {"sort": sort_t["sort"], "gather": sort_t["gather"],
                      "main_kernel_mean": statistics.mean(prof_ms) if prof_ms else None,

@@ -266,6 +266,11 @@ class Engine:
                                     XC_MEM_HOST, None))
         return I, a, g
 
+    def line_params_device(self, cond: XcCondition, I, alpha, gamma):
+        """FP64 I, alpha_D, gamma_L of every (sorted) line into CUDA tensors of n_lines doubles."""
+        _check(lib().xc_line_params(self._h, C.byref(cond), I.data_ptr(), alpha.data_ptr(), gamma.data_ptr(),
+                                    XC_MEM_DEVICE, _stream_of(I)))
+
     def count_evals(self, conds: Sequence[XcCondition], grid: XcGrid, opts: XcOpts) -> int:
         arr = (XcCondition * len(conds))(*conds)
         out = C.c_int64()

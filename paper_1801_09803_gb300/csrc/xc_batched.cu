@@ -1072,10 +1072,12 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
 // precision follows each term's weight (four terms, x = C r <= 0.012): for j = 0 (the
 // value itself) and j = 1 (<= 3x = 0.036 of it) r^(j+1) and p_j are split x = hi + lo
 // with hi exact in TF32, D += Ahi Bhi + Ahi Blo + Alo Bhi (the dropped Alo Blo is
-// < 2^-21 of the product); the j = 2 term (<= 5x^2 = 7e-4 of the value) takes r^3 and
-// p2 rounded to TF32 (< 2e-7), the j = 3 term (<= 7x^3 = 1.3e-5) r^4 and p3 as the MMA
-// reads them.  Eight MMAs per chunk and block.  A and B are double buffered (the next
-// chunk is built while the MMAs of this one run).  The tensor
+// < 2^-20 of the product; hi is x with its low 13 mantissa bits cleared, a bias
+// toward zero below 5e-7); the j = 2 term (<= 5x^2 = 7e-4 of the value) and the j = 3
+// term (<= 7x^3 = 1.3e-5) take r^3, r^4, p2, p3 as the MMA reads them (TF32: relative
+// error <= 2^-10 of a term that small, < 7e-7).  Eight MMAs per chunk and block.  A
+// and B are double buffered (the next chunk is built while the MMAs of this one run).
+// The tensor
 // core adds in FP32 with truncation, a bias that grows with the number of MMAs
 // summed into one accumulator, so D is restarted every TC_FOLD chunks after its
 // value is added into compensated (Kahan) FP32 sums in shared memory; the blocks
@@ -1263,8 +1265,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     na = g.x;
                     S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3);
                 }
-                const float p0h = tc::tf32_hi(S.x), p1h = tc::tf32_hi(S.y), p2h = tc::tf32_hi(S.z);
-                const float p0l = S.x - p0h, p1l = S.y - p1h;
+                const float p0h = tc::tf32_trunc(S.x), p1h = tc::tf32_trunc(S.y);
+                const float p0l = S.x - p0h, p1l = S.y - p1h, p2h = S.z;
 #pragma unroll
                 for (int hb = 0; hb < TC_BLK; ++hb) {
                     const int b0 = t0 + hb * TC_M;
@@ -1294,13 +1296,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                         // meet zero B entries (not far), r is kept finite there
                         r = (l0 + l8 < nl && kf >= g.z && kf <= g.w) ? rcp_approx(fmaxf(d * d, 1.f)) : 0.f;
                     }
-                    const float r2 = r * r, r3 = r2 * r;
-                    const float rh = tc::tf32_hi(r), r2h = tc::tf32_hi(r2);
+                    const float r2 = r * r;
+                    const float rh = tc::tf32_trunc(r), r2h = tc::tf32_trunc(r2);
                     av[l8] = rh;
                     av[TC_L + l8] = r - rh;
                     av[2 * TC_L + l8] = r2h;
                     av[3 * TC_L + l8] = r2 - r2h;
-                    av[4 * TC_L + l8] = tc::tf32_hi(r3);
+                    av[4 * TC_L + l8] = r2 * r;    // the MMA reads r^3, r^4, p2, p3 as TF32
                     av[5 * TC_L + l8] = r2 * r2;
                 }
                 const uint32_t ta = t_lane + 32u + (uint32_t)b * TC_ACOLS;

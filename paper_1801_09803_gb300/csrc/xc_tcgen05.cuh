@@ -112,6 +112,12 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(r);
 }
 
+// hi = x with the 13 low mantissa bits cleared (exact in TF32; one logic op), for
+// splits x = hi + lo whose lo enters the product too
+__device__ __forceinline__ float tf32_trunc(float x) {
+    return __int_as_float(__float_as_int(x) & (int)0xffffe000);
+}
+
 // the same split on the FMA pipe (Veltkamp): hi keeps the leading 11 significant bits
 // (exact in TF32), lo = x - hi exactly; for |x| < 2^100
 __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
