@@ -1269,8 +1269,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                 const float p0l = S.x - p0h, p1l = S.y - p1h, p2h = S.z;
 #pragma unroll
                 for (int hb = 0; hb < TC_BLK; ++hb) {
-                    const int b0 = t0 + hb * TC_M;
-                    const bool far = live && span_far((int)na, S.w, b0, b0 + TC_M - 1);
+                    // span_far in float: na and the block ends are exact integers below 2^24,
+                    // so the differences are exact and the test is the same
+                    const float b0 = (float)(t0 + hb * TC_M);
+                    const bool far = live && ((na - (b0 + (float)(TC_M - 1)) > S.w) || (b0 - na > S.w));
                     float *bt = sB + (size_t)(hb * 2 + b) * TC_BT * TC_BTILE + bix;
                     bt[0 * TC_BTILE] = far ? p0h : 0.f;
                     bt[1 * TC_BTILE] = far ? p0l : 0.f;
@@ -1493,7 +1495,24 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             }
         }
         __syncthreads();
-        for (int i = 0; i < cnt; ++i) {
+        // the chunk's lines whose widest centre zone can reach this warp's 32 points
+        unsigned wl = 0;
+        {
+            bool hit = false;
+            if (lane < cnt) {
+                const int4 m = sMi[lane];
+                const float2 mf = sMf[lane];
+                if (mf.y > 0.f) {
+                    const float cpos = (float)m.x + mf.x, thr = sqrtf(mf.y) + 2.f;
+                    const float w0 = (float)(tid - lane), w1 = w0 + 31.f;
+                    hit = cpos + thr >= w0 && cpos - thr <= w1 && m.y <= (int)w1 && m.z >= (int)w0;
+                }
+            }
+            wl = __ballot_sync(0xffffffffu, hit);
+        }
+        while (wl) {
+            const int i = __ffs(wl) - 1;
+            wl &= wl - 1;
             const int4 m = sMi[i];
             const float2 mf = sMf[i];
             const float d = (jf - (float)m.x) - mf.x;
