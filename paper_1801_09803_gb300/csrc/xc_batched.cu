@@ -1413,6 +1413,27 @@ struct CoreParams {
     double *sigma;
 };
 
+// Re w in w4's regions III and IV (|x| + y < 5.5), the same forms as w4_eval with only
+// the real part formed: region III the real part of the quotient; region IV needs
+// cos(Im u) of exp(u), u = t^2, and no sine
+__device__ __forceinline__ float w4_region34_re(float x, float y) {
+    const Cx<float> t = cx<float>(y, -x);
+    const float ax = fabsf(x);
+    if (y >= 0.195f * ax - 0.176f) {
+        const Cx<float> N = 16.4955f + t * (20.20933f + t * (11.96482f + t * (3.778987f + 0.5642236f * t)));
+        const Cx<float> D = 16.4955f + t * (38.82363f + t * (39.27121f + t * (21.69274f + t * (6.699398f + t))));
+        return (N.re * D.re + N.im * D.im) * recip(D.re * D.re + D.im * D.im);
+    }
+    const Cx<float> u = t * t;
+    const Cx<float> m = cx<float>(-u.re, -u.im);
+    const Cx<float> N = 36183.31f + m * (3321.9905f + m * (1540.787f + m * (219.0313f +
+                        m * (35.76683f + m * (1.320522f + 0.56419f * m)))));
+    const Cx<float> D = 32066.6f + m * (24322.84f + m * (9022.228f + m * (2186.181f +
+                        m * (364.2191f + m * (61.57037f + m * (1.841439f + m))))));
+    const Cx<float> r = cdiv(N, D);
+    return expf(u.re) * cosf(u.im) - (t.re * r.re - t.im * r.im);
+}
+
 // Re w in w4's region I from (x, y): 0.5641896 y (0.5 + X + Y) / ((X + Y - 0.5)^2 + 2Y)
 __device__ __forceinline__ float w4_region1_re(float x, float y) {
     float X = x * x, Y = y * y;
@@ -1526,7 +1547,7 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
                 const float4 B = sB[i][c];
                 float x = B.x * ad, y = B.y, s = x + y;
                 float w = s >= 15.f ? w4_region1_re(x, y)
-                                    : (s >= 5.5f ? w4_region2_re(x, y) : w4_eval<float>(x, y, nullptr).re);
+                                    : (s >= 5.5f ? w4_region2_re(x, y) : w4_region34_re(x, y));
                 sAcc[c][tid] = fmaf(B.z, w, sAcc[c][tid]);
             }
         }
