@@ -84,6 +84,19 @@ __device__ inline float w4_re_grad_12(float x, float y, float *dx, float *dy) {
     return y * S;
 }
 
+// compensated FP32 sum (Kahan): the running compensation keeps the rounding of every
+// addition, so the sum is good to a few FP32 ulps of its terms whatever its length
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // value and derivatives of the profile (FP64 reference form, all w4 regions)
 template <int PROF>
 __device__ inline void prof_deriv64(double D, double al, double ga, double *V, double *dVa, double *dVg) {
@@ -158,13 +171,15 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                 const float yv = a_sc * gaf;
                 const float thr = yv < 15.f ? (15.f - yv) / a_sc : -1.f;  // region I iff |D| >= thr
                 const float thr2 = thr > 0.f ? thr * thr : -1.f;
-                // FP32 terms summed 8 at a time, folded into FP64; centre points (w4 regions
-                // II-IV), which carry the largest terms of sums that cancel (the derivatives of
-                // a unit-area profile integrate to zero), are evaluated in FP64.
-                double S0 = 0.0, S1 = 0.0, S2 = 0.0, C0 = 0.0, C1 = 0.0, C2 = 0.0;
+                // FP32 terms in compensated (Kahan) FP32 sums: as accurate as folding them into
+                // FP64 and free of FP64 instructions, which run at a small fraction of the FP32
+                // rate on this GPU.  Centre points of w4 regions III/IV, which carry the largest
+                // terms of sums that cancel (the derivatives of a unit-area profile integrate to
+                // zero), are evaluated and added in FP64.
+                double C0 = 0.0, C1 = 0.0, C2 = 0.0;
+                KahanF s0, s1, s2, c0, c1, c2;
                 const float *gc = g32 + (size_t)c * n_pts;
                 for (int64_t kb8 = ka + lane; kb8 <= kb; kb8 += 32 * 8) {
-                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll 4
                     for (int j = 0; j < 8; ++j) {
                         const int64_t k = kb8 + 32 * j;
@@ -179,10 +194,10 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                                 float N = u + bg;
                                 float rD = 1.f / Dn;
                                 float rD2 = rD * rD;
-                                s0 = fmaf(g, N * rD, s0);
-                                s1 = fmaf(g, fmaf(-2.f * N, t, Dn) * rD2, s1);
+                                s0.add(g * (N * rD));
+                                s1.add(g * (fmaf(-2.f * N, t, Dn) * rD2));
                                 float q = fmaf(Dn, N + 2.f * g2, -4.f * g2 * N * N);
-                                s2 = fmaf(g, q * rD2, s2);
+                                s2.add(g * (q * rD2));
                             } else if (a_sc * fabsf(D) + yv >= 5.5f) {
                                 // region II (or I by rounding at its edge): real form, FP32
                                 float rx, ry;
@@ -190,9 +205,9 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                                 float v = (float)0.46971863934982566 / alf * w;
                                 float k2 = (float)(0.6931471805599453 / 1.772453850905516027) / (alf * alf);
                                 float dVD = k2 * (D < 0.f ? -rx : rx), dg = k2 * ry;
-                                c0 = fmaf(g, v, c0);
-                                c1 = fmaf(g, -(v + D * dVD + gaf * dg) / alf, c1);
-                                c2 = fmaf(g, dg, c2);
+                                c0.add(g * v);
+                                c1.add(g * (-(v + D * dVD + gaf * dg) / alf));
+                                c2.add(g * dg);
                             } else {
                                 // regions III/IV: complex rationals whose derivative cancels in
                                 // FP32; evaluated in FP64 (a narrow band around the centre)
@@ -206,17 +221,19 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
                             }
                         } else if (PROF == XC_DOPPLER) {
                             float e = expf(-(float)kLn2 * u / (alf * alf));
-                            c0 = fmaf(g, e, c0);
-                            c1 = fmaf(g, e * u, c1);
+                            c0.add(g * e);
+                            c1.add(g * (e * u));
                         } else {
                             float r = 1.f / (u + g2);
-                            c0 = fmaf(g, r, c0);
-                            c2 = fmaf(g, (u - g2) * r * r, c2);
+                            c0.add(g * r);
+                            c2.add(g * ((u - g2) * r * r));
                         }
                     }
-                    S0 += s0; S1 += s1; S2 += s2;
-                    C0 += c0; C1 += c1; C2 += c2;
                 }
+                const double S0 = s0.value(), S1 = s1.value(), S2 = s2.value();
+                C0 += c0.value();
+                C1 += c1.value();
+                C2 += c2.value();
                 if (PROF == XC_VOIGT_W4) {
                     double kg = kKappa64 * ga;
                     SI = kg * S0 + C0;
