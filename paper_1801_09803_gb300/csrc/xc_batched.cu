@@ -227,8 +227,13 @@ __global__ void k_win_ranges_near(const double *__restrict__ nu, int64_t n, doub
     float db = 0.f;
     for (int c = g * CG; c < min(n_cond, (g + 1) * CG); ++c) db = fmaxf(db, cp[c].dbound);
     const double cutmax = fmin(cutoff, ((double)db + 2.0) * step);
+    // the nominal window, also past the last grid point: both kernels test far-ness on
+    // whole nominal 128-point blocks, so a line within its radius of a block's nominal
+    // end but farther from the last grid point is left out by the far-wing kernel and
+    // must be staged here (its far wing still reaches the grid)
     int64_t k0 = (int64_t)w * W;
-    int64_t k1 = i64min(k0 + W, n_pts) - 1;
+    int64_t k1 = k0 + W - 1;
+    (void)n_pts;
     double x0 = grid_x(nu_A, step, k0), x1 = grid_x(nu_A, step, k1);
     double margin = cutmax * (1.0 + 1e-12) + 1e-12 * (fabs(x0) + fabs(x1)) + 1e-300;
     int64_t a = 0, b = n;
@@ -1106,7 +1111,8 @@ __device__ __forceinline__ bool tc_line_plain(const float4 &g, int t0) {
     return g.z <= (float)t0 && g.w >= (float)(t0 + TC_T - 1) &&
            (g.x <= (float)(t0 - 2) || g.x >= (float)(t0 + TC_T + 1));
 }
-static_assert(TC_N * TC_L == TC_T, "one (line, condition) pair per thread and chunk");
+constexpr int TC_NB = TC_N * TC_L;        // (line, condition) pairs per chunk
+static_assert(TC_NB == TC_T, "one (line, condition) pair per thread and chunk");
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 struct TcParams {
@@ -1182,6 +1188,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     // One MMA-issuing thread per block, in a warp of that block.  MMA issue from one
     // SM sub-partition is serialised, so the two issuers sit on different sub-partitions
     // (warp % 4), and CTAs of odd index use the other two (two CTAs share an SM).
+    // (One CTA of four blocks and four issuers per SM measured slower.)
     const bool odd_cta = (blockIdx.x & 1) != 0;
     const bool issuer = (tid & 31) == 0 && (warp == (odd_cta ? 2 : 0) || warp == (odd_cta ? 7 : 5));
     // descriptor of this block's B operand (buffer 0, hi); the whole region lies below

@@ -198,6 +198,45 @@ def test_batched_conditions(eng, xc, oracle_lib, precision):
     assert worst[0] < tol[0] and worst[1] < tol[1]
 
 
+def test_tensor_core_partition_on_offset_grid(eng, xc, oracle_lib):
+    """The integer far tests, block ranges and line records on a grid that starts
+    between line positions and has a step that is not a power of ten (the far/near/
+    centre-zone partition must still count every pair once), 24 conditions, and the
+    per-kernel statistics of the timed sweep."""
+    L = xs.gen_lines(112, 0, 15000, 900.0, 1100.0)
+    E, g = xs.gen_states(112, 3000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    base = xs.conditions_for(xs.WORKLOADS["C3"])
+    conds = [base[i] for i in range(0, 32) if i % 4 != 3]        # 24 conditions, P <= 1 bar
+    cx = [xc.make_condition(c["T"], c["P"]) for c in conds]
+    nu_A, step, n = 912.3456, 0.0137, 12345
+    grid = xc.make_grid(nu_A, step, n)
+    eng.set_timing(True)
+    try:
+        tc = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0))
+        far_ms, main_ms, cz_ms, mma = eng.sweep_kernels()
+        cu = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0, tensor_cores=False))
+        far2, main2, cz2, mma2 = eng.sweep_kernels()
+    finally:
+        eng.set_timing(False)
+    assert mma > 0 and far_ms > 0 and main_ms > 0 and cz_ms > 0
+    assert mma2 == 0 and far2 < 0 and main2 > 0
+    m = cu > 1e-6 * cu.max(axis=1, keepdims=True)
+    diff = float(np.max(np.abs(tc[m] - cu[m]) / cu[m]))
+    full = np.where(m, np.abs(tc - cu) / np.where(m, cu, 1.0), 0.0)
+    ci, ki = np.unravel_index(np.argmax(full), full.shape)
+    worst, worst_cu = 0.0, 0.0
+    for i in (0, 11, 23, int(ci)):
+        ref = oracle_sigma(oracle_lib, L, E, g, conds[i]["T"], conds[i]["P"], nu_A, step, n, "voigt_w4", 10.0)
+        worst = max(worst, metrics(tc[i], ref)[0])
+        worst_cu = max(worst_cu, metrics(cu[i], ref)[0])
+    print(f"offset grid: tensor-core vs CUDA-core {diff:.3g} (condition {ci}, point {ki}, "
+          f"{tc[ci, ki]:.6g} vs {cu[ci, ki]:.6g}; {int((full > 2e-5).sum())} points), vs oracle: tensor-core "
+          f"{worst:.3g}, CUDA-core {worst_cu:.3g}; {mma} MMAs")
+    assert diff < 2e-5 and worst < TOL32
+
+
 @pytest.mark.parametrize("n_cond", [16, 20, 33])
 def test_batched_tensor_core_far_wings(eng, xc, oracle_lib, n_cond):
     """FP32 Voigt w4 with >= 16 conditions sums the far wings on the tensor cores
