@@ -10,7 +10,8 @@ Functions follow the paper's equations (arXiv:1801.09803):
 Eq. (e:pf) partition function, Eq. (e:int) intensity, Eq. (e:alphaD) Doppler
 HWHM, Eq. (e:gamma_L) Lorentz HWHM, Eqs. (e:Gauss), (e:lor), (e:Voigt) profiles,
 Humlicek's w4 for the Voigt function, Eqs. (e:V-quad) and (e:sigma:quad) for
-Gauss-Hermite Voigt, and the sampling method of Sec. 3.1.
+Gauss-Hermite Voigt, Eqs. (eqn:sig_ij) and (eqn:sig_lor-2) for the binned
+Gaussian and Lorentzian, and the sampling method of Sec. 3.1.
 """
 from __future__ import annotations
 
@@ -28,7 +29,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4}
+PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4,
+            "doppler_binned": 5, "lorentz_binned": 6}
 
 
 class Condition(C.Structure):
@@ -81,6 +83,9 @@ def lib():
         L.xo_voigt_gh.restype = d
         L.xo_voigt_gh_binned.argtypes = [d, d, d, d, i, vp, vp]
         L.xo_voigt_gh_binned.restype = d
+        for f in ("xo_gauss_binned", "xo_lorentz_binned"):
+            getattr(L, f).argtypes = [d, d, d]
+            getattr(L, f).restype = d
         L.xo_profile.argtypes = [i, d, d, d, d, i, vp, vp, vp, vp]
         L.xo_profile.restype = d
         L.xo_cross_section.argtypes = [vp] * 6 + [C.c_size_t, C.POINTER(Condition), d, d, C.c_longlong,
@@ -177,6 +182,16 @@ def voigt_gh(D, alpha, gamma, n=20):
 def voigt_gh_binned(D, h, alpha, gamma, n=20):
     x, w = gauss_hermite(n)
     return lib().xo_voigt_gh_binned(float(D), float(h), float(alpha), float(gamma), n, _p(x), _p(w))
+
+
+def gauss_binned(D, h, alpha):
+    """Eq. (eqn:sig_ij) without I: the Gaussian averaged over the bin [D - h/2, D + h/2]."""
+    return lib().xo_gauss_binned(float(D), float(h), float(alpha))
+
+
+def lorentz_binned(D, h, gamma):
+    """Eq. (eqn:sig_lor-2) without I: the Lorentzian averaged over the bin [D - h/2, D + h/2]."""
+    return lib().xo_lorentz_binned(float(D), float(h), float(gamma))
 
 
 def profile(name: str, D, h, alpha, gamma, n_gh=20):

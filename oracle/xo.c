@@ -21,6 +21,9 @@
  *                 (J. Humlicek, JQSRT 27 (1982) 437), restated below
  *   GH sampled    Eq. (e:V-quad) with the node shift alpha*x_j/sqrt(ln2)
  *   GH binned     Eq. (e:sigma:quad), y^+- = (nu_k +- dnu/2 - nu_fi - alpha x_j/sqrt(ln2))/gamma
+ *   Gauss binned  Eq. (eqn:sig_ij), bin average by the erf difference, Sec. "Binned Gaussian"
+ *   Lorentz binned Eq. (eqn:sig_lor-2), bin average by the arctan difference, with
+ *                 y^+- = (nu_k +- dnu/2 - nu_fi)/gamma (Eq. e:y_k^pm read with its lost minus)
  *   sampling      sigma(nu_k) = sum_fi I_fi f(nu_k)  (Sec. 3.1), lines outer,
  *                 grid points inner, within the cutoff ("Off-set", Sec. 3.10)
  *   grid          nu_k = nu_A + k * dnu, N points including both ends, Eq. (e:Ngrid)
@@ -57,7 +60,8 @@ static const double XO_LN2 = 0.69314718055994530942;
 
 double xo_c2(void) { return XO_H * (XO_C_SI * 100.0) / XO_KB; } /* cm K */
 
-enum { XO_DOPPLER = 0, XO_LORENTZ = 1, XO_VOIGT_W4 = 2, XO_GH_BINNED = 3, XO_GH_SAMPLED = 4 };
+enum { XO_DOPPLER = 0, XO_LORENTZ = 1, XO_VOIGT_W4 = 2, XO_GH_BINNED = 3, XO_GH_SAMPLED = 4,
+       XO_DOPPLER_BINNED = 5, XO_LORENTZ_BINNED = 6 };
 
 /* ---------------------------------------------------------------------- */
 /* Partition function, Eq. (e:pf), and its temperature derivative          */
@@ -303,6 +307,29 @@ double xo_voigt_gh_binned(double D, double h, double alpha, double gamma,
     return s / (pow(XO_PI, 1.5) * h);
 }
 
+/* bin average of the Gaussian over [D - h/2, D + h/2], Eq. (eqn:sig_ij) without I:
+ * (erf(x+) - erf(x-)) / (2h), x+- = sqrt(ln2)/alpha (D +- h/2).  When both limits lie
+ * on one side of the centre the same difference is taken as erfc(x-) - erfc(x+) (on the
+ * mirrored side), which is the identical quantity without the cancellation of two
+ * values near 1. */
+double xo_gauss_binned(double D, double h, double alpha)
+{
+    double sl = sqrt(XO_LN2);
+    double xp = sl * (D + 0.5 * h) / alpha, xm = sl * (D - 0.5 * h) / alpha;
+    double d;
+    if (xm >= 0.0) d = erfc(xm) - erfc(xp);
+    else if (xp <= 0.0) d = erfc(-xp) - erfc(-xm);
+    else d = erf(xp) - erf(xm);
+    return d / (2.0 * h);
+}
+
+/* bin average of the Lorentzian, Eq. (eqn:sig_lor-2) without I:
+ * (atan(y+) - atan(y-)) / (pi h), y+- = (D +- h/2)/gamma */
+double xo_lorentz_binned(double D, double h, double gamma)
+{
+    return (atan((D + 0.5 * h) / gamma) - atan((D - 0.5 * h) / gamma)) / (XO_PI * h);
+}
+
 /* profile value and its partial derivatives w.r.t. alpha and gamma */
 static double profile_eval(int prof, double D, double h, double alpha, double gamma,
                            int ngh, const double *xg, const double *wg,
@@ -340,6 +367,20 @@ static double profile_eval(int prof, double D, double h, double alpha, double ga
         }
         double k = pow(XO_PI, -1.5);
         V = s * k; dg *= k; da *= k;
+        break;
+    }
+    case XO_DOPPLER_BINNED: {
+        /* d/dalpha erf(x) = 2/sqrt(pi) e^{-x^2} (-x/alpha) */
+        double xp = sl * (D + 0.5 * h) / alpha, xm = sl * (D - 0.5 * h) / alpha;
+        V = xo_gauss_binned(D, h, alpha);
+        da = (-xp * exp(-xp * xp) + xm * exp(-xm * xm)) / (sqrt(XO_PI) * alpha * h);
+        break;
+    }
+    case XO_LORENTZ_BINNED: {
+        /* d/dgamma atan(s/gamma) = -s/(s^2 + gamma^2) */
+        double sp = D + 0.5 * h, sm = D - 0.5 * h;
+        V = xo_lorentz_binned(D, h, gamma);
+        dg = (-sp / (sp * sp + gamma * gamma) + sm / (sm * sm + gamma * gamma)) / (XO_PI * h);
         break;
     }
     case XO_GH_BINNED:

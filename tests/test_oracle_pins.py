@@ -234,6 +234,52 @@ def test_gh_binned_telescopes_and_matches_bin_average(oracle_lib):
         assert oracle_lib.voigt_gh_binned(D, h, a, g, 20) == pytest.approx(ex / h, rel=5e-3)
 
 
+@pytest.mark.parametrize("h", [0.004, 0.01, 0.1])
+def test_binned_gauss_and_lorentz_are_bin_averages(oracle_lib, h):
+    """Eqs. (eqn:sig_ij) and (eqn:sig_lor-2): the bin average of the unit-area Gaussian /
+    Lorentzian, checked against adaptive quadrature of the library pdfs over the bin."""
+    a, g = 0.02, 0.015
+    sig = a / math.sqrt(2 * LN2)
+    for D in (0.0, 0.3 * h, -0.7 * h, 2.0 * h, 0.05, -0.12, 0.3):
+        ex, _ = si.quad(lambda u: st.norm.pdf(u, scale=sig), D - h / 2, D + h / 2, epsabs=0, epsrel=1e-13)
+        assert oracle_lib.gauss_binned(D, h, a) == pytest.approx(ex / h, rel=1e-10)
+        ex, _ = si.quad(lambda u: st.cauchy.pdf(u, scale=g), D - h / 2, D + h / 2, epsabs=0, epsrel=1e-13)
+        assert oracle_lib.lorentz_binned(D, h, g) == pytest.approx(ex / h, rel=1e-10)
+        # symmetric in D
+        assert oracle_lib.gauss_binned(-D, h, a) == pytest.approx(oracle_lib.gauss_binned(D, h, a), rel=1e-14)
+        assert oracle_lib.lorentz_binned(-D, h, g) == pytest.approx(oracle_lib.lorentz_binned(D, h, g), rel=1e-14)
+
+
+def test_binned_gauss_and_lorentz_conserve_area_on_coarse_grids(oracle_lib):
+    """The bin averages telescope: h * sum_k equals the profile's integral over the union
+    of the bins on any grid, also one far coarser than the line (where sampling fails)."""
+    a, g = 0.02, 0.015
+    for h in (0.1, 0.037):
+        K = 400
+        for off in (0.0, 0.013):
+            gb = sum(oracle_lib.gauss_binned(k * h + off, h, a) for k in range(-K, K + 1)) * h
+            assert gb == pytest.approx(1.0, rel=1e-13)
+            lb = sum(oracle_lib.lorentz_binned(k * h + off, h, g) for k in range(-K, K + 1)) * h
+            top, bot = (K + 0.5) * h + off, -(K + 0.5) * h + off
+            assert lb == pytest.approx((st.cauchy.cdf(top, scale=g) - st.cauchy.cdf(bot, scale=g)), rel=1e-12)
+    # the sampled Gaussian on the coarse grid (points 2.5 alpha either side) keeps ~6 %
+    smp = sum(oracle_lib.gauss(k * 0.1 + 0.05, a) for k in range(-40, 41)) * 0.1
+    assert smp < 0.1
+    # narrow bins: the bin average tends to the sampled profile (error ~ h^2 f''/24)
+    for D in (0.0, 0.01, 0.04):
+        assert oracle_lib.gauss_binned(D, 1e-5, a) == pytest.approx(oracle_lib.gauss(D, a), rel=1e-7)
+        assert oracle_lib.lorentz_binned(D, 1e-5, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1e-7)
+
+
+def test_binned_lorentz_is_one_node_binned_gauss_hermite(oracle_lib):
+    """alpha -> 0 collapses Eq. (e:sigma:quad) onto Eq. (eqn:sig_lor-2): every node sits on the
+    line centre and the weights sum to sqrt(pi)."""
+    g, h = 0.015, 0.01
+    for D in (0.0, 0.004, 0.05, 1.3):
+        assert oracle_lib.voigt_gh_binned(D, h, 1e-300, g, 20) == pytest.approx(
+            oracle_lib.lorentz_binned(D, h, g), rel=1e-13)
+
+
 # --------------------------------------------- full cross sections
 def _tiny_lines(n, seed=3, lo=1000.0, hi=1001.0):
     return xs.gen_lines(seed, 0, n, lo, hi)
@@ -272,6 +318,37 @@ def test_cross_section_bruteforce(oracle_lib, profile):
     mask = out > 0
     assert np.array_equal(mask, sig > 0)
     assert np.max(np.abs(sig[mask] - out[mask]) / out[mask]) < tol
+
+
+@pytest.mark.parametrize("profile", ["doppler_binned", "lorentz_binned"])
+def test_cross_section_bruteforce_binned(oracle_lib, profile):
+    """Sums of bin averages: each (line, bin) by adaptive quadrature of the library pdf."""
+    L = _tiny_lines(5, seed=4)
+    T, P, Q = 1500.0, 2.0, 700.0
+    cond = oracle_lib.make_condition(T, P, Q)
+    nu_A, h, N, cut = 999.7, 0.013, 61, 0.35
+    sig = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts(profile, cut))
+    c2, c_cm = 1.438776877503933802, 2.99792458e10
+    out = np.zeros(N)
+    for k in range(N):
+        xk = nu_A + k * h
+        for l in range(5):
+            nu = float(L["nu"][l]); D = xk - nu
+            if abs(D) > cut:
+                continue
+            I = (float(L["g_up"][l]) * float(L["A"][l]) / (8 * math.pi * c_cm * nu * nu)
+                 * math.exp(-c2 * float(L["elower"][l]) / T) * (1 - math.exp(-c2 * nu / T)) / Q)
+            if profile == "doppler_binned":
+                al = nu / 2.99792458e8 * math.sqrt(2 * 1.380649e-23 * T * LN2 / (18 * 1.66053906660e-27))
+                pdf = lambda u: st.norm.pdf(u, scale=al / math.sqrt(2 * LN2))
+            else:
+                ga = float(L["gamma_ref"][l]) * (296.0 / T) ** float(L["n_T"][l]) * P
+                pdf = lambda u: st.cauchy.pdf(u, scale=ga)
+            v, _ = si.quad(pdf, D - h / 2, D + h / 2, epsabs=0, epsrel=1e-12)
+            out[k] += I * v / h
+    big = out > 1e-9 * out.max()
+    assert np.max(np.abs(sig[big] - out[big]) / out[big]) < 1e-9
+    assert np.all(np.abs(sig[~big]) <= 2e-9 * out.max())
 
 
 def test_cutoff_is_inclusive_and_ragged_edges(oracle_lib):
@@ -339,7 +416,8 @@ def test_width_limited_cut(oracle_lib):
 
 
 # --------------------------------------------- adjoint
-@pytest.mark.parametrize("profile", ["voigt_w4", "doppler", "lorentz", "voigt_gh_binned"])
+@pytest.mark.parametrize("profile", ["voigt_w4", "doppler", "lorentz", "voigt_gh_binned", "doppler_binned",
+                                     "lorentz_binned"])
 def test_vjp_matches_central_differences(oracle_lib, profile):
     L = xs.gen_lines(31, 0, 6, 1000.0, 1000.5)
     E, gst = xs.gen_states(31, 400)
