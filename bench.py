@@ -258,7 +258,7 @@ def _timed(torch, fn, reps=1):
 def secondary_measurements(xc, torch, dev):
     """The other workloads, one timing each (CUDA events, device-resident inputs):
     C1 (1e5 lines, FP64 plain and FP32), C2 (1e7 lines, width-limited cut, Voigt w4
-    FP64 plain and FP32, GH binned FP32), C4 (1e7 lines, 2x2 conditions: FP32
+    FP64 plain and FP32; GH binned, binned Gaussian and binned Lorentzian FP32), C4 (1e7 lines, 2x2 conditions: FP32
     forward and FP32 adjoint).  Values are evals/s over the exact eval count."""
     out = {}
     for name in ("C1", "C2", "C4"):
@@ -274,7 +274,7 @@ def secondary_measurements(xc, torch, dev):
         res = {}
         cases = [("voigt_w4", "fp32")] if name == "C4" else [("voigt_w4", "fp64"), ("voigt_w4", "fp32")]
         if name == "C2":
-            cases.append(("voigt_gh_binned", "fp32"))
+            cases += [("voigt_gh_binned", "fp32"), ("doppler_binned", "fp32"), ("lorentz_binned", "fp32")]
         for prof, prec in cases:
             o = xc.make_opts(prof, prec, W.cutoff, W.cutoff_width_mult, W.n_gh)
             ev = eng.count_evals(conds, grid, o)

@@ -50,7 +50,9 @@ enum {
     XC_LORENTZ = 1,          /* Eq. (e:lor) with gamma_L of Eq. (e:gamma_L) */
     XC_VOIGT_W4 = 2,         /* Eq. (e:Voigt), w(z) by Humlicek's w4 */
     XC_VOIGT_GH_BINNED = 3,  /* Eq. (e:sigma:quad): bin-averaged Gauss-Hermite (area-conserving) */
-    XC_VOIGT_GH_SAMPLED = 4  /* Eq. (e:V-quad): Gauss-Hermite sum sampled at the grid point */
+    XC_VOIGT_GH_SAMPLED = 4, /* Eq. (e:V-quad): Gauss-Hermite sum sampled at the grid point */
+    XC_DOPPLER_BINNED = 5,   /* Eq. (eqn:sig_ij): Gaussian averaged over each grid bin (erf) */
+    XC_LORENTZ_BINNED = 6    /* Eq. (eqn:sig_lor-2): Lorentzian averaged over each grid bin (arctan) */
 };
 
 /* arithmetic of the profile evaluation */
@@ -113,7 +115,7 @@ typedef struct {
  * (inclusive), cut_l = cutoff, or min(cutoff, width_mult * max(alpha_l, gamma_l))
  * when width_mult > 0 (Sec. 3.10 "Off-set").  n_gh: Gauss-Hermite nodes (1..64). */
 typedef struct {
-    int profile;        /* XC_DOPPLER .. XC_VOIGT_GH_SAMPLED */
+    int profile;        /* XC_DOPPLER .. XC_LORENTZ_BINNED */
     int precision;      /* XC_FP64_PLAIN or XC_FP32 */
     double cutoff;      /* cm^-1, > 0 */
     double width_mult;  /* 0 = fixed cut */

@@ -23,7 +23,8 @@ __all__ = [
 
 LIB_PATH = _build.LIB
 XC_MEM_HOST, XC_MEM_DEVICE = 0, 1
-PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4}
+PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4,
+            "doppler_binned": 5, "lorentz_binned": 6}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "XC_OK", 1: "XC_EINVAL", 2: "XC_ENOMEM", 3: "XC_ECUDA", 4: "XC_ETIMEOUT", 5: "XC_EUNSUPPORTED"}
 EXPORTED_SYMBOLS = [

@@ -153,7 +153,7 @@ xc_status check_grid(const xc_grid *g) {
 
 xc_status check_opts(const xc_opts *o) {
     if (!o) { set_error("NULL opts"); return XC_EINVAL; }
-    if (o->profile < XC_DOPPLER || o->profile > XC_VOIGT_GH_SAMPLED) {
+    if (o->profile < XC_DOPPLER || o->profile > XC_LORENTZ_BINNED) {
         set_error("unknown profile %d", o->profile);
         return XC_EUNSUPPORTED;
     }

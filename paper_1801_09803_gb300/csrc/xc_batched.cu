@@ -442,6 +442,12 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         *A = make_float4(qd, I * kSqrtLn2OverPi * rcp_approx(al), 0.f, 0.f);
     } else if (PROF == XC_VOIGT_GH_SAMPLED) {
         *A = make_float4(ah / kSqrtLn2f, fmaxf(gh * gh, 1e-30f), I * kPiM32 * gh * inv_h, 0.f);
+    } else if (PROF == XC_DOPPLER_BINNED) {
+        // Eq. (eqn:sig_ij) in grid steps: x+- = (sqrt(ln2)/ah) (delta +- 1/2), I/(2h)
+        *A = make_float4(kSqrtLn2f * rcp_approx(ah), 0.5f * I * inv_h, 0.f, 0.f);
+    } else if (PROF == XC_LORENTZ_BINNED) {
+        // Eq. (eqn:sig_lor-2) in grid steps: y+- = (delta +- 1/2)/gh, I/(pi h)
+        *A = make_float4(gh, gh * gh - 0.25f, I * inv_h * (float)(1.0 / 3.141592653589793), 0.f);
     } else {
         *A = make_float4(ah / kSqrtLn2f, gh, gh * gh - 0.25f, I * kPiM32 * inv_h);
     }
@@ -493,6 +499,14 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
             s = fmaf(s_w[j], rcp_approx(fmaf(e, e, A.y)), s);
         }
         return A.z * s;
+    } else if (PROF == XC_DOPPLER_BINNED) {
+        // erf(x+) - erf(x-) on the side |delta| of the (symmetric) profile, as
+        // erfc(x-) - erfc(x+): no difference of two numbers near 1 in the wings
+        const float t = fabsf(delta);
+        return A.y * (erfcf(A.x * (t - 0.5f)) - erfcf(A.x * (t + 0.5f)));
+    } else if (PROF == XC_LORENTZ_BINNED) {
+        // atan(y+) - atan(y-) = atan2(y+ - y-, 1 + y+ y-), both arguments scaled by gh^2 > 0
+        return A.z * atan2f(A.x, u + A.y);
     } else {
         float s = 0.f;
         for (int j = 0; j < ngh; ++j) {
@@ -1612,6 +1626,10 @@ static const Variant kVariants[] = {
     XC_VARIANT(XC_VOIGT_GH_SAMPLED, 8, 1),
     XC_VARIANT(XC_VOIGT_GH_BINNED, 4, 16), XC_VARIANT(XC_VOIGT_GH_BINNED, 8, 4),
     XC_VARIANT(XC_VOIGT_GH_BINNED, 8, 1),
+    XC_VARIANT(XC_DOPPLER_BINNED, 4, 16), XC_VARIANT(XC_DOPPLER_BINNED, 8, 4),
+    XC_VARIANT(XC_DOPPLER_BINNED, 8, 1),
+    XC_VARIANT(XC_LORENTZ_BINNED, 4, 16), XC_VARIANT(XC_LORENTZ_BINNED, 8, 4),
+    XC_VARIANT(XC_LORENTZ_BINNED, 8, 1),
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1933,17 +1951,21 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
     int dev = 0;
     cudaGetDevice(&dev);
     std::vector<int> cands;
-    for (int i = 0; i < kNumVariants; ++i) {
-        const Variant &v = kVariants[i];
-        if (v.profile != a.opts.profile) continue;
-        if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
-        if (a.opts.width_mult <= 0.0 && st->force_R == 0) {
-            if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
-            if (v.CG < std::min(nc, 8)) continue;              // enough conditions share each staged line
+    // the shape heuristics first; if they leave no variant of this profile (e.g. 5 to 7
+    // conditions where only groups of 1, 4 and 16 exist), every admissible shape
+    for (int pass = 0; pass < 2 && cands.empty(); ++pass) {
+        for (int i = 0; i < kNumVariants; ++i) {
+            const Variant &v = kVariants[i];
+            if (v.profile != a.opts.profile) continue;
+            if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
+            if (pass == 0 && a.opts.width_mult <= 0.0 && st->force_R == 0) {
+                if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
+                if (v.CG < std::min(nc, 8)) continue;              // enough conditions share each staged line
+            }
+            if (tc && v.R != 4) continue;  // spans of 128 points = the far-wing kernel's blocks
+            if (st->force_R > 0 && (v.R != st->force_R || v.CG != st->force_CG)) continue;
+            cands.push_back(i);
         }
-        if (tc && v.R != 4) continue;  // spans of 128 points = the far-wing kernel's blocks
-        if (st->force_R > 0 && (v.R != st->force_R || v.CG != st->force_CG)) continue;
-        cands.push_back(i);
     }
     if (cands.empty()) {
         set_error("no FP32 kernel variant for profile %d", a.opts.profile);
@@ -2241,12 +2263,16 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
         set_error("the allocation-free entry point computes the FP32 kernel with a fixed cut");
         return XC_EUNSUPPORTED;
     }
-    if (opts->profile < XC_DOPPLER || opts->profile > XC_VOIGT_GH_SAMPLED || !(opts->cutoff > 0.0)) {
+    if (opts->profile < XC_DOPPLER || opts->profile > XC_LORENTZ_BINNED || !(opts->cutoff > 0.0)) {
         set_error("bad opts");
         return XC_EINVAL;
     }
     if (opts->profile == XC_VOIGT_GH_BINNED || opts->profile == XC_VOIGT_GH_SAMPLED) {
         set_error("Gauss-Hermite profiles need node tables: use xc_cross_section_batched");
+        return XC_EUNSUPPORTED;
+    }
+    if (opts->profile == XC_DOPPLER_BINNED || opts->profile == XC_LORENTZ_BINNED) {
+        set_error("binned profiles: use xc_cross_section_batched");
         return XC_EUNSUPPORTED;
     }
     for (size_t i = 0; i < n_cond; ++i) {

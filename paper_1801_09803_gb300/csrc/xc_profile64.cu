@@ -28,6 +28,16 @@ __device__ inline double profile64(double D, double step, double al, double ga, 
         double ia = kSqrtLn2 / al;
         Cx<double> w = w4_eval<double>(D * ia, ga * ia, nullptr);
         return 0.46971863934982566 / al * w.re;
+    } else if (PROF == XC_DOPPLER_BINNED) {
+        // Eq. (eqn:sig_ij) without I: (erf(x+) - erf(x-)) / (2h), x+- = sqrt(ln2)/alpha (D +- h/2),
+        // taken on the side |D| as erfc(x-) - erfc(x+) (the profile is symmetric)
+        double t = fabs(D), c = kSqrtLn2 / al;
+        return (erfc(c * (t - 0.5 * step)) - erfc(c * (t + 0.5 * step))) / (2.0 * step);
+    } else if (PROF == XC_LORENTZ_BINNED) {
+        // Eq. (eqn:sig_lor-2) without I: (atan(y+) - atan(y-)) / (pi h), y+- = (D +- h/2)/gamma,
+        // as one atan2 with both arguments scaled by gamma^2 > 0
+        double hh = 0.5 * step;
+        return atan2(step * ga, (D + hh) * (D - hh) + ga * ga) / (kPi * step);
     } else if (PROF == XC_VOIGT_GH_SAMPLED) {
         // Eq. (e:V-quad) with node shift alpha x_j / sqrt(ln2)
         double s = 0.0, g2 = ga * ga, sh = al / kSqrtLn2;
@@ -122,6 +132,14 @@ cudaError_t launch_gather_f64(int profile, const double *nu, const double *I, co
     case XC_VOIGT_GH_SAMPLED:
         k_gather_f64<XC_VOIGT_GH_SAMPLED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
                                                                 step, n_pts, ghx, ghw, ngh, sigma);
+        break;
+    case XC_DOPPLER_BINNED:
+        k_gather_f64<XC_DOPPLER_BINNED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
+                                                              step, n_pts, ghx, ghw, ngh, sigma);
+        break;
+    case XC_LORENTZ_BINNED:
+        k_gather_f64<XC_LORENTZ_BINNED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
+                                                              step, n_pts, ghx, ghw, ngh, sigma);
         break;
     default:
         return cudaErrorInvalidValue;

@@ -17,7 +17,8 @@ import xcsynth as xs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PROFILES = ["doppler", "lorentz", "voigt_w4", "voigt_gh_binned", "voigt_gh_sampled"]
+PROFILES = ["doppler", "lorentz", "voigt_w4", "voigt_gh_binned", "voigt_gh_sampled", "doppler_binned",
+            "lorentz_binned"]
 TOL64 = 1e-5
 TOL32 = 2e-4
 TOL32_BAND = 1e-5
@@ -310,6 +311,25 @@ def test_every_w4_tile_shape(eng, xc, oracle_lib):
     assert not bad, bad
 
 
+@pytest.mark.parametrize("n_cond", [5, 6, 7, 9])
+def test_every_profile_at_odd_condition_counts(eng, xc, oracle_lib, n_cond):
+    """Condition counts between the kernel's group sizes (1, 4, 8, 16) run for every profile."""
+    L = xs.gen_lines(110, 0, 3000, 1000.0, 1030.0)
+    E, g = xs.gen_states(110, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    nu_A, step, n, cut = 995.0, 0.01, 4001, 4.0
+    TP = [(300.0 * 1.4 ** i, 0.05 * 2.0 ** i) for i in range(n_cond)]
+    grid = xc.make_grid(nu_A, step, n)
+    for profile in PROFILES:
+        got = eng.cross_section_batched([xc.make_condition(T, P) for T, P in TP], grid,
+                                        xc.make_opts(profile, "fp32", cut, n_gh=10))
+        for j in (0, n_cond - 1):
+            ref = oracle_sigma(oracle_lib, L, E, g, TP[j][0], TP[j][1], nu_A, step, n, profile, cut, n_gh=10)
+            mr, band = metrics(got[j], ref)
+            assert mr < TOL32 and band < TOL32_BAND, (profile, n_cond, j, mr, band)
+
+
 @pytest.mark.parametrize("profile", ["voigt_w4", "voigt_gh_binned"])
 def test_width_limited_cut(eng, xc, oracle_lib, profile):
     L = xs.gen_lines(108, 0, 10000, 0.0, 100.0)
@@ -323,6 +343,39 @@ def test_width_limited_cut(eng, xc, oracle_lib, profile):
         mr, band = metrics(got, ref)
         print(f"width-limited {profile} {precision}: {mr:.3g} {band:.3g}")
         assert mr < tol[0] and band < tol[1]
+
+
+@pytest.mark.parametrize("profile", ["doppler_binned", "lorentz_binned"])
+def test_binned_profiles_on_a_coarse_grid(eng, xc, oracle_lib, profile):
+    """Binned Gaussian / Lorentzian (Eqs. eqn:sig_ij, eqn:sig_lor-2) on a grid up to 50 times
+    coarser than the lines, several conditions in one batched sweep, a ragged last tile;
+    the FP64 path keeps the area: h sum_k sigma_k = sum_l I_l (to the cut's truncation)."""
+    L = xs.gen_lines(109, 0, 30000, 1000.0, 1400.0)
+    E, g = xs.gen_states(109, 2000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    nu_A, step, n, cut = 990.0, 0.1, 4237, 6.0
+    TP = [(300.0, 0.01), (900.0, 0.3), (2000.0, 1.0), (3000.0, 5.0), (1200.0, 0.1), (600.0, 2.0)]
+    grid = xc.make_grid(nu_A, step, n)
+    got32 = eng.cross_section_batched([xc.make_condition(T, P) for T, P in TP], grid,
+                                      xc.make_opts(profile, "fp32", cut))
+    worst = (0.0, 0.0)
+    for j, (T, P) in enumerate(TP):
+        ref = oracle_sigma(oracle_lib, L, E, g, T, P, nu_A, step, n, profile, cut)
+        mr, band = metrics(got32[j], ref)
+        worst = (max(worst[0], mr), max(worst[1], band))
+        if j < 2:
+            got64 = eng.cross_section(xc.make_condition(T, P), grid, xc.make_opts(profile, "fp64", cut))
+            m64, b64 = metrics(got64, ref)
+            assert m64 < TOL64 and b64 < TOL64, (T, P, m64, b64)
+            if profile == "doppler_binned":
+                Q, _ = oracle_lib.partition_function(E, g, T)
+                c = oracle_lib.make_condition(T, P, Q)
+                I = sum(oracle_lib.intensity(float(L["nu"][l]), float(L["elower"][l]), float(L["A"][l]),
+                                             float(L["g_up"][l]), c) for l in range(len(L["nu"])))
+                assert float(np.sum(got64)) * step == pytest.approx(I, rel=1e-9)
+    print(f"binned {profile} fp32 (6 conditions): worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
+    assert worst[0] < TOL32 and worst[1] < TOL32_BAND
 
 
 def test_c1_full_size(eng, xc, oracle_lib):
