@@ -41,7 +41,11 @@ class Condition(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("profile", C.c_int), ("cutoff", C.c_double), ("width_mult", C.c_double),
-                ("n_gh", C.c_int)]
+                ("n_gh", C.c_int), ("quantity", C.c_int), ("thr_mode", C.c_int), ("I_cut", C.c_double),
+                ("nu_crit", C.c_double), ("I_crit", C.c_double)]
+
+
+QUANTITIES = {"absorption": 0, "emission": 1}
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +70,10 @@ def lib():
         L.xo_c2.restype = d
         L.xo_partition_function.argtypes = [vp, vp, C.c_size_t, d, vp, vp]
         L.xo_intensity.argtypes = [d, d, d, d, C.POINTER(Condition)]
+        L.xo_emissivity.argtypes = [d, d, d, d, C.POINTER(Condition)]
+        L.xo_emissivity.restype = d
+        L.xo_threshold.argtypes = [d, d, C.POINTER(Opts)]
+        L.xo_threshold.restype = d
         L.xo_intensity.restype = d
         L.xo_alpha_doppler.argtypes = [d, C.POINTER(Condition)]
         L.xo_alpha_doppler.restype = d
@@ -130,12 +138,31 @@ def make_condition(T: float, P: float, Q: float, dQdT: float = 0.0, mass_da: flo
 
 
 def make_opts(profile: str = "voigt_w4", cutoff: float = 25.0, width_mult: float = 0.0,
-              n_gh: int = 20) -> Opts:
-    return Opts(PROFILES[profile], cutoff, width_mult, n_gh)
+              n_gh: int = 20, quantity: str = "absorption", threshold=None) -> Opts:
+    """threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit)."""
+    mode, I_cut, nu_crit, I_crit = 0, 0.0, 0.0, 0.0
+    if threshold is not None:
+        if threshold[0] == "constant":
+            mode, I_cut = 1, float(threshold[1])
+        elif threshold[0] == "hitran":
+            mode, nu_crit, I_crit = 2, float(threshold[1]), float(threshold[2])
+        else:
+            raise ValueError(f"unknown threshold {threshold[0]!r}")
+    return Opts(PROFILES[profile], cutoff, width_mult, n_gh, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit)
 
 
 def intensity(nu, elower, A, g_up, cond: Condition) -> float:
     return lib().xo_intensity(float(nu), float(elower), float(A), float(g_up), C.byref(cond))
+
+
+def emissivity(nu, elower, A, g_up, cond: Condition) -> float:
+    """Eq. (e:emiss) times the photon energy h c nu: erg/s/sr per molecule."""
+    return lib().xo_emissivity(float(nu), float(elower), float(A), float(g_up), C.byref(cond))
+
+
+def threshold(nu, T, opts: Opts) -> float:
+    """The intensity threshold at nu (0 when opts sets none)."""
+    return lib().xo_threshold(float(nu), float(T), C.byref(opts))
 
 
 def alpha_doppler(nu, cond: Condition) -> float:

@@ -11,6 +11,12 @@
  * Tennyson 2018, arXiv:1801.09803), in its notation, in the order it gives:
  *   Q(T)          Eq. (e:pf)   direct state sum
  *   I_fi          Eq. (e:int)  LTE absorption intensity, upper degeneracy
+ *   eps_fi        Eq. (e:emiss) LTE emissivity from the upper state (E' = E'' + nu),
+ *                 with the photon energy h c nu so that it comes out in the unit the
+ *                 text gives (erg/s/sr per molecule; the printed formula omits h c)
+ *   thresholds    Sec. "Intensity thresholds": constant, or HITRAN's dynamic
+ *                 I_crit (nu/nu_crit) tanh(c2 nu / 2T) below nu_crit, I_crit above;
+ *                 a line whose intensity (or emissivity) is below it is left out
  *   alpha_D       Eq. (e:alphaD)
  *   gamma_L       Eq. (e:gamma_L)
  *   Gauss         Eq. (e:Gauss)        Lorentz  Eq. (e:lor)
@@ -95,6 +101,9 @@ typedef struct {
     double cutoff;               /* cm^-1 */
     double width_mult;           /* > 0: cut_l = min(cutoff, width_mult*max(alpha, gamma)) */
     int n_gh;
+    int quantity;                /* 0: absorption, Eq. (e:int); 1: emission, Eq. (e:emiss) */
+    int thr_mode;                /* 0: none; 1: constant I_cut; 2: HITRAN dynamic (nu_crit, I_crit) */
+    double I_cut, nu_crit, I_crit;
 } xo_opts;
 
 /* Eq. (e:int): I = g' A / (8 pi c nu^2) * exp(-c2 E''/T) * (1 - exp(-c2 nu/T)) / Q(T) */
@@ -105,6 +114,38 @@ double xo_intensity(double nu, double elower, double A, double g_up, const xo_co
     double boltz = exp(-c2 * elower / c->T);
     double stim = -expm1(-c2 * nu / c->T);
     return c->abundance * g_up * A / (8.0 * XO_PI * c_cm * nu * nu) * boltz * stim / c->Q;
+}
+
+/* Eq. (e:emiss): emissivity of the line from its upper state, E' = E'' + nu, times the
+ * photon energy h c nu (erg): g' A h c nu / (4 pi) * exp(-c2 E'/T) / Q(T) */
+double xo_emissivity(double nu, double elower, double A, double g_up, const xo_condition *c)
+{
+    const double c2 = xo_c2();
+    const double c_cm = XO_C_SI * 100.0;
+    const double h_erg = XO_H * 1e7;
+    double boltz = exp(-c2 * (elower + nu) / c->T);
+    return c->abundance * g_up * A * (h_erg * c_cm * nu) / (4.0 * XO_PI) * boltz / c->Q;
+}
+
+/* Intensity threshold at wavenumber nu (Sec. "Intensity thresholds"): 0 = none */
+double xo_threshold(double nu, double T, const xo_opts *o)
+{
+    if (o->thr_mode == 1) return o->I_cut;
+    if (o->thr_mode == 2) {
+        if (nu > o->nu_crit) return o->I_crit;
+        return o->I_crit * (nu / o->nu_crit) * tanh(xo_c2() * nu / (2.0 * T));
+    }
+    return 0.0;
+}
+
+/* the line's strength for the chosen quantity, or -1 if the threshold leaves it out */
+static double line_strength(const xo_opts *o, double nu, double elower, double A, double g_up,
+                            const xo_condition *c)
+{
+    double S = o->quantity == 1 ? xo_emissivity(nu, elower, A, g_up, c)
+                                : xo_intensity(nu, elower, A, g_up, c);
+    if (o->thr_mode != 0 && S < xo_threshold(nu, c->T, o)) return -1.0;
+    return S;
 }
 
 /* Eq. (e:alphaD): Doppler HWHM */
@@ -459,7 +500,8 @@ int xo_cross_section(const double *nu, const float *elower, const float *A, cons
         size_t l1 = n_lines * (size_t)(t + 1) / (size_t)nthreads;
         for (size_t l = l0; l < l1; ++l) {
             double nul = nu[l];
-            double Ifi = xo_intensity(nul, elower[l], A[l], g_up[l], cond);
+            double Ifi = line_strength(o, nul, elower[l], A[l], g_up[l], cond);
+            if (Ifi < 0.0) continue;   /* below the intensity threshold */
             double al = xo_alpha_doppler(nul, cond);
             double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cond);
             double cut = line_cut(o, al, ga);
@@ -528,7 +570,8 @@ int xo_cross_section_points(const double *nu, const float *elower, const float *
             double cut = line_cut(o, al, ga);
             double D = xk - nu[l];
             if (fabs(D) > cut) continue;
-            double Ifi = xo_intensity(nu[l], elower[l], A[l], g_up[l], cond);
+            double Ifi = line_strength(o, nu[l], elower[l], A[l], g_up[l], cond);
+            if (Ifi < 0.0) continue;   /* below the intensity threshold */
             neumaier_add(&s, &c, Ifi * profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, NULL, NULL));
         }
         out[i] = s + c;
@@ -536,7 +579,8 @@ int xo_cross_section_points(const double *nu, const float *elower, const float *
     return 0;
 }
 
-/* number of (line, grid point) pairs inside the cutoff: the algorithmic work */
+/* number of (line, grid point) pairs inside the cutoff: the algorithmic work (every
+ * line counts, whatever an intensity threshold would leave out) */
 long long xo_count_evals(const double *nu, const float *gamma_ref, const float *n_T, size_t n_lines,
                          const xo_condition *cond, double nu_A, double h, long long n_pts,
                          const xo_opts *o)
@@ -575,6 +619,7 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
     const double c2 = xo_c2();
     double xg[200], wg[200];
     int ngh = 0;
+    if (o->quantity != 0 || o->thr_mode != 0) return -4;   /* absorption, no threshold */
     if (o->profile == XO_GH_BINNED || o->profile == XO_GH_SAMPLED) {
         ngh = o->n_gh;
         if (xo_gauss_hermite(ngh, xg, wg) != 0) return -1;

@@ -90,6 +90,77 @@ def test_intensity_structure(oracle_lib):
     assert oracle_lib.intensity(nu, 0.0, 1.0, 1.0, hot) == pytest.approx(expect, rel=1e-8)
 
 
+# --------------------------------------------- emissivity, Eq. (e:emiss); thresholds
+def test_emissivity_over_intensity_is_planck(oracle_lib):
+    """Kirchhoff's law in LTE: emissivity / absorption intensity of the same line equals the
+    Planck function in wavenumber units, B(nu, T) = 2 h c^2 nu^3 / (exp(h c nu / k T) - 1)
+    (CGS: erg s^-1 cm^-2 sr^-1 per cm^-1), for any Q, degeneracy, A and lower energy."""
+    import scipy.constants as sc
+    h, c, k = sc.h * 1e7, sc.c * 100.0, sc.k * 1e7
+    for T, nu, El, A, g, Q in ((296.0, 1000.0, 0.0, 1.0, 3.0, 100.0), (1500.0, 3750.5, 2000.0, 25.0, 11.0, 870.0),
+                                 (3000.0, 0.37, 15000.0, 1e-5, 1.0, 5000.0), (5000.0, 20000.0, 300.0, 2.0, 7.0, 9e3)):
+        cond = oracle_lib.make_condition(T, 1.0, Q)
+        B = 2 * h * c ** 2 * nu ** 3 / math.expm1(h * c * nu / (k * T))
+        ratio = oracle_lib.emissivity(nu, El, A, g, cond) / oracle_lib.intensity(nu, El, A, g, cond)
+        assert ratio == pytest.approx(B, rel=1e-12)
+
+
+def test_emissivity_from_upper_state_population(oracle_lib):
+    """Emitted power per molecule and steradian = (fraction of molecules in the upper level)
+    x A x photon energy / 4 pi, with the upper level's Boltzmann fraction g' e^{-c2 E'/T}/Q."""
+    import scipy.constants as sc
+    c2 = sc.h * sc.c * 100.0 / sc.k
+    El, nu, gu, A, T, Q = 700.0, 2500.0, 9.0, 40.0, 2200.0, 3100.0
+    frac = gu * math.exp(-c2 * (El + nu) / T) / Q
+    expect = frac * A * (sc.h * 1e7) * (sc.c * 100.0) * nu / (4 * math.pi)
+    eps = oracle_lib.emissivity(nu, El, A, gu, oracle_lib.make_condition(T, 1.0, Q))
+    assert eps == pytest.approx(expect, rel=1e-12)
+
+
+def test_hitran_dynamic_threshold(oracle_lib):
+    """I_crit above nu_crit; below it, I_crit (nu/nu_crit) tanh(c2 nu/2T), which tends to
+    I_crit nu/nu_crit where c2 nu >> T and to I_crit c2 nu^2 / (2 T nu_crit) where c2 nu << T."""
+    o = oracle_lib.make_opts(threshold=("hitran", 2000.0, 1e-29))
+    assert oracle_lib.threshold(2500.0, 296.0, o) == 1e-29
+    assert oracle_lib.threshold(1999.0, 50.0, o) == pytest.approx(1e-29 * 1999.0 / 2000.0, rel=1e-12)
+    nu, T = 0.01, 3000.0
+    c2 = 1.438776877503933802
+    assert oracle_lib.threshold(nu, T, o) == pytest.approx(1e-29 * c2 * nu * nu / (2 * T * 2000.0), rel=1e-9)
+    assert oracle_lib.threshold(500.0, 1000.0, o) < oracle_lib.threshold(1000.0, 1000.0, o) < 1e-29
+    assert oracle_lib.threshold(123.0, 1000.0, oracle_lib.make_opts(threshold=("constant", 3e-25))) == 3e-25
+    assert oracle_lib.threshold(123.0, 1000.0, oracle_lib.make_opts()) == 0.0
+
+
+@pytest.mark.parametrize("quantity", ["absorption", "emission"])
+def test_threshold_leaves_out_exactly_the_weak_lines(oracle_lib, quantity):
+    """A cross section with a threshold equals the cross section of the sub-list of lines whose
+    strength (chosen in the test from the pinned intensity / emissivity) is at least the
+    threshold at their wavenumber."""
+    L = xs.gen_lines(33, 0, 400, 100.0, 3000.0)
+    T, Q = 900.0, 300.0
+    cond = oracle_lib.make_condition(T, 1.0, Q)
+    strength = oracle_lib.emissivity if quantity == "emission" else oracle_lib.intensity
+    S = np.array([strength(L["nu"][l], L["elower"][l], L["A"][l], L["g_up"][l], cond) for l in range(400)])
+    for thr in (("constant", float(np.median(S))), ("hitran", 2000.0, float(np.quantile(S, 0.3)))):
+        o = oracle_lib.make_opts("voigt_w4", 5.0, quantity=quantity, threshold=thr)
+        cut = np.array([oracle_lib.threshold(L["nu"][l], T, o) for l in range(400)])
+        keep = S >= cut
+        assert 50 < keep.sum() < 350
+        sub = {k: v[keep] for k, v in L.items()}
+        o0 = oracle_lib.make_opts("voigt_w4", 5.0, quantity=quantity)
+        a = oracle_lib.cross_section(L, cond, 95.0, 0.05, 58201, o, nthreads=2)
+        b = oracle_lib.cross_section(sub, cond, 95.0, 0.05, 58201, o0, nthreads=1)
+        assert np.allclose(a, b, rtol=1e-13, atol=0)
+    # emission sums emissivities, absorption intensities: their ratio line by line is Planck
+    if quantity == "emission":
+        one = {k: v[:1] for k, v in L.items()}
+        e = oracle_lib.cross_section(one, cond, 95.0, 0.05, 58201, oracle_lib.make_opts("doppler", 5.0, quantity="emission"))
+        a = oracle_lib.cross_section(one, cond, 95.0, 0.05, 58201, oracle_lib.make_opts("doppler", 5.0))
+        m = a > 0
+        assert np.allclose(e[m] / a[m], S[0] / oracle_lib.intensity(L["nu"][0], L["elower"][0], L["A"][0],
+                                                                    L["g_up"][0], cond), rtol=1e-13)
+
+
 # --------------------------------------------- widths, Eqs. (e:alphaD), (e:gamma_L)
 def test_doppler_hwhm_textbook_constant(oracle_lib):
     # alpha_D = 3.581e-7 * nu * sqrt(T / M[g/mol])  (the usual practical form)
@@ -464,6 +535,11 @@ def test_vjp_matches_central_differences(oracle_lib, profile):
     fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
     assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4)
     assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12)
+    # the adjoint covers absorption without a threshold only
+    for o2 in (oracle_lib.make_opts(profile, cut, quantity="emission"),
+               oracle_lib.make_opts(profile, cut, threshold=("constant", 1e-30))):
+        with pytest.raises(RuntimeError):
+            oracle_lib.cross_section_vjp(L, [c], nu_A, h, N, o2, gs)
 
 
 def test_point_evaluation_matches_full_grid(oracle_lib):
