@@ -72,6 +72,23 @@ enum { XC_ASSUME_SORTED = 1u };
  * accumulation); XC_OPT_NO_TENSOR_CORES keeps every evaluation on the CUDA cores. */
 enum { XC_OPT_NO_TENSOR_CORES = 1 };
 
+/* xc_opts.quantity: what each line contributes, times its profile */
+enum {
+    XC_ABSORPTION = 0,  /* absorption intensity I, Eq. (e:int): cm/molecule */
+    XC_EMISSION = 1     /* emissivity, Eq. (e:emiss), from the upper state E' = E'' + nu, times
+                           the photon energy h c nu so that it is in erg/s/sr per molecule (the
+                           unit the paper states; its printed formula leaves out h c) */
+};
+
+/* xc_opts.threshold (Sec. "Intensity thresholds"): lines whose strength (I, or the
+ * emissivity with XC_EMISSION) is below the threshold at their wavenumber are left out.
+ * The decision is taken in FP64 for every precision. */
+enum {
+    XC_THRESHOLD_NONE = 0,
+    XC_THRESHOLD_CONSTANT = 1,  /* I_cut */
+    XC_THRESHOLD_HITRAN = 2     /* I_crit (nu/nu_crit) tanh(c2 nu / 2T) for nu <= nu_crit, else I_crit */
+};
+
 typedef struct xc_handle xc_handle;
 
 /* Line list, structure of arrays, n entries each (28 bytes per line).
@@ -121,6 +138,11 @@ typedef struct {
     double width_mult;  /* 0 = fixed cut */
     int n_gh;
     int flags;          /* XC_OPT_* bits, 0 by default */
+    int quantity;       /* XC_ABSORPTION (default) or XC_EMISSION */
+    int threshold;      /* XC_THRESHOLD_* */
+    double I_cut;       /* constant threshold, >= 0, in the unit of the quantity */
+    double nu_crit;     /* HITRAN threshold: > 0, cm^-1 (the paper's default 2000) */
+    double I_crit;      /* HITRAN threshold: >= 0, in the unit of the quantity (default 1e-29) */
 } xc_opts;
 
 /* Library version string (static storage). */

@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = [
     "XcError", "Engine", "partition_function", "lib", "LIB_PATH", "make_condition", "make_grid", "make_opts",
-    "PROFILES", "PRECISIONS", "XC_MEM_HOST", "XC_MEM_DEVICE", "EXPORTED_SYMBOLS",
+    "PROFILES", "PRECISIONS", "QUANTITIES", "THRESHOLDS", "XC_MEM_HOST", "XC_MEM_DEVICE", "EXPORTED_SYMBOLS",
 ]
 
 LIB_PATH = _build.LIB
@@ -59,7 +59,13 @@ class XcGrid(C.Structure):
 
 class XcOpts(C.Structure):
     _fields_ = [("profile", C.c_int), ("precision", C.c_int), ("cutoff", C.c_double),
-                ("width_mult", C.c_double), ("n_gh", C.c_int), ("flags", C.c_int)]
+                ("width_mult", C.c_double), ("n_gh", C.c_int), ("flags", C.c_int),
+                ("quantity", C.c_int), ("threshold", C.c_int), ("I_cut", C.c_double),
+                ("nu_crit", C.c_double), ("I_crit", C.c_double)]
+
+
+QUANTITIES = {"absorption": 0, "emission": 1}
+THRESHOLDS = {"constant": 1, "hitran": 2}
 
 
 _lib = None
@@ -154,10 +160,20 @@ XC_OPT_NO_TENSOR_CORES = 1
 
 
 def make_opts(profile: str = "voigt_w4", precision: str = "fp64", cutoff: float = 25.0,
-              width_mult: float = 0.0, n_gh: int = 20, tensor_cores: bool = True) -> XcOpts:
-    """tensor_cores=False keeps the FP32 Voigt w4 far wings on the CUDA cores."""
+              width_mult: float = 0.0, n_gh: int = 20, tensor_cores: bool = True,
+              quantity: str = "absorption", threshold=None) -> XcOpts:
+    """tensor_cores=False keeps the FP32 Voigt w4 far wings on the CUDA cores.
+    quantity: "absorption" (Eq. e:int) or "emission" (Eq. e:emiss, times h c nu).
+    threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit)."""
+    mode, I_cut, nu_crit, I_crit = 0, 0.0, 0.0, 0.0
+    if threshold is not None:
+        mode = THRESHOLDS[threshold[0]]
+        if mode == 1:
+            I_cut = float(threshold[1])
+        else:
+            nu_crit, I_crit = float(threshold[1]), float(threshold[2])
     return XcOpts(PROFILES[profile], PRECISIONS[precision], float(cutoff), float(width_mult), int(n_gh),
-                  0 if tensor_cores else XC_OPT_NO_TENSOR_CORES)
+                  0 if tensor_cores else XC_OPT_NO_TENSOR_CORES, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit)
 
 
 _LINE_FIELDS = [("nu", np.float64), ("elower", np.float32), ("A", np.float32), ("gamma_ref", np.float32),

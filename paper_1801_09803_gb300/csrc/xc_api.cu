@@ -168,6 +168,23 @@ xc_status check_opts(const xc_opts *o) {
         set_error("n_gh must be in 1..64");
         return XC_EINVAL;
     }
+    if (o->quantity != XC_ABSORPTION && o->quantity != XC_EMISSION) {
+        set_error("unknown quantity %d", o->quantity);
+        return XC_EINVAL;
+    }
+    if (o->threshold < XC_THRESHOLD_NONE || o->threshold > XC_THRESHOLD_HITRAN) {
+        set_error("unknown threshold mode %d", o->threshold);
+        return XC_EINVAL;
+    }
+    if (o->threshold == XC_THRESHOLD_CONSTANT && !(o->I_cut >= 0.0 && isfinite(o->I_cut))) {
+        set_error("I_cut must be finite and >= 0");
+        return XC_EINVAL;
+    }
+    if (o->threshold == XC_THRESHOLD_HITRAN &&
+        !(o->nu_crit > 0.0 && isfinite(o->nu_crit) && o->I_crit >= 0.0 && isfinite(o->I_crit))) {
+        set_error("the HITRAN threshold needs nu_crit > 0 and a finite I_crit >= 0");
+        return XC_EINVAL;
+    }
     return XC_OK;
 }
 
@@ -275,7 +292,7 @@ xc_status cross_section_f64(xc_handle *h, const CondDev *dcond, const xc_grid *g
     int64_t *lo = h->ranges.as<int64_t>(), *hi = lo + n_win;
     stage_begin(h, ST_PARAMS, s);
     XC_TRY(launch_line_params64(lines_of(h), n, dcond, o->width_mult > 0.0 ? 1 : 0, o->cutoff, o->width_mult, I, al,
-                                ga, cut, s));
+                                ga, cut, s, strength_sel(*o)));
     stage_end(h, ST_PARAMS, s);
     stage_begin(h, ST_RANGES, s);
     XC_TRY(launch_window_ranges(h->nu, n, g->nu_A, g->step, g->n, W, o->cutoff, n_win, lo, hi, s));
@@ -715,6 +732,10 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
     if ((st = check_grid(grid)) || (st = check_opts(opts)) || (st = check_conds(conds, n_cond, h))) return st;
     if (opts->profile != XC_DOPPLER && opts->profile != XC_LORENTZ && opts->profile != XC_VOIGT_W4) {
         set_error("the adjoint supports Doppler, Lorentz and Voigt-w4 profiles");
+        return XC_EUNSUPPORTED;
+    }
+    if (opts->quantity != XC_ABSORPTION || opts->threshold != XC_THRESHOLD_NONE) {
+        set_error("the adjoint supports absorption without an intensity threshold");
         return XC_EUNSUPPORTED;
     }
     if (n_cond && (!grad_sigma || !dT || !dP)) { set_error("NULL grad_sigma / dT / dP"); return XC_EINVAL; }

@@ -62,6 +62,7 @@ struct CParam {
     float nshift;
     int row;            // output row (the caller's condition index)
     float dbound;       // upper bound of the far radius D4 over all lines (grid steps)
+    float emis;         // 1: emission (pref = abundance h c / (4 pi Q) * scale), 0: absorption
 };
 
 struct GeomStats {
@@ -161,7 +162,8 @@ __device__ double cond_width_key(const CondDev &d) {
 
 // Per-condition constants, stored in order of increasing profile width (stable), so that
 // the conditions sharing a tile have similar far-wing radii; row keeps the caller's index.
-__global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp, double step) {
+__global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp, double step,
+                          int quantity) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cond) return;
     const CondDev d = conds[c];
@@ -175,10 +177,14 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
     double kT = kC2 * log2e / d.T;
     float hi = (float)kT;
     float lo = (float)(kT - (double)hi);
-    double pref = d.abundance / (8.0 * kPi * kLightCm * d.Q);
+    const bool emis = quantity == XC_EMISSION;
+    double pref = emis ? d.abundance * kPlanckErg * kLightCm / (4.0 * kPi * d.Q)
+                       : d.abundance / (8.0 * kPi * kLightCm * d.Q);
     double s1 = (double)__uint_as_float(gs->gA_nu2_bits);
     double s2 = (double)__uint_as_float(gs->gA_nu_bits);
-    double ib = pref * fmin(s1, kC2 / d.T * s2);  // bound on the largest intensity
+    const double numax = (double)__uint_as_float(gs->nu_bits);
+    // bound on the largest intensity (absorption), or emissivity: g A nu <= max(g A / nu) nu_max^2
+    double ib = emis ? pref * s2 * numax * numax : pref * fmin(s1, kC2 / d.T * s2);
     int e2 = 0;
     if (ib > 0.0 && isfinite(ib)) {
         e2 = (int)floor(log2(1e10 / ib));
@@ -196,6 +202,7 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
     p.pscale = (float)(d.gamma_scale * d.P / d.P_ref);
     p.nshift = (float)d.n_shift;
     p.row = c;
+    p.emis = emis ? 1.f : 0.f;
     {
         // D4 <= ceil(sqrt(max(C k4, t2))) + 1 grows with both widths; t2 <= (15 a_h / sqrt ln2)^2.
         // Upper bounds of the widths from the line statistics (|n| <= nT_max), with margin.
@@ -413,8 +420,17 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     // Boltzmann factor exp(-c2 E/T) = 2^-(E c2 log2e / T), product kept to ~1 ulp
     float z = fmaf(E, c.kT_hi, E * c.kT_lo);
     float boltz = exp2_neg(z);
-    float stim = -expm1f(-c.c2T * nu);
-    float I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
+    float I;
+    if (c.emis != 0.f) {
+        // Eq. (e:emiss) times h c nu: the upper state's Boltzmann factor as exp(-c2 E''/T)
+        // exp(-c2 nu/T), each to ~1 ulp
+        I = c.pref * ((float)L.g_up[l] * L.A[l]) * nu * boltz * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo));
+    } else {
+        float stim = -expm1f(-c.c2T * nu);
+        I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
+    }
+    // left out by the intensity threshold for this condition (decided in FP64)
+    if (L.keep && !((L.keep[l * (size_t)L.keep_words + (c.row >> 5)] >> (c.row & 31)) & 1u)) I = 0.f;
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ah, gh;                                                              // widths in grid steps
     line_widths(nu, L.gamma_ref[l], L.n_T[l], c, inv_h, &ah, &gh);
@@ -1134,6 +1150,8 @@ struct TcParams {
     const float4 *phys;                // per line: nu, E'', g A / nu^2, gamma_ref (float)
     const float *n_T;                  // per line: temperature exponent
     const CParam *cp;
+    const uint32_t *keep;              // intensity-threshold decisions (see LinesDev::keep), or nullptr
+    int keep_words;
     const unsigned *blk_lo, *blk_hi;   // per TC_T-point super-block: line range
     int *counter;
     int *status;                       // set to 1 if a wait ran out
@@ -1155,7 +1173,9 @@ __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, c
                                                    float *p3) {
     const float nu = ph.x, E = ph.y;
     const float z = fmaf(E, c.kT_hi, E * c.kT_lo);
-    const float I = c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
+    const float I = c.emis != 0.f
+                        ? c.pref * (ph.z * (nu * nu * nu)) * exp2_neg(z) * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo))
+                        : c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
     float ah, gh;
     line_widths(nu, ph.w, nT, c, inv_h, &ah, &gh);
     const W4Zone zn = w4_zone(ah, gh);
@@ -1285,6 +1305,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
                     S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3);
+                    const size_t lg = (size_t)lo + (size_t)(l0 + lB);
+                    if (p.keep && !((p.keep[lg * (size_t)p.keep_words + (cpr.row >> 5)] >> (cpr.row & 31)) & 1u)) {
+                        S.x = S.y = S.z = 0.f;   // left out by the intensity threshold
+                        p3 = 0.f;
+                    }
                 }
                 const float p0h = tc::tf32_trunc(S.x), p1h = tc::tf32_trunc(S.y);
                 const float p0l = S.x - p0h, p1l = S.y - p1h, p2h = S.z;
@@ -1676,6 +1701,7 @@ struct Plan {
     unsigned *blk_lo = nullptr, *blk_hi = nullptr;
     int *tc_counter = nullptr, *tc_status = nullptr;
     float4 *tc_geo = nullptr, *tc_phys = nullptr;
+    uint32_t *keep = nullptr;                   // intensity-threshold decisions (with a threshold)
 };
 
 xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl,
@@ -1696,7 +1722,8 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_ord = carve((size_t)pl->n_tiles * 4), o_ctr = carve(64), o_gs = carve(64), o_nodes = carve(512);
     pl->n_win_core = (int)((a.grid.n + CORE_T - 1) / CORE_T);
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
-    size_t o_blo = 0, o_bhi = 0, o_tcc = 0, o_geo = 0, o_phys = 0;
+    size_t o_blo = 0, o_bhi = 0, o_tcc = 0, o_geo = 0, o_phys = 0, o_keep = 0;
+    if (a.opts.threshold != XC_THRESHOLD_NONE) o_keep = carve(n * (size_t)((n_cond_call + 31) / 32) * 4);
     if (tc) {
         pl->n_blk = (int)((a.grid.n + TC_T - 1) / TC_T);
         pl->n_tc_tiles = pl->n_blk * ((n_cond_call + TC_N - 1) / TC_N);
@@ -1722,6 +1749,7 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     pl->gw = pl->gx + 64;
     pl->core_lo = (unsigned *)(b + o_clo);
     pl->core_hi = (unsigned *)(b + o_chi);
+    if (a.opts.threshold != XC_THRESHOLD_NONE) pl->keep = (uint32_t *)(b + o_keep);
     if (tc) {
         pl->blk_lo = (unsigned *)(b + o_blo);
         pl->blk_hi = (unsigned *)(b + o_bhi);
@@ -1752,7 +1780,15 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
                                         per_cond_cut ? a.opts.width_mult : 0.0,
                                         per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
                                         pl.gs, pl.tc ? pl.tc_geo : nullptr, pl.tc ? pl.tc_phys : nullptr);
-    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step);
+    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step, a.opts.quantity);
+    LinesDev L = a.L;   // the lines as the profile kernels see them: with the threshold decisions
+    if (pl.keep) {
+        const int words = (nc + 31) / 32;
+        BT_TRY(launch_line_keep(a.L, n, a.conds_dev + c0, nc, strength_sel(a.opts), pl.keep, words, s));
+        L.keep = pl.keep;
+        L.keep_words = words;
+        *launches += 1;
+    }
     if (pl.tc)
         k_win_ranges_near<<<(pl.n_tiles + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step,
                                                                   a.grid.n, pl.W, a.opts.cutoff, pl.n_win,
@@ -1769,7 +1805,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     }
     BT_TRY(cudaMemsetAsync(pl.counter, 0, sizeof(int), s));
     GatherParams gp;
-    gp.L = a.L;
+    gp.L = L;
     gp.n_abs = pl.n_abs;
     gp.f_frac = pl.f;
     gp.ka_abs = pl.ka;
@@ -1804,6 +1840,8 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.phys = pl.tc_phys;
         tp.n_T = a.L.n_T;
         tp.cp = pl.cp;
+        tp.keep = L.keep;
+        tp.keep_words = L.keep_words;
         tp.blk_lo = pl.blk_lo;
         tp.blk_hi = pl.blk_hi;
         tp.counter = pl.tc_counter;
@@ -1832,7 +1870,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
                                                                    a.grid.n, K, pl.n_win_core, pl.core_lo,
                                                                    pl.core_hi);
         CoreParams cp;
-        cp.L = a.L;
+        cp.L = L;
         cp.n_abs = pl.n_abs;
         cp.f_frac = pl.f;
         cp.ka_abs = pl.ka;
@@ -1857,10 +1895,11 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
 bool use_tc(const BatchedArgs &a, int nc);
 
 std::string shape_key(const BatchedArgs &a, int nc) {
-    char buf[256];
-    snprintf(buf, sizeof(buf), "p%d n%zu c%d g%lld/%.17g/%.17g cut%.17g wm%.17g gh%d f%d tc%d", a.opts.profile,
-             a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff, a.opts.width_mult,
-             a.opts.n_gh, a.opts.flags, use_tc(a, nc) ? 1 : 0);
+    char buf[384];
+    snprintf(buf, sizeof(buf), "p%d n%zu c%d g%lld/%.17g/%.17g cut%.17g wm%.17g gh%d f%d tc%d q%d t%d/%.17g/%.17g/%.17g",
+             a.opts.profile, a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff,
+             a.opts.width_mult, a.opts.n_gh, a.opts.flags, use_tc(a, nc) ? 1 : 0, a.opts.quantity,
+             a.opts.threshold, a.opts.I_cut, a.opts.nu_crit, a.opts.I_crit);
     return buf;
 }
 
@@ -2273,6 +2312,10 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
     }
     if (opts->profile == XC_DOPPLER_BINNED || opts->profile == XC_LORENTZ_BINNED) {
         set_error("binned profiles: use xc_cross_section_batched");
+        return XC_EUNSUPPORTED;
+    }
+    if (opts->quantity != XC_ABSORPTION || opts->threshold != XC_THRESHOLD_NONE) {
+        set_error("emission and intensity thresholds: use xc_cross_section_batched");
         return XC_EUNSUPPORTED;
     }
     for (size_t i = 0; i < n_cond; ++i) {

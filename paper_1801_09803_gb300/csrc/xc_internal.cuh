@@ -27,6 +27,22 @@ constexpr double kSqrtLn2 = 0.8325546111576977563;
 constexpr double kSqrtPi = 1.772453850905516027;
 constexpr double kC2 = kPlanck * (kLightSI * 100.0) / kBoltzmann;  // second radiation constant, cm K
 constexpr double kLightCm = kLightSI * 100.0;
+constexpr double kPlanckErg = kPlanck * 1e7;                       // erg s
+
+// What a line contributes (absorption or emission) and the intensity threshold
+struct StrengthSel {
+    int quantity = XC_ABSORPTION, threshold = XC_THRESHOLD_NONE;
+    double I_cut = 0.0, nu_crit = 0.0, I_crit = 0.0;
+};
+inline StrengthSel strength_sel(const xc_opts &o) {
+    StrengthSel s;
+    s.quantity = o.quantity;
+    s.threshold = o.threshold;
+    s.I_cut = o.I_cut;
+    s.nu_crit = o.nu_crit;
+    s.I_crit = o.I_crit;
+    return s;
+}
 
 // w4 region-I constant (Humlicek 1982): w ~ t * 0.5641896 / (0.5 + t^2)
 constexpr double kW4c1 = 0.5641896;
@@ -38,6 +54,11 @@ struct LinesDev {
     const double *nu;
     const float *elower, *A, *gamma_ref, *n_T;
     const int16_t *g_up, *j_lo;
+    // intensity-threshold decisions of the FP32 kernels: bit c of word l * keep_words + c / 32
+    // set when line l is kept for condition c (in the order the launch's CParam rows name);
+    // nullptr: every line is kept
+    const uint32_t *keep = nullptr;
+    int keep_words = 0;
 };
 
 struct CondDev {  // mirrors xc_condition plus resolved Q
@@ -53,6 +74,29 @@ __host__ __device__ inline int64_t i64max(int64_t a, int64_t b) { return a > b ?
 __host__ __device__ inline double alpha_coef(double T, double mass_da) {
     // alpha_D / nu = sqrt(2 k T ln2 / m) / c   (Eq. e:alphaD)
     return sqrt(2.0 * kBoltzmann * T * kLn2 / (mass_da * kDalton)) / kLightSI;
+}
+
+// Line strength in FP64: the absorption intensity of Eq. (e:int), or with XC_EMISSION the
+// emissivity of Eq. (e:emiss) (upper state E' = E'' + nu) times the photon energy h c nu;
+// -1 when the intensity threshold leaves the line out.  pref_abs = abundance / (8 pi c Q).
+__device__ inline double line_strength64(double nu, double elower, double gA, const CondDev &c,
+                                         const StrengthSel &s) {
+    const double inv_T = 1.0 / c.T;
+    double S;
+    if (s.quantity == XC_EMISSION) {
+        S = c.abundance * gA * (kPlanckErg * kLightCm * nu) / (4.0 * kPi) * exp(-kC2 * (elower + nu) * inv_T) / c.Q;
+    } else {
+        const double boltz = exp(-kC2 * elower * inv_T);
+        const double stim = -expm1(-kC2 * nu * inv_T);
+        S = c.abundance / (8.0 * kPi * kLightCm * c.Q) * gA / (nu * nu) * boltz * stim;
+    }
+    if (s.threshold != XC_THRESHOLD_NONE) {
+        double thr = s.I_cut;
+        if (s.threshold == XC_THRESHOLD_HITRAN)
+            thr = nu > s.nu_crit ? s.I_crit : s.I_crit * (nu / s.nu_crit) * tanh(kC2 * nu * inv_T * 0.5);
+        if (S < thr) return -1.0;
+    }
+    return S;
 }
 
 // grid point nu_k = nu_A + k * step, rounded exactly as two separate operations
@@ -235,7 +279,10 @@ cudaError_t launch_sort_lines(const LinesDev &in, size_t n, bool assume_sorted, 
                               bool *bad_input, bool *unsorted);
 cudaError_t launch_line_params64(const LinesDev &L, size_t n, const CondDev *cond_dev, int cut_mode,
                                  double cutoff, double width_mult, double *I, double *alpha, double *gamma,
-                                 double *cut, cudaStream_t s);
+                                 double *cut, cudaStream_t s, const StrengthSel &sel = StrengthSel());
+// per (line, condition) threshold decisions for the FP32 kernels (see LinesDev::keep)
+cudaError_t launch_line_keep(const LinesDev &L, size_t n, const CondDev *conds, int nc, const StrengthSel &sel,
+                             uint32_t *keep, int words, cudaStream_t s);
 cudaError_t launch_window_ranges(const double *nu, size_t n, double nu_A, double step, int64_t n_pts,
                                  int64_t W, double cutmax, int64_t n_win, int64_t *lo, int64_t *hi,
                                  cudaStream_t s);

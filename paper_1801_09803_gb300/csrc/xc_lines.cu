@@ -65,35 +65,60 @@ __device__ inline double line_cut(int cut_mode, double cutoff, double width_mult
 
 __global__ void __launch_bounds__(256) k_line_params64(LinesDev L, size_t n, const CondDev *__restrict__ cd,
                                                        int cut_mode, double cutoff, double width_mult,
-                                                       double *I, double *alpha, double *gamma, double *cut) {
+                                                       double *I, double *alpha, double *gamma, double *cut,
+                                                       StrengthSel sel) {
     const CondDev c = *cd;
     const double inv_T = 1.0 / c.T;
-    const double pref = c.abundance / (8.0 * kPi * kLightCm * c.Q);
     const double acoef = alpha_coef(c.T, c.mass_da);
     const double lnTr = log(c.T_ref * inv_T);
     const double pscale = c.gamma_scale * (c.P / c.P_ref);
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
         double nu = L.nu[l];
-        double boltz = exp(-kC2 * (double)L.elower[l] * inv_T);
-        double stim = -expm1(-kC2 * nu * inv_T);
-        double Il = pref * (double)L.g_up[l] * (double)L.A[l] / (nu * nu) * boltz * stim;
+        double Il = line_strength64(nu, (double)L.elower[l], (double)L.g_up[l] * (double)L.A[l], c, sel);
         double al = acoef * nu;
         double ga = pscale * (double)L.gamma_ref[l] * exp(((double)L.n_T[l] + c.n_shift) * lnTr);
+        double cl = line_cut(cut_mode, cutoff, width_mult, al, ga);
+        if (Il < 0.0) {   // left out by the intensity threshold: no grid point is within a negative cut
+            Il = 0.0;
+            cl = -1.0;
+        }
         if (I) I[l] = Il;
         if (alpha) alpha[l] = al;
         if (gamma) gamma[l] = ga;
-        if (cut) cut[l] = line_cut(cut_mode, cutoff, width_mult, al, ga);
+        if (cut) cut[l] = cl;
     }
+}
+
+__global__ void __launch_bounds__(256) k_line_keep(LinesDev L, size_t n, const CondDev *__restrict__ conds, int nc,
+                                                   StrengthSel sel, uint32_t *keep, int words) {
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+        const double nu = L.nu[l], E = (double)L.elower[l], gA = (double)L.g_up[l] * (double)L.A[l];
+        for (int w = 0; w < words; ++w) {
+            uint32_t bits = 0u;
+            for (int b = 0; b < 32 && w * 32 + b < nc; ++b)
+                if (line_strength64(nu, E, gA, conds[w * 32 + b], sel) >= 0.0) bits |= 1u << b;
+            keep[l * (size_t)words + w] = bits;
+        }
+    }
+}
+
+cudaError_t launch_line_keep(const LinesDev &L, size_t n, const CondDev *conds, int nc, const StrengthSel &sel,
+                             uint32_t *keep, int words, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_line_keep<<<(unsigned)blocks, 256, 0, s>>>(L, n, conds, nc, sel, keep, words);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_params64(const LinesDev &L, size_t n, const CondDev *cond_dev, int cut_mode,
                                  double cutoff, double width_mult, double *I, double *alpha, double *gamma,
-                                 double *cut, cudaStream_t s) {
+                                 double *cut, cudaStream_t s, const StrengthSel &sel) {
     if (n == 0) return cudaSuccess;
     size_t blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_line_params64<<<(unsigned)blocks, 256, 0, s>>>(L, n, cond_dev, cut_mode, cutoff, width_mult, I, alpha,
-                                                     gamma, cut);
+                                                     gamma, cut, sel);
     return cudaGetLastError();
 }
 

@@ -53,10 +53,12 @@ def metrics(got, ref, frac=1e-6):
     return mr, band
 
 
-def oracle_sigma(oracle, lines, E, g, T, P, nu_A, step, n, profile, cut, wm=0.0, n_gh=20, **kw):
+def oracle_sigma(oracle, lines, E, g, T, P, nu_A, step, n, profile, cut, wm=0.0, n_gh=20, quantity="absorption",
+                 threshold=None, **kw):
     Q, dQ = oracle.partition_function(E, g, T)
     c = oracle.make_condition(T, P, Q, dQ, **kw)
-    return oracle.cross_section(lines, c, nu_A, step, n, oracle.make_opts(profile, cut, wm, n_gh),
+    return oracle.cross_section(lines, c, nu_A, step, n,
+                                oracle.make_opts(profile, cut, wm, n_gh, quantity=quantity, threshold=threshold),
                                 nthreads=NTHREADS)
 
 
@@ -376,6 +378,74 @@ def test_binned_profiles_on_a_coarse_grid(eng, xc, oracle_lib, profile):
                 assert float(np.sum(got64)) * step == pytest.approx(I, rel=1e-9)
     print(f"binned {profile} fp32 (6 conditions): worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
     assert worst[0] < TOL32 and worst[1] < TOL32_BAND
+
+
+def _strengths(oracle_lib, L, E, g, TP, quantity):
+    f = oracle_lib.emissivity if quantity == "emission" else oracle_lib.intensity
+    out = np.empty((len(TP), len(L["nu"])))
+    for j, (T, P) in enumerate(TP):
+        Q, _ = oracle_lib.partition_function(E, g, T)
+        c = oracle_lib.make_condition(T, P, Q)
+        out[j] = [f(L["nu"][l], L["elower"][l], L["A"][l], L["g_up"][l], c) for l in range(len(L["nu"]))]
+    return out
+
+
+@pytest.mark.parametrize("quantity", ["absorption", "emission"])
+def test_emission_and_intensity_thresholds(eng, xc, oracle_lib, quantity):
+    """Eq. (e:emiss) and the constant / HITRAN intensity thresholds, FP64 and the FP32 batched
+    sweep (18 conditions: far wings on the tensor cores).  Threshold values sit where no
+    (line, condition) strength is within 1e-6 of them, so the FP64 keep decisions are unique."""
+    L = xs.gen_lines(111, 0, 3000, 1000.0, 1040.0)
+    E, g = xs.gen_states(111, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    nu_A, step, n, cut = 995.0, 0.01, 5001, 5.0
+    TP = [(300.0 * 1.15 ** i, 0.02 * 1.5 ** i) for i in range(18)]
+    grid = xc.make_grid(nu_A, step, n)
+    S = _strengths(oracle_lib, L, E, g, TP, quantity)
+    # constant threshold: a value inside a gap of the sorted strengths near the median
+    srt = np.sort(S.ravel())
+    mid = len(srt) // 2
+    gaps = srt[mid - 500:mid + 500]
+    i = int(np.argmax(gaps[1:] / gaps[:-1]))
+    I_cut = float(np.sqrt(gaps[i] * gaps[i + 1]))
+    # HITRAN threshold: I_crit scaled so that it also sits away from every ratio S / (thr / I_crit)
+    o1 = oracle_lib.make_opts(threshold=("hitran", 1020.0, 1.0))
+    base = np.array([[oracle_lib.threshold(L["nu"][l], T, o1) for l in range(len(L["nu"]))] for T, _ in TP])
+    r = np.sort((S / base).ravel())
+    rm = r[len(r) // 2 - 500:len(r) // 2 + 500]
+    k = int(np.argmax(rm[1:] / rm[:-1]))
+    I_crit = float(np.sqrt(rm[k] * rm[k + 1]))
+    for thr in (None, ("constant", I_cut), ("hitran", 1020.0, I_crit)):
+        sel = [0, 7, 17]
+        refs = {j: oracle_sigma(oracle_lib, L, E, g, TP[j][0], TP[j][1], nu_A, step, n, "voigt_w4", cut,
+                                quantity=quantity, threshold=thr) for j in sel}
+        if thr is not None:
+            kept = S >= (I_cut if thr[0] == "constant" else I_crit * base)
+            assert 0.2 < kept.mean() < 0.8
+        for j in sel[:2]:
+            got = eng.cross_section(xc.make_condition(*TP[j]), grid,
+                                    xc.make_opts("voigt_w4", "fp64", cut, quantity=quantity, threshold=thr))
+            m64, b64 = metrics(got, refs[j])
+            assert m64 < TOL64 and b64 < TOL64, (thr, j, m64, b64)
+        conds = [xc.make_condition(T, P) for T, P in TP]
+        eng.set_timing(True)
+        try:
+            got = eng.cross_section_batched(conds, grid, xc.make_opts("voigt_w4", "fp32", cut, quantity=quantity,
+                                                                      threshold=thr))
+            assert eng.sweep_kernels()[3] > 0   # the tensor-core kernel took the far wings
+        finally:
+            eng.set_timing(False)
+        cu = eng.cross_section_batched(conds, grid, xc.make_opts("voigt_w4", "fp32", cut, tensor_cores=False,
+                                                                 quantity=quantity, threshold=thr))
+        worst = (0.0, 0.0)
+        for j in sel:
+            mr, band = metrics(got[j], refs[j])
+            worst = (max(worst[0], mr), max(worst[1], band))
+            mc, _ = metrics(got[j], cu[j])
+            assert mc < 2e-5, (thr, j, mc)
+        print(f"{quantity} threshold {thr}: fp32 batched worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
+        assert worst[0] < TOL32 and worst[1] < TOL32_BAND, (thr, worst)
 
 
 def test_c1_full_size(eng, xc, oracle_lib):
