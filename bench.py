@@ -258,7 +258,9 @@ def _timed(torch, fn, reps=1):
 def secondary_measurements(xc, torch, dev):
     """The other workloads, one timing each (CUDA events, device-resident inputs):
     C1 (1e5 lines, FP64 plain and FP32), C2 (1e7 lines, width-limited cut, Voigt w4
-    FP64 plain and FP32; GH binned, binned Gaussian and binned Lorentzian FP32), C4 (1e7 lines, 2x2 conditions: FP32
+    FP64 plain and FP32; GH binned, binned Gaussian and binned Lorentzian FP32; Voigt w4 FP32
+    emission and with the HITRAN threshold, whose eval count still includes the lines it
+    leaves out), C4 (1e7 lines, 2x2 conditions: FP32
     forward and FP32 adjoint).  Values are evals/s over the exact eval count."""
     out = {}
     for name in ("C1", "C2", "C4"):
@@ -272,14 +274,17 @@ def secondary_measurements(xc, torch, dev):
         conds = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da) for c in xs.conditions_for(W)]
         sig = torch.empty((len(conds), W.n_points), dtype=torch.float64, device=dev)
         res = {}
-        cases = [("voigt_w4", "fp32")] if name == "C4" else [("voigt_w4", "fp64"), ("voigt_w4", "fp32")]
+        cases = [("voigt_w4", "fp32", {})] if name == "C4" else [("voigt_w4", "fp64", {}), ("voigt_w4", "fp32", {})]
         if name == "C2":
-            cases += [("voigt_gh_binned", "fp32"), ("doppler_binned", "fp32"), ("lorentz_binned", "fp32")]
-        for prof, prec in cases:
-            o = xc.make_opts(prof, prec, W.cutoff, W.cutoff_width_mult, W.n_gh)
+            cases += [("voigt_gh_binned", "fp32", {}), ("doppler_binned", "fp32", {}), ("lorentz_binned", "fp32", {}),
+                      ("voigt_w4", "fp32", {"quantity": "emission"}),
+                      ("voigt_w4", "fp32", {"threshold": ("hitran", 2000.0, 1e-29)})]
+        for prof, prec, kw in cases:
+            o = xc.make_opts(prof, prec, W.cutoff, W.cutoff_width_mult, W.n_gh, **kw)
             ev = eng.count_evals(conds, grid, o)
             ms = _timed(torch, lambda: eng.cross_section_batched(conds, grid, o, sig))
-            res[f"{prof}_{prec}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+            tag = "_emission" if kw.get("quantity") == "emission" else ("_hitran_threshold" if "threshold" in kw else "")
+            res[f"{prof}_{prec}{tag}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
         if name == "C4":
             o = xc.make_opts("voigt_w4", "fp32", W.cutoff)
             gs = torch.ones((len(conds), W.n_points), dtype=torch.float64, device=dev)
