@@ -48,6 +48,35 @@ class Opts(C.Structure):
 QUANTITIES = {"absorption": 0, "emission": 1}
 
 
+class Broadener(C.Structure):
+    _fields_ = [("type", C.c_int), ("fraction", C.c_double), ("gamma0", C.c_double), ("n", C.c_double),
+                ("n_entries", C.c_longlong), ("j_lo", C.c_void_p), ("j_up", C.c_void_p),
+                ("gamma0_j", C.c_void_p), ("n_j", C.c_void_p)]
+
+
+BROAD_TYPES = {"constant": 0, "a0": 1, "a1": 2}
+
+
+def make_broadener(kind: str, fraction: float, gamma0: float, n: float, table=None) -> Broadener:
+    """One broadener: kind "constant", "a0" (table {J'': (gamma0, n)}) or "a1" (table
+    {(J'', J'): (gamma0, n)}); gamma0 / n are the defaults for lines the table does not list."""
+    t = BROAD_TYPES[kind]
+    rows = sorted((table or {}).items())
+    jl = np.array([k if t == 1 else k[0] for k, _ in rows], np.int32)
+    ju = np.array([k[1] for k, _ in rows] if t == 2 else [], np.int32)
+    g0 = np.array([v[0] for _, v in rows], np.float64)
+    nn = np.array([v[1] for _, v in rows], np.float64)
+    b = Broadener(t, float(fraction), float(gamma0), float(n), len(rows), _p(jl), _p(ju) if t == 2 else None,
+                  _p(g0), _p(nn))
+    b._keep = (jl, ju, g0, nn)   # the arrays the pointers refer to
+    return b
+
+
+def _broad_array(broadeners):
+    arr = (Broadener * len(broadeners))(*broadeners)
+    return arr
+
+
 def build(force: bool = False) -> str:
     """Compile xo.c into liboracle.so (plain gcc; OpenMP for the threaded baseline)."""
     with _lock:
@@ -74,6 +103,11 @@ def lib():
         L.xo_emissivity.restype = d
         L.xo_threshold.argtypes = [d, d, C.POINTER(Opts)]
         L.xo_threshold.restype = d
+        L.xo_gamma_mixture.argtypes = [i, i, vp, i, C.POINTER(Condition)]
+        L.xo_gamma_mixture.restype = d
+        L.xo_cross_section_broad.argtypes = [vp] * 6 + [C.c_size_t, vp, i, C.POINTER(Condition), d, d,
+                                                        C.c_longlong, C.POINTER(Opts), vp, i]
+        L.xo_cross_section_broad.restype = i
         L.xo_intensity.restype = d
         L.xo_alpha_doppler.argtypes = [d, C.POINTER(Condition)]
         L.xo_alpha_doppler.restype = d
@@ -158,6 +192,33 @@ def intensity(nu, elower, A, g_up, cond: Condition) -> float:
 def emissivity(nu, elower, A, g_up, cond: Condition) -> float:
     """Eq. (e:emiss) times the photon energy h c nu: erg/s/sr per molecule."""
     return lib().xo_emissivity(float(nu), float(elower), float(A), float(g_up), C.byref(cond))
+
+
+def gamma_mixture(j_lo, j_up, broadeners, cond: Condition) -> float:
+    """Lorentz HWHM of a line with these J under a mixture of broadeners."""
+    arr = _broad_array(broadeners)
+    return lib().xo_gamma_mixture(int(j_lo), int(j_up), C.cast(arr, C.c_void_p), len(broadeners), C.byref(cond))
+
+
+def cross_section_broad(lines, j_up, broadeners, cond: Condition, nu_A, step, n_pts, opts: Opts,
+                        nthreads: Optional[int] = None) -> np.ndarray:
+    """Cross section with every line's Lorentz HWHM from the broadener mixture (J'' from
+    lines["j_lo"], J' from j_up)."""
+    nu = np.ascontiguousarray(lines["nu"], np.float64)
+    el = np.ascontiguousarray(lines["elower"], np.float32)
+    A = np.ascontiguousarray(lines["A"], np.float32)
+    jl = np.ascontiguousarray(lines["j_lo"], np.int16)
+    ju = np.ascontiguousarray(j_up, np.int16)
+    g = np.ascontiguousarray(lines["g_up"], np.int16)
+    out = np.zeros(max(int(n_pts), 0))
+    arr = _broad_array(broadeners)
+    nt = nthreads or min(16, os.cpu_count() or 1)
+    rc = lib().xo_cross_section_broad(_p(nu), _p(el), _p(A), _p(jl), _p(ju), _p(g), len(nu), C.cast(arr, C.c_void_p),
+                                      len(broadeners), C.byref(cond), float(nu_A), float(step), int(n_pts),
+                                      C.byref(opts), _p(out), int(nt))
+    if rc != 0:
+        raise RuntimeError(f"xo_cross_section_broad failed: {rc}")
+    return out
 
 
 def threshold(nu, T, opts: Opts) -> float:

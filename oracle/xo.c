@@ -14,6 +14,10 @@
  *   eps_fi        Eq. (e:emiss) LTE emissivity from the upper state (E' = E'' + nu),
  *                 with the photon energy h c nu so that it comes out in the unit the
  *                 text gives (erg/s/sr per molecule; the printed formula omits h c)
+ *   broadening    Sec. "Broadening parameters" (.broad): per broadener a constant
+ *                 (gamma_0, n_L), or a table by J'' (a0) or by (J'', J') (a1), with the
+ *                 broadener's defaults for a line whose quantum numbers it does not
+ *                 list; Sec. "Mixtures of broadeners": gamma_L = sum_i rho_i gamma_i
  *   thresholds    Sec. "Intensity thresholds": constant, or HITRAN's dynamic
  *                 I_crit (nu/nu_crit) tanh(c2 nu / 2T) below nu_crit, I_crit above;
  *                 a line whose intensity (or emissivity) is below it is left out
@@ -159,6 +163,58 @@ double xo_alpha_doppler(double nu, const xo_condition *c)
 double xo_gamma_lorentz(double gamma_ref, double n_T, const xo_condition *c)
 {
     return c->gamma_scale * gamma_ref * pow(c->T_ref / c->T, n_T + c->n_shift) * (c->P / c->P_ref);
+}
+
+/* One broadener of a mixture (Sec. "Broadening parameters", "Mixtures of broadeners") */
+typedef struct {
+    int type;                    /* 0: constant, 1: a0 (by J''), 2: a1 (by J'' and J') */
+    double fraction;             /* rho_i */
+    double gamma0, n;            /* the constant values, and the default for unlisted lines */
+    long long n_entries;
+    const int32_t *j_lo, *j_up;  /* table keys (j_up for a1 only) */
+    const double *gamma0_j, *n_j;
+} xo_broadener;
+
+/* gamma_0 and n_L of broadener b for a line with lower / upper J */
+static void broad_lookup(const xo_broadener *b, int jl, int ju, double *g0, double *n)
+{
+    *g0 = b->gamma0;
+    *n = b->n;
+    if (b->type == 0) return;
+    for (long long i = 0; i < b->n_entries; ++i) {
+        if (b->j_lo[i] != jl) continue;
+        if (b->type == 2 && b->j_up[i] != ju) continue;
+        *g0 = b->gamma0_j[i];
+        *n = b->n_j[i];
+        return;
+    }
+}
+
+/* Lorentz HWHM of a line under a mixture: sum_i rho_i gamma_0,i (T_ref/T)^(n_i + n_shift)
+ * P/P_ref, times the global gamma_scale (the single-broadener form of Eq. e:gamma_L per term) */
+double xo_gamma_mixture(int jl, int ju, const xo_broadener *b, int nb, const xo_condition *c)
+{
+    double g = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        double g0, n;
+        broad_lookup(&b[i], jl, ju, &g0, &n);
+        g += b[i].fraction * g0 * pow(c->T_ref / c->T, n + c->n_shift);
+    }
+    return c->gamma_scale * g * (c->P / c->P_ref);
+}
+
+/* where a line's Lorentz HWHM comes from: its own (gamma_ref, n_T), or a mixture */
+typedef struct {
+    const float *gamma_ref, *n_T;
+    const int16_t *j_lo, *j_up;
+    const xo_broadener *b;
+    int nb;
+} xo_gsrc;
+
+static double line_gamma(const xo_gsrc *g, size_t l, const xo_condition *c)
+{
+    if (g->nb > 0) return xo_gamma_mixture(g->j_lo[l], g->j_up ? g->j_up[l] : 0, g->b, g->nb, c);
+    return xo_gamma_lorentz(g->gamma_ref[l], g->n_T[l], c);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -475,10 +531,32 @@ static long long grid_floor_index(double x, double nu_A, double h)
     return (long long)floor((x - nu_A) / h);
 }
 
+static int cross_section_impl(const double *nu, const float *elower, const float *A, const xo_gsrc *gsrc,
+                              const int16_t *g_up, size_t n_lines, const xo_condition *cond, double nu_A,
+                              double h, long long n_pts, const xo_opts *o, double *sigma, int nthreads);
+
 int xo_cross_section(const double *nu, const float *elower, const float *A, const float *gamma_ref,
                      const float *n_T, const int16_t *g_up, size_t n_lines,
                      const xo_condition *cond, double nu_A, double h, long long n_pts,
                      const xo_opts *o, double *sigma, int nthreads)
+{
+    xo_gsrc g = {gamma_ref, n_T, NULL, NULL, NULL, 0};
+    return cross_section_impl(nu, elower, A, &g, g_up, n_lines, cond, nu_A, h, n_pts, o, sigma, nthreads);
+}
+
+/* the same with every line's Lorentz HWHM from a mixture of .broad broadeners */
+int xo_cross_section_broad(const double *nu, const float *elower, const float *A, const int16_t *j_lo,
+                           const int16_t *j_up, const int16_t *g_up, size_t n_lines, const xo_broadener *b,
+                           int nb, const xo_condition *cond, double nu_A, double h, long long n_pts,
+                           const xo_opts *o, double *sigma, int nthreads)
+{
+    xo_gsrc g = {NULL, NULL, j_lo, j_up, b, nb};
+    return cross_section_impl(nu, elower, A, &g, g_up, n_lines, cond, nu_A, h, n_pts, o, sigma, nthreads);
+}
+
+static int cross_section_impl(const double *nu, const float *elower, const float *A, const xo_gsrc *gsrc,
+                              const int16_t *g_up, size_t n_lines, const xo_condition *cond, double nu_A,
+                              double h, long long n_pts, const xo_opts *o, double *sigma, int nthreads)
 {
     if (n_pts <= 0) return 0;
     double xg[200], wg[200];
@@ -503,7 +581,7 @@ int xo_cross_section(const double *nu, const float *elower, const float *A, cons
             double Ifi = line_strength(o, nul, elower[l], A[l], g_up[l], cond);
             if (Ifi < 0.0) continue;   /* below the intensity threshold */
             double al = xo_alpha_doppler(nul, cond);
-            double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cond);
+            double ga = line_gamma(gsrc, l, cond);
             double cut = line_cut(o, al, ga);
             long long k0 = grid_floor_index(nul - cut, nu_A, h) - 1;
             long long k1 = grid_floor_index(nul + cut, nu_A, h) + 1;

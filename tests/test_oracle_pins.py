@@ -161,6 +161,68 @@ def test_threshold_leaves_out_exactly_the_weak_lines(oracle_lib, quantity):
                                                                     L["g_up"][0], cond), rtol=1e-13)
 
 
+# --------------------------------------------- .broad broadening and mixtures
+def _read_broad(path):
+    rows = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        code, g0, n, j = line.split()
+        assert code == "a0"
+        rows[int(j)] = (float(g0), float(n))
+    return rows
+
+
+def test_broad_a0_table_from_the_paper(oracle_lib):
+    """The a0 rows printed for CS in air: at T_ref and P_ref each listed J'' gets its own
+    gamma_0; an unlisted J'' the broadener's default; away from T_ref the row's n_L applies."""
+    import os
+    rows = _read_broad(os.path.join(os.path.dirname(__file__), "golden", "cs_air_a0_broad.txt"))
+    assert len(rows) == 7 and rows[3] == (0.0840, 0.089)
+    b = oracle_lib.make_broadener("a0", 1.0, 0.07, 0.5, rows)
+    ref = oracle_lib.make_condition(296.0, 1.0, 1.0)
+    for j, (g0, n) in rows.items():
+        assert oracle_lib.gamma_mixture(j, j + 1, [b], ref) == pytest.approx(g0, rel=1e-15)
+        hot = oracle_lib.make_condition(1184.0, 2.0, 1.0)   # T_ref / T = 1/4
+        assert oracle_lib.gamma_mixture(j, j, [b], hot) == pytest.approx(g0 * 0.25 ** n * 2.0, rel=1e-14)
+    assert oracle_lib.gamma_mixture(10, 11, [b], ref) == pytest.approx(0.07, rel=1e-15)
+
+
+def test_broad_a1_and_mixture_are_weighted_single_broadeners(oracle_lib):
+    """a1 keys on (J'', J'); a mixture's HWHM is the rho-weighted sum of each broadener's
+    Eq. (e:gamma_L) value (pinned separately), whatever their exponents."""
+    a1 = oracle_lib.make_broadener("a1", 0.7, 0.05, 0.6, {(3, 4): (0.08, 0.7), (3, 2): (0.06, 0.4)})
+    cst = oracle_lib.make_broadener("constant", 0.3, 0.03, 0.25)
+    for T, P in ((296.0, 1.0), (900.0, 0.3), (2500.0, 7.0)):
+        c = oracle_lib.make_condition(T, P, 1.0, gamma_scale=1.1, n_shift=0.05)
+        for (jl, ju), (g0, n) in (((3, 4), (0.08, 0.7)), ((3, 2), (0.06, 0.4)), ((3, 3), (0.05, 0.6))):
+            expect = 0.7 * oracle_lib.gamma_lorentz(g0, n, c) + 0.3 * oracle_lib.gamma_lorentz(0.03, 0.25, c)
+            assert oracle_lib.gamma_mixture(jl, ju, [a1, cst], c) == pytest.approx(expect, rel=1e-14)
+    # two halves of one broadener are that broadener
+    half = oracle_lib.make_broadener("constant", 0.5, 0.03, 0.25)
+    one = oracle_lib.make_broadener("constant", 1.0, 0.03, 0.25)
+    c = oracle_lib.make_condition(700.0, 3.0, 1.0)
+    assert oracle_lib.gamma_mixture(0, 1, [half, half], c) == pytest.approx(oracle_lib.gamma_mixture(0, 1, [one], c),
+                                                                            rel=1e-15)
+
+
+def test_cross_section_with_a0_broadening_equals_per_line_widths(oracle_lib):
+    """One a0 broadener (rho = 1) gives the cross section of the same lines with gamma_ref and
+    n_T set to their table rows (values exact in float32)."""
+    L = xs.gen_lines(34, 0, 300, 1000.0, 1010.0)
+    table = {j: (0.0625 + 0.001953125 * (j % 7), 0.5 + 0.0625 * (j % 3)) for j in range(0, 40, 2)}
+    b = oracle_lib.make_broadener("a0", 1.0, 0.046875, 0.75, table)
+    j_up = (L["g_up"].astype(np.int32) - 1) // 2
+    L2 = dict(L)
+    L2["gamma_ref"] = np.array([table.get(int(j), (0.046875, 0.75))[0] for j in L["j_lo"]], np.float32)
+    L2["n_T"] = np.array([table.get(int(j), (0.046875, 0.75))[1] for j in L["j_lo"]], np.float32)
+    cond = oracle_lib.make_condition(1300.0, 0.8, 400.0)
+    o = oracle_lib.make_opts("voigt_w4", 3.0)
+    a = oracle_lib.cross_section_broad(L, j_up, [b], cond, 995.0, 0.01, 2001, o, nthreads=2)
+    ref = oracle_lib.cross_section(L2, cond, 995.0, 0.01, 2001, o, nthreads=1)
+    assert np.allclose(a, ref, rtol=1e-14, atol=0) and ref.max() > 0
+
+
 # --------------------------------------------- widths, Eqs. (e:alphaD), (e:gamma_L)
 def test_doppler_hwhm_textbook_constant(oracle_lib):
     # alpha_D = 3.581e-7 * nu * sqrt(T / M[g/mol])  (the usual practical form)
