@@ -179,6 +179,35 @@ xc_status xc_get_lines(xc_handle *h, double *nu, float *elower, float *A, float 
 /* Sorted position -> input position (uint32, n entries). */
 xc_status xc_get_permutation(xc_handle *h, uint32_t *perm_out, int mem, void *stream);
 
+/* .broad broadening schemes of one broadener (Sec. "Broadening parameters") */
+enum { XC_BROAD_CONSTANT = 0, XC_BROAD_A0 = 1, XC_BROAD_A1 = 2 };
+
+/* One broadener of a mixture (Secs. "Broadening parameters", "Mixtures of broadeners").
+ * All table arrays are host memory, n_entries rows each. */
+typedef struct {
+    int type;                 /* XC_BROAD_CONSTANT, XC_BROAD_A0 (key J'') or XC_BROAD_A1 (J'', J') */
+    double fraction;          /* rho_i >= 0: the broadener's share of the mixture */
+    double gamma0, n;         /* gamma_0 at T_ref, P_ref (cm^-1) and n_L: the constant values,
+                                 and the defaults for lines the table does not list */
+    int64_t n_entries;        /* table rows (a0, a1), <= 2^20 */
+    const int32_t *j_lo;      /* J'' of each row */
+    const int32_t *j_up;      /* J' of each row (a1; may be NULL otherwise) */
+    const double *gamma0_j;   /* gamma_0 of each row (>= 0, finite) */
+    const double *n_j;        /* n_L of each row (finite) */
+} xc_broadener;
+
+/* Lorentz widths from a mixture of .broad broadeners instead of the line list's gamma_ref
+ * and n_T: gamma_L = gamma_scale P/P_ref sum_i rho_i gamma_0,i (T_ref/T)^(n_L,i + n_shift),
+ * each term Eq. (e:gamma_L) of the paper, the sum its Sec. "Mixtures of broadeners".
+ * a0 finds a line's row by its J'' (j_lo of the loaded lines), a1 by J'' and J'
+ * (j_up: one int16 per line in the order given to xc_load_lines, host or device per mem;
+ * may be NULL when no broadener is a1); a line without a row takes gamma0 and n.
+ * At most 8 broadeners; duplicate table keys, negative widths or fractions: EINVAL.
+ * n_broadeners = 0 returns to the line list's widths, as does the next xc_load_lines.
+ * Synchronises `stream`.  The adjoint does not support a mixture (EUNSUPPORTED). */
+xc_status xc_set_broadening(xc_handle *h, const xc_broadener *b, int n_broadeners, const int16_t *j_up, int mem,
+                            void *stream);
+
 /* Give the handle a state list (E term values cm^-1 float64, total degeneracy
  * g int32 >= 0) for conditions with Q <= 0.  Paper Eq. (e:pf). */
 xc_status xc_set_states(xc_handle *h, const double *E, const int32_t *g, size_t n_states,

@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = [
     "XcError", "Engine", "partition_function", "lib", "LIB_PATH", "make_condition", "make_grid", "make_opts",
-    "PROFILES", "PRECISIONS", "QUANTITIES", "THRESHOLDS", "XC_MEM_HOST", "XC_MEM_DEVICE", "EXPORTED_SYMBOLS",
+    "PROFILES", "PRECISIONS", "QUANTITIES", "THRESHOLDS", "make_broadener", "XC_MEM_HOST", "XC_MEM_DEVICE", "EXPORTED_SYMBOLS",
 ]
 
 LIB_PATH = _build.LIB
@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
     "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static", "xc_set_tile_shape",
-    "xc_last_sweep_kernels",
+    "xc_last_sweep_kernels", "xc_set_broadening",
 ]
 
 
@@ -65,6 +65,28 @@ class XcOpts(C.Structure):
 
 
 QUANTITIES = {"absorption": 0, "emission": 1}
+BROAD_TYPES = {"constant": 0, "a0": 1, "a1": 2}
+
+
+class XcBroadener(C.Structure):
+    _fields_ = [("type", C.c_int), ("fraction", C.c_double), ("gamma0", C.c_double), ("n", C.c_double),
+                ("n_entries", C.c_int64), ("j_lo", C.c_void_p), ("j_up", C.c_void_p), ("gamma0_j", C.c_void_p),
+                ("n_j", C.c_void_p)]
+
+
+def make_broadener(kind: str, fraction: float, gamma0: float, n: float, table=None) -> XcBroadener:
+    """One .broad broadener: kind "constant", "a0" (table {J'': (gamma0, n)}) or "a1" (table
+    {(J'', J'): (gamma0, n)}); gamma0 / n are the defaults for lines the table does not list."""
+    t = BROAD_TYPES[kind]
+    rows = sorted((table or {}).items())
+    jl = np.array([k if t == 1 else k[0] for k, _ in rows], np.int32)
+    ju = np.array([k[1] for k, _ in rows] if t == 2 else [], np.int32)
+    g0 = np.array([v[0] for _, v in rows], np.float64)
+    nn = np.array([v[1] for _, v in rows], np.float64)
+    b = XcBroadener(t, float(fraction), float(gamma0), float(n), len(rows), jl.ctypes.data,
+                    ju.ctypes.data if t == 2 else None, g0.ctypes.data, nn.ctypes.data)
+    b._keep = (jl, ju, g0, nn)   # the arrays the pointers refer to
+    return b
 THRESHOLDS = {"constant": 1, "hitran": 2}
 
 
@@ -104,6 +126,7 @@ def lib(build_if_missing: bool = False):
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
         "xc_get_tuning": ([vp, C.c_char_p, st], i),
         "xc_set_tile_shape": ([vp, i, i], i),
+        "xc_set_broadening": ([vp, vp, i, vp, i, vp], i),
         "xc_last_sweep_kernels": ([vp, vp, C.POINTER(C.c_int64)], i),
         "xc_cross_section_batched_static": ([C.POINTER(XcLines), st, vp, vp, st, C.POINTER(XcCondition), st,
                                              C.POINTER(XcGrid), C.POINTER(XcOpts), vp, vp], i),
@@ -274,6 +297,14 @@ class Engine:
         E = np.ascontiguousarray(E, np.float64)
         g = np.ascontiguousarray(g, np.int32)
         _check(lib().xc_set_states(self._h, E.ctypes.data, g.ctypes.data, len(E), XC_MEM_HOST, None))
+
+    def set_broadening(self, broadeners, j_up=None):
+        """Lorentz widths from a mixture of .broad broadeners (make_broadener); j_up: J' of every
+        line in load order (needed by a1 tables).  An empty list returns to the lines' widths."""
+        arr = (XcBroadener * max(1, len(broadeners)))(*broadeners)
+        ju = None if j_up is None else np.ascontiguousarray(j_up, np.int16)
+        _check(lib().xc_set_broadening(self._h, C.cast(arr, C.c_void_p), len(broadeners),
+                                       None if ju is None else ju.ctypes.data, XC_MEM_HOST, None))
 
     # ---------------------------------------------------------------- compute
     def line_params(self, cond: XcCondition):

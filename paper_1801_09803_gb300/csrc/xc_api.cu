@@ -59,6 +59,8 @@ struct xc_handle {
     DevBuf gh;               // Gauss-Hermite nodes (x then w)
     DevBuf misc;             // counters
     DevBuf vjp;              // adjoint scratch
+    DevBuf broad;            // broadener mixture: per broadener rho gamma_0 and n_L per line, tables
+    int n_broad = 0;         // broadeners in use (0: the line list's gamma_ref, n_T)
     int gh_n = 0;
     bool timing = false;
     cudaEvent_t ev[2 * ST_COUNT + 4] = {};
@@ -263,7 +265,14 @@ xc_status resolve_conds(xc_handle *h, const xc_condition *conds, size_t n, cudaS
 }
 
 LinesDev lines_of(const xc_handle *h) {
-    return LinesDev{h->nu, h->elower, h->A, h->gamma_ref, h->n_T, h->g_up, h->j_lo};
+    LinesDev L{h->nu, h->elower, h->A, h->gamma_ref, h->n_T, h->g_up, h->j_lo};
+    if (h->n_broad > 0) {
+        L.bgam = h->broad.as<double>();
+        L.bn = L.bgam + (size_t)h->n_broad * h->n_lines;
+        L.bstride = h->n_lines;
+        L.n_broad = h->n_broad;
+    }
+    return L;
 }
 
 xc_status ensure_gh(xc_handle *h, int n, cudaStream_t s) {
@@ -385,6 +394,7 @@ xc_status xc_destroy(xc_handle *h) {
     h->gh.release();
     h->misc.release();
     h->vjp.release();
+    h->broad.release();
     batched_release(&h->batched);
     for (auto &ev : h->ev)
         if (ev) cudaEventDestroy(ev);
@@ -419,6 +429,7 @@ xc_status xc_load_lines(xc_handle *h, const xc_lines *L, size_t n, unsigned flag
         h->cap_lines = n;
     }
     h->n_lines = 0;
+    h->n_broad = 0;   // a broadener mixture belongs to the lines it was set for
     // graphs and tuning stay valid: they key on shapes and buffer addresses, and read the
     // line data when replayed
     if (n == 0) return XC_OK;
@@ -497,6 +508,117 @@ xc_status xc_get_lines(xc_handle *h, double *nu, float *elower, float *A, float 
     if (g_up) XC_TRY(cudaMemcpyAsync(g_up, h->g_up, n * 2, k, s));
     if (j_lo) XC_TRY(cudaMemcpyAsync(j_lo, h->j_lo, n * 2, k, s));
     if (mem == XC_MEM_HOST) XC_TRY(cudaStreamSynchronize(s));
+    return XC_OK;
+}
+
+xc_status xc_set_broadening(xc_handle *h, const xc_broadener *b, int n_broadeners, const int16_t *j_up, int mem,
+                            void *stream) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (n_broadeners < 0 || n_broadeners > 8) { set_error("0..8 broadeners"); return XC_EINVAL; }
+    if (n_broadeners > 0 && !b) { set_error("NULL broadeners"); return XC_EINVAL; }
+    if (mem != XC_MEM_HOST && mem != XC_MEM_DEVICE) { set_error("bad mem flag"); return XC_EINVAL; }
+    // host tables: per broadener its rows sorted by key (a0: J'', a1: J'' * 65536 + J')
+    const int nb = n_broadeners;
+    std::vector<int> type(nb), row0(nb + 1, 0);
+    std::vector<double> frac(nb), gdef(nb), ndef(nb);
+    std::vector<int64_t> keys;
+    std::vector<double> g0, nl;
+    bool need_jup = false;
+    for (int i = 0; i < nb; ++i) {
+        const xc_broadener &x = b[i];
+        if (x.type != XC_BROAD_CONSTANT && x.type != XC_BROAD_A0 && x.type != XC_BROAD_A1) {
+            set_error("broadener %d: unknown type %d", i, x.type);
+            return XC_EINVAL;
+        }
+        if (!(x.fraction >= 0.0) || !isfinite(x.fraction) || !(x.gamma0 >= 0.0) || !isfinite(x.gamma0) ||
+            !isfinite(x.n)) {
+            set_error("broadener %d: fraction and gamma0 must be finite and >= 0, n finite", i);
+            return XC_EINVAL;
+        }
+        type[i] = x.type;
+        frac[i] = x.fraction;
+        gdef[i] = x.gamma0;
+        ndef[i] = x.n;
+        std::vector<std::pair<int64_t, int64_t>> rows;   // (key, row)
+        if (x.type != XC_BROAD_CONSTANT) {
+            if (x.n_entries < 0 || x.n_entries > (1 << 20)) { set_error("broadener %d: 0..2^20 rows", i); return XC_EINVAL; }
+            if (x.n_entries > 0 && (!x.j_lo || !x.gamma0_j || !x.n_j || (x.type == XC_BROAD_A1 && !x.j_up))) {
+                set_error("broadener %d: NULL table array", i);
+                return XC_EINVAL;
+            }
+            for (int64_t r = 0; r < x.n_entries; ++r) {
+                if (!(x.gamma0_j[r] >= 0.0) || !isfinite(x.gamma0_j[r]) || !isfinite(x.n_j[r]) ||
+                    x.j_lo[r] < 0 || x.j_lo[r] > 32767 || (x.type == XC_BROAD_A1 && (x.j_up[r] < 0 || x.j_up[r] > 32767))) {
+                    set_error("broadener %d row %lld: bad values", i, (long long)r);
+                    return XC_EINVAL;
+                }
+                const int64_t key = x.type == XC_BROAD_A1 ? (int64_t)x.j_lo[r] * 65536 + x.j_up[r] : (int64_t)x.j_lo[r];
+                rows.emplace_back(key, r);
+            }
+            std::sort(rows.begin(), rows.end());
+            for (size_t r = 1; r < rows.size(); ++r)
+                if (rows[r].first == rows[r - 1].first) { set_error("broadener %d: duplicate key", i); return XC_EINVAL; }
+            need_jup |= x.type == XC_BROAD_A1 && x.n_entries > 0;
+        }
+        for (auto &kr : rows) {
+            keys.push_back(kr.first);
+            g0.push_back(x.gamma0_j[kr.second]);
+            nl.push_back(x.n_j[kr.second]);
+        }
+        row0[i + 1] = (int)keys.size();
+    }
+    if (need_jup && !j_up && h->n_lines) { set_error("an a1 broadener needs j_up"); return XC_EINVAL; }
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    h->n_broad = 0;
+    const size_t n = h->n_lines;
+    if (nb == 0 || n == 0) return XC_OK;
+    // device layout: bgam [nb][n], bn [nb][n], J' sorted [n], then the tables
+    const size_t nr = keys.size();
+    // bn follows bgam with no gap (lines_of finds it there)
+    const size_t o_bg = 0, o_bn = (size_t)nb * n * 8;
+    size_t off = 2 * (size_t)nb * n * 8;
+    auto carve = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        size_t o = off;
+        off += bytes;
+        return o;
+    };
+    const size_t o_ju = carve(n * 2),
+                 o_jin = carve(n * 2), o_type = carve(nb * 4), o_row0 = carve((nb + 1) * 4), o_frac = carve(nb * 8),
+                 o_gdef = carve(nb * 8), o_ndef = carve(nb * 8), o_keys = carve(nr * 8 + 8), o_g0 = carve(nr * 8 + 8),
+                 o_nl = carve(nr * 8 + 8);
+    XC_TRY_MEM(h->broad.ensure(off));
+    char *d = h->broad.as<char>();
+    int16_t *jus = nullptr;
+    if (j_up) {
+        const int16_t *jin = j_up;
+        if (mem == XC_MEM_HOST) {
+            XC_TRY(cudaMemcpyAsync(d + o_jin, j_up, n * 2, cudaMemcpyHostToDevice, s));
+            jin = (const int16_t *)(d + o_jin);
+        }
+        jus = (int16_t *)(d + o_ju);
+        XC_TRY(launch_permute_i16(jin, h->perm, n, jus, s));
+    }
+    XC_TRY(cudaMemcpyAsync(d + o_type, type.data(), nb * 4, cudaMemcpyHostToDevice, s));
+    XC_TRY(cudaMemcpyAsync(d + o_row0, row0.data(), (nb + 1) * 4, cudaMemcpyHostToDevice, s));
+    XC_TRY(cudaMemcpyAsync(d + o_frac, frac.data(), nb * 8, cudaMemcpyHostToDevice, s));
+    XC_TRY(cudaMemcpyAsync(d + o_gdef, gdef.data(), nb * 8, cudaMemcpyHostToDevice, s));
+    XC_TRY(cudaMemcpyAsync(d + o_ndef, ndef.data(), nb * 8, cudaMemcpyHostToDevice, s));
+    if (nr) {
+        XC_TRY(cudaMemcpyAsync(d + o_keys, keys.data(), nr * 8, cudaMemcpyHostToDevice, s));
+        XC_TRY(cudaMemcpyAsync(d + o_g0, g0.data(), nr * 8, cudaMemcpyHostToDevice, s));
+        XC_TRY(cudaMemcpyAsync(d + o_nl, nl.data(), nr * 8, cudaMemcpyHostToDevice, s));
+    }
+    XC_TRY(launch_apply_broadening(h->j_lo, jus, n, nb, (const int *)(d + o_type), (const double *)(d + o_frac),
+                                   (const double *)(d + o_gdef), (const double *)(d + o_ndef),
+                                   (const int *)(d + o_row0), (const int64_t *)(d + o_keys),
+                                   (const double *)(d + o_g0), (const double *)(d + o_nl), (double *)(d + o_bg),
+                                   (double *)(d + o_bn), s));
+    h->launches += j_up ? 2 : 1;
+    XC_TRY(cudaStreamSynchronize(s));   // the host tables above live on this stack frame
+    h->n_broad = nb;
     return XC_OK;
 }
 
@@ -736,6 +858,10 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
     }
     if (opts->quantity != XC_ABSORPTION || opts->threshold != XC_THRESHOLD_NONE) {
         set_error("the adjoint supports absorption without an intensity threshold");
+        return XC_EUNSUPPORTED;
+    }
+    if (h->n_broad > 0) {
+        set_error("the adjoint does not support a broadener mixture (xc_set_broadening)");
         return XC_EUNSUPPORTED;
     }
     if (n_cond && (!grad_sigma || !dT || !dP)) { set_error("NULL grad_sigma / dT / dP"); return XC_EINVAL; }

@@ -163,7 +163,7 @@ __device__ double cond_width_key(const CondDev &d) {
 // Per-condition constants, stored in order of increasing profile width (stable), so that
 // the conditions sharing a tile have similar far-wing radii; row keeps the caller's index.
 __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp, double step,
-                          int quantity) {
+                          int quantity, const unsigned *gmax_bits) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cond) return;
     const CondDev d = conds[c];
@@ -212,7 +212,9 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
         const double lr = log(d.T_ref / d.T);
         const double tf = fmax(exp((ntm + d.n_shift) * lr), exp((-ntm + d.n_shift) * lr));
         const double ah = alpha_coef(d.T, d.mass_da) * num / step;
-        const double gh = fabs(d.gamma_scale * d.P / d.P_ref) * grm * tf / step;
+        // under a broadener mixture the largest width of this condition over all lines
+        const double gh = gmax_bits ? (double)__uint_as_float(gmax_bits[c]) / step
+                                    : fabs(d.gamma_scale * d.P / d.P_ref) * grm * tf / step;
         const double C = ah * ah * (0.5 / 0.6931471805599453) + gh * gh;
         const double t2 = 225.0 * ah * ah / 0.6931471805599453;
         const double uf = fmax(C * (1.0 / 0.012), t2);
@@ -271,8 +273,9 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
         if (width_mult > 0.0 && cond) {
             const CondDev c = *cond;
             double al = alpha_coef(c.T, c.mass_da) * nu;
-            double ga = c.gamma_scale * (double)L.gamma_ref[l] *
-                        exp(((double)L.n_T[l] + c.n_shift) * log(c.T_ref / c.T)) * (c.P / c.P_ref);
+            double ga = L.n_broad > 0 ? mixture_gamma64(L, l, c)
+                                      : c.gamma_scale * (double)L.gamma_ref[l] *
+                                            exp(((double)L.n_T[l] + c.n_shift) * log(c.T_ref / c.T)) * (c.P / c.P_ref);
             cut = fmin(width_mult * fmax(al, ga), cutoff);
         }
         double d = (nu - nu_A) * inv_h;
@@ -433,7 +436,13 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     if (L.keep && !((L.keep[l * (size_t)L.keep_words + (c.row >> 5)] >> (c.row & 31)) & 1u)) I = 0.f;
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ah, gh;                                                              // widths in grid steps
-    line_widths(nu, L.gamma_ref[l], L.n_T[l], c, inv_h, &ah, &gh);
+    if (L.gamma_lc) {
+        // broadener mixture: the width of this (line, condition), computed in FP64
+        ah = __fmul_rn(c.acoef * nu, inv_h);
+        gh = __fmul_rn(L.gamma_lc[l * (size_t)L.gamma_stride + c.row], inv_h);
+    } else {
+        line_widths(nu, L.gamma_ref[l], L.n_T[l], c, inv_h, &ah, &gh);
+    }
     *thr2 = -1.f;
     *S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
     if (PROF == XC_VOIGT_W4) {
@@ -1152,6 +1161,8 @@ struct TcParams {
     const CParam *cp;
     const uint32_t *keep;              // intensity-threshold decisions (see LinesDev::keep), or nullptr
     int keep_words;
+    const float *gamma_lc;             // widths under a broadener mixture (see LinesDev::gamma_lc), or nullptr
+    int gamma_stride;
     const unsigned *blk_lo, *blk_hi;   // per TC_T-point super-block: line range
     int *counter;
     int *status;                       // set to 1 if a wait ran out
@@ -1170,14 +1181,19 @@ __device__ __forceinline__ int tc_b_index(int n, int k) {
 // series coefficients (p0, p1, p2) and far radius D4 of a (line, condition), p3 in *p3;
 // D4 is the same value line_consts gives (same inputs, same rounded operations)
 __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, const CParam &c, float inv_h,
-                                                   float *p3) {
+                                                   float *p3, float ga_lc) {
     const float nu = ph.x, E = ph.y;
     const float z = fmaf(E, c.kT_hi, E * c.kT_lo);
     const float I = c.emis != 0.f
                         ? c.pref * (ph.z * (nu * nu * nu)) * exp2_neg(z) * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo))
                         : c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
     float ah, gh;
-    line_widths(nu, ph.w, nT, c, inv_h, &ah, &gh);
+    if (ga_lc >= 0.f) {   // broadener mixture: this (line, condition)'s width (see line_consts)
+        ah = __fmul_rn(c.acoef * nu, inv_h);
+        gh = __fmul_rn(ga_lc, inv_h);
+    } else {
+        line_widths(nu, ph.w, nT, c, inv_h, &ah, &gh);
+    }
     const W4Zone zn = w4_zone(ah, gh);
     const float b = ah * ah * (float)(0.5 / 0.6931471805599453), g2 = gh * gh;
     const float P = I * kKappa * gh * inv_h;
@@ -1304,8 +1320,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     const float4 g = cGeo[lB];
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
-                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3);
                     const size_t lg = (size_t)lo + (size_t)(l0 + lB);
+                    const float ga_lc = p.gamma_lc ? p.gamma_lc[lg * (size_t)p.gamma_stride + cpr.row] : -1.f;
+                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3, ga_lc);
                     if (p.keep && !((p.keep[lg * (size_t)p.keep_words + (cpr.row >> 5)] >> (cpr.row & 31)) & 1u)) {
                         S.x = S.y = S.z = 0.f;   // left out by the intensity threshold
                         p3 = 0.f;
@@ -1702,6 +1719,8 @@ struct Plan {
     int *tc_counter = nullptr, *tc_status = nullptr;
     float4 *tc_geo = nullptr, *tc_phys = nullptr;
     uint32_t *keep = nullptr;                   // intensity-threshold decisions (with a threshold)
+    float *gamma_lc = nullptr;                  // widths per (line, condition) (broadener mixture)
+    unsigned *gmax = nullptr;                   // their per-condition maxima (float bits)
 };
 
 xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, int n_cond_call, Plan *pl,
@@ -1724,6 +1743,11 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
     size_t o_blo = 0, o_bhi = 0, o_tcc = 0, o_geo = 0, o_phys = 0, o_keep = 0;
     if (a.opts.threshold != XC_THRESHOLD_NONE) o_keep = carve(n * (size_t)((n_cond_call + 31) / 32) * 4);
+    size_t o_glc = 0, o_gmax = 0;
+    if (a.L.n_broad > 0) {
+        o_glc = carve(n * (size_t)n_cond_call * 4);
+        o_gmax = carve((size_t)n_cond_call * 4);
+    }
     if (tc) {
         pl->n_blk = (int)((a.grid.n + TC_T - 1) / TC_T);
         pl->n_tc_tiles = pl->n_blk * ((n_cond_call + TC_N - 1) / TC_N);
@@ -1750,6 +1774,10 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     pl->core_lo = (unsigned *)(b + o_clo);
     pl->core_hi = (unsigned *)(b + o_chi);
     if (a.opts.threshold != XC_THRESHOLD_NONE) pl->keep = (uint32_t *)(b + o_keep);
+    if (a.L.n_broad > 0) {
+        pl->gamma_lc = (float *)(b + o_glc);
+        pl->gmax = (unsigned *)(b + o_gmax);
+    }
     if (tc) {
         pl->blk_lo = (unsigned *)(b + o_blo);
         pl->blk_hi = (unsigned *)(b + o_bhi);
@@ -1776,12 +1804,20 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     unsigned gblocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
     if (gblocks == 0) gblocks = 1;
     BT_TRY(cudaMemsetAsync(pl.gs, 0, sizeof(GeomStats), s));
+    LinesDev L = a.L;   // the lines as the profile kernels see them (threshold decisions, mixture widths)
+    if (pl.gamma_lc) {
+        BT_TRY(cudaMemsetAsync(pl.gmax, 0, (size_t)nc * 4, s));
+        BT_TRY(launch_line_gamma(a.L, n, a.conds_dev + c0, nc, pl.gamma_lc, pl.gmax, s));
+        L.gamma_lc = pl.gamma_lc;
+        L.gamma_stride = nc;
+        *launches += 1;
+    }
     k_line_geom<<<gblocks, 256, 0, s>>>(a.L, n, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
                                         per_cond_cut ? a.opts.width_mult : 0.0,
                                         per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
                                         pl.gs, pl.tc ? pl.tc_geo : nullptr, pl.tc ? pl.tc_phys : nullptr);
-    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step, a.opts.quantity);
-    LinesDev L = a.L;   // the lines as the profile kernels see them: with the threshold decisions
+    k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step, a.opts.quantity,
+                                            pl.gmax);
     if (pl.keep) {
         const int words = (nc + 31) / 32;
         BT_TRY(launch_line_keep(a.L, n, a.conds_dev + c0, nc, strength_sel(a.opts), pl.keep, words, s));
@@ -1842,6 +1878,8 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.cp = pl.cp;
         tp.keep = L.keep;
         tp.keep_words = L.keep_words;
+        tp.gamma_lc = L.gamma_lc;
+        tp.gamma_stride = L.gamma_stride;
         tp.blk_lo = pl.blk_lo;
         tp.blk_hi = pl.blk_hi;
         tp.counter = pl.tc_counter;
@@ -1900,6 +1938,11 @@ std::string shape_key(const BatchedArgs &a, int nc) {
              a.opts.profile, a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff,
              a.opts.width_mult, a.opts.n_gh, a.opts.flags, use_tc(a, nc) ? 1 : 0, a.opts.quantity,
              a.opts.threshold, a.opts.I_cut, a.opts.nu_crit, a.opts.I_crit);
+    if (a.L.n_broad > 0) {
+        char bb[64];
+        snprintf(bb, sizeof(bb), " b%d@%p", a.L.n_broad, (const void *)a.L.bgam);
+        return std::string(buf) + bb;
+    }
     return buf;
 }
 

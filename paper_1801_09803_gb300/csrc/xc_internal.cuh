@@ -59,6 +59,16 @@ struct LinesDev {
     // nullptr: every line is kept
     const uint32_t *keep = nullptr;
     int keep_words = 0;
+    // broadener mixture (xc_set_broadening): per broadener i and line l, rho_i gamma_0,i at
+    // bgam[i * bstride + l] and n_L,i at bn[i * bstride + l]; n_broad = 0: the line's own
+    // gamma_ref and n_T
+    const double *bgam = nullptr, *bn = nullptr;
+    size_t bstride = 0;
+    int n_broad = 0;
+    // FP32 kernels under a mixture: the Lorentz HWHM (cm^-1) of line l for condition row c
+    // at gamma_lc[l * gamma_stride + c], computed in FP64
+    const float *gamma_lc = nullptr;
+    int gamma_stride = 0;
 };
 
 struct CondDev {  // mirrors xc_condition plus resolved Q
@@ -97,6 +107,16 @@ __device__ inline double line_strength64(double nu, double elower, double gA, co
         if (S < thr) return -1.0;
     }
     return S;
+}
+
+// Lorentz HWHM of line l under the broadener mixture (Sec. "Mixtures of broadeners"):
+// gamma_scale P/P_ref sum_i rho_i gamma_0,i (T_ref/T)^(n_i + n_shift), each term Eq. (e:gamma_L)
+__device__ inline double mixture_gamma64(const LinesDev &L, size_t l, const CondDev &c) {
+    const double lnTr = log(c.T_ref / c.T);
+    double g = 0.0;
+    for (int i = 0; i < L.n_broad; ++i)
+        g += L.bgam[(size_t)i * L.bstride + l] * exp((L.bn[(size_t)i * L.bstride + l] + c.n_shift) * lnTr);
+    return c.gamma_scale * g * (c.P / c.P_ref);
 }
 
 // grid point nu_k = nu_A + k * step, rounded exactly as two separate operations
@@ -280,6 +300,17 @@ cudaError_t launch_sort_lines(const LinesDev &in, size_t n, bool assume_sorted, 
 cudaError_t launch_line_params64(const LinesDev &L, size_t n, const CondDev *cond_dev, int cut_mode,
                                  double cutoff, double width_mult, double *I, double *alpha, double *gamma,
                                  double *cut, cudaStream_t s, const StrengthSel &sel = StrengthSel());
+// per-line mixture parameters from broadener tables (keys sorted on the host): for broadener
+// i, type[i] 0 constant, 1 a0 (key J''), 2 a1 (key J'' * 65536 + J'); rows [row0[i], row0[i+1])
+cudaError_t launch_apply_broadening(const int16_t *j_lo, const int16_t *j_up, size_t n, int nb, const int *type,
+                                    const double *frac, const double *g0_def, const double *n_def,
+                                    const int *row0, const int64_t *keys, const double *g0, const double *nl,
+                                    double *bgam, double *bn, cudaStream_t s);
+// out[i] = in[perm[i]]: a per-line int16 field given in input order -> sorted order
+cudaError_t launch_permute_i16(const int16_t *in, const uint32_t *perm, size_t n, int16_t *out, cudaStream_t s);
+// FP32 kernels under a mixture: gamma_lc[l * nc + c] and the per-condition maximum (float bits)
+cudaError_t launch_line_gamma(const LinesDev &L, size_t n, const CondDev *conds, int nc, float *gamma_lc,
+                              unsigned *gmax_bits, cudaStream_t s);
 // per (line, condition) threshold decisions for the FP32 kernels (see LinesDev::keep)
 cudaError_t launch_line_keep(const LinesDev &L, size_t n, const CondDev *conds, int nc, const StrengthSel &sel,
                              uint32_t *keep, int words, cudaStream_t s);

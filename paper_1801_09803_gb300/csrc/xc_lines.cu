@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(256) k_line_params64(LinesDev L, size_t n, con
         double nu = L.nu[l];
         double Il = line_strength64(nu, (double)L.elower[l], (double)L.g_up[l] * (double)L.A[l], c, sel);
         double al = acoef * nu;
-        double ga = pscale * (double)L.gamma_ref[l] * exp(((double)L.n_T[l] + c.n_shift) * lnTr);
+        double ga = L.n_broad > 0 ? mixture_gamma64(L, l, c)
+                                  : pscale * (double)L.gamma_ref[l] * exp(((double)L.n_T[l] + c.n_shift) * lnTr);
         double cl = line_cut(cut_mode, cutoff, width_mult, al, ga);
         if (Il < 0.0) {   // left out by the intensity threshold: no grid point is within a negative cut
             Il = 0.0;
@@ -100,6 +101,84 @@ __global__ void __launch_bounds__(256) k_line_keep(LinesDev L, size_t n, const C
             keep[l * (size_t)words + w] = bits;
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_apply_broadening(const int16_t *j_lo, const int16_t *j_up, size_t n, int nb,
+                                                          const int *type, const double *frac, const double *g0_def,
+                                                          const double *n_def, const int *row0, const int64_t *keys,
+                                                          const double *g0, const double *nl, double *bgam,
+                                                          double *bn) {
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+        const int jl = j_lo ? j_lo[l] : 0, ju = j_up ? j_up[l] : 0;
+        for (int i = 0; i < nb; ++i) {
+            double g = g0_def[i], m = n_def[i];
+            if (type[i] != XC_BROAD_CONSTANT && row0[i + 1] > row0[i]) {
+                const int64_t key = type[i] == XC_BROAD_A1 ? (int64_t)jl * 65536 + ju : (int64_t)jl;
+                int lo = row0[i], hi = row0[i + 1];
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (keys[mid] < key) lo = mid + 1; else hi = mid;
+                }
+                if (lo < row0[i + 1] && keys[lo] == key) {
+                    g = g0[lo];
+                    m = nl[lo];
+                }
+            }
+            bgam[(size_t)i * n + l] = frac[i] * g;
+            bn[(size_t)i * n + l] = m;
+        }
+    }
+}
+
+cudaError_t launch_apply_broadening(const int16_t *j_lo, const int16_t *j_up, size_t n, int nb, const int *type,
+                                    const double *frac, const double *g0_def, const double *n_def,
+                                    const int *row0, const int64_t *keys, const double *g0, const double *nl,
+                                    double *bgam, double *bn, cudaStream_t s) {
+    if (n == 0 || nb == 0) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_apply_broadening<<<(unsigned)blocks, 256, 0, s>>>(j_lo, j_up, n, nb, type, frac, g0_def, n_def, row0, keys, g0,
+                                                        nl, bgam, bn);
+    return cudaGetLastError();
+}
+
+__global__ void k_permute_i16(const int16_t *__restrict__ in, const uint32_t *__restrict__ perm, size_t n,
+                              int16_t *__restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+cudaError_t launch_permute_i16(const int16_t *in, const uint32_t *perm, size_t n, int16_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_permute_i16<<<(unsigned)blocks, 256, 0, s>>>(in, perm, n, out);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_line_gamma(LinesDev L, size_t n, const CondDev *__restrict__ conds, int nc,
+                                                    float *gamma_lc, unsigned *gmax_bits) {
+    for (int c = 0; c < nc; ++c) {
+        const CondDev cd = conds[c];
+        float m = 0.f;
+        for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
+            const float g = (float)mixture_gamma64(L, l, cd);
+            gamma_lc[l * (size_t)nc + c] = g;
+            m = fmaxf(m, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // non-negative floats order as their bit patterns; rounded up so that the bound holds
+        if ((threadIdx.x & 31) == 0) atomicMax(&gmax_bits[c], __float_as_uint(m) + 1u);
+    }
+}
+
+cudaError_t launch_line_gamma(const LinesDev &L, size_t n, const CondDev *conds, int nc, float *gamma_lc,
+                              unsigned *gmax_bits, cudaStream_t s) {
+    if (n == 0 || nc == 0) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_line_gamma<<<(unsigned)blocks, 256, 0, s>>>(L, n, conds, nc, gamma_lc, gmax_bits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_keep(const LinesDev &L, size_t n, const CondDev *conds, int nc, const StrengthSel &sel,
@@ -182,8 +261,10 @@ __global__ void __launch_bounds__(256) k_count_evals(LinesDev L, size_t n, const
             if (width_mult > 0.0) {
                 const CondDev &cd = conds[c];
                 double al = alpha_coef(cd.T, cd.mass_da) * nu;
-                double ga = cd.gamma_scale * (double)L.gamma_ref[l] *
-                            exp(((double)L.n_T[l] + cd.n_shift) * log(cd.T_ref / cd.T)) * (cd.P / cd.P_ref);
+                double ga = L.n_broad > 0 ? mixture_gamma64(L, l, cd)
+                                          : cd.gamma_scale * (double)L.gamma_ref[l] *
+                                                exp(((double)L.n_T[l] + cd.n_shift) * log(cd.T_ref / cd.T)) *
+                                                (cd.P / cd.P_ref);
                 cut = fmin(width_mult * fmax(al, ga), cutoff);
             }
             int64_t ka, kb;

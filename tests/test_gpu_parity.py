@@ -448,6 +448,65 @@ def test_emission_and_intensity_thresholds(eng, xc, oracle_lib, quantity):
         assert worst[0] < TOL32 and worst[1] < TOL32_BAND, (thr, worst)
 
 
+def test_broadener_mixture(eng, xc, oracle_lib):
+    """.broad a0 and a1 broadeners mixed 0.6 / 0.4 (Secs. "Broadening parameters", "Mixtures of
+    broadeners"): FP64 and the FP32 batched sweep (18 conditions, far wings on the tensor
+    cores), a width-limited cut, and the way back to the lines' own widths."""
+    L = xs.gen_lines(112, 0, 3000, 1000.0, 1040.0)
+    E, g = xs.gen_states(112, 1000)
+    j_up = (L["g_up"].astype(np.int32) - 1) // 2
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    a0 = {j: (0.09 - 0.0011 * j, 0.75 - 0.004 * j) for j in range(0, 60, 2)}
+    a1 = {(j, j + 1): (0.05 + 0.0007 * j, 0.6) for j in range(0, 60, 3)}
+    a1.update({(j, j - 1): (0.04, 0.45 + 0.002 * j) for j in range(1, 60, 4)})
+    ob = [oracle_lib.make_broadener("a0", 0.6, 0.07, 0.5, a0), oracle_lib.make_broadener("a1", 0.4, 0.03, 0.7, a1)]
+    eng.set_broadening([xc.make_broadener("a0", 0.6, 0.07, 0.5, a0), xc.make_broadener("a1", 0.4, 0.03, 0.7, a1)],
+                       j_up=j_up)
+    nu_A, step, n, cut = 995.0, 0.01, 5001, 5.0
+    TP = [(300.0 * 1.15 ** i, 0.02 * 1.5 ** i) for i in range(18)]
+    grid = xc.make_grid(nu_A, step, n)
+
+    def ref(j, o):
+        Q, dQ = oracle_lib.partition_function(E, g, TP[j][0])
+        c = oracle_lib.make_condition(TP[j][0], TP[j][1], Q, dQ)
+        return oracle_lib.cross_section_broad(L, j_up, ob, c, nu_A, step, n, o, nthreads=NTHREADS)
+
+    sel = [0, 9, 17]
+    refs = {j: ref(j, oracle_lib.make_opts("voigt_w4", cut)) for j in sel}
+    for j in sel[:2]:
+        got = eng.cross_section(xc.make_condition(*TP[j]), grid, xc.make_opts("voigt_w4", "fp64", cut))
+        m64, b64 = metrics(got, refs[j])
+        assert m64 < TOL64 and b64 < TOL64, (j, m64, b64)
+    conds = [xc.make_condition(T, P) for T, P in TP]
+    eng.set_timing(True)
+    try:
+        got = eng.cross_section_batched(conds, grid, xc.make_opts("voigt_w4", "fp32", cut))
+        assert eng.sweep_kernels()[3] > 0
+    finally:
+        eng.set_timing(False)
+    cu = eng.cross_section_batched(conds, grid, xc.make_opts("voigt_w4", "fp32", cut, tensor_cores=False))
+    worst = (0.0, 0.0)
+    for j in sel:
+        mr, band = metrics(got[j], refs[j])
+        worst = (max(worst[0], mr), max(worst[1], band))
+        assert metrics(got[j], cu[j])[0] < 2e-5
+    print(f"broadener mixture fp32 batched: worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
+    assert worst[0] < TOL32 and worst[1] < TOL32_BAND
+    # width-limited cut uses the mixture widths too
+    r = ref(5, oracle_lib.make_opts("voigt_w4", 25.0, 200.0))
+    for prec, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        got = eng.cross_section(conds[5], grid, xc.make_opts("voigt_w4", prec, 25.0, 200.0))
+        assert metrics(got, r)[0] < tol, prec
+    # the adjoint refuses a mixture; an empty mixture returns to the lines' own widths
+    with pytest.raises(xc.XcError):
+        eng.cross_section_vjp(conds[:1], grid, xc.make_opts("voigt_w4", "fp64", cut), np.ones((1, n)))
+    eng.set_broadening([])
+    plain = eng.cross_section(conds[0], grid, xc.make_opts("voigt_w4", "fp64", cut))
+    r0 = oracle_sigma(oracle_lib, L, E, g, TP[0][0], TP[0][1], nu_A, step, n, "voigt_w4", cut)
+    assert metrics(plain, r0)[0] < TOL64
+
+
 def test_c1_full_size(eng, xc, oracle_lib):
     """The single-condition FP64 workload at full size: 1e5 lines, 200001 points."""
     W = xs.WORKLOADS["C1"]
