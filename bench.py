@@ -260,7 +260,7 @@ def secondary_measurements(xc, torch, dev):
     C1 (1e5 lines, FP64 plain and FP32), C2 (1e7 lines, width-limited cut, Voigt w4
     FP64 plain and FP32; GH binned, binned Gaussian and binned Lorentzian FP32; Voigt w4 FP32
     emission and with the HITRAN threshold, whose eval count still includes the lines it
-    leaves out), C4 (1e7 lines, 2x2 conditions: FP32
+    leaves out, and with a two-broadener mixture), C4 (1e7 lines, 2x2 conditions: FP32
     forward and FP32 adjoint).  Values are evals/s over the exact eval count."""
     out = {}
     for name in ("C1", "C2", "C4"):
@@ -285,6 +285,16 @@ def secondary_measurements(xc, torch, dev):
             ms = _timed(torch, lambda: eng.cross_section_batched(conds, grid, o, sig))
             tag = "_emission" if kw.get("quantity") == "emission" else ("_hitran_threshold" if "threshold" in kw else "")
             res[f"{prof}_{prec}{tag}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+        if name == "C2":
+            # Lorentz widths from a two-broadener mixture (an a0 table by J'' and a constant)
+            a0 = {j: (0.09 - 0.001 * j, 0.75 - 0.004 * j) for j in range(0, 80)}
+            eng.set_broadening([xc.make_broadener("a0", 0.8, 0.07, 0.5, a0),
+                                xc.make_broadener("constant", 0.2, 0.03, 0.7)])
+            o = xc.make_opts("voigt_w4", "fp32", W.cutoff, W.cutoff_width_mult, W.n_gh)
+            ev = eng.count_evals(conds, grid, o)
+            ms = _timed(torch, lambda: eng.cross_section_batched(conds, grid, o, sig))
+            res["voigt_w4_fp32_broadener_mixture"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+            eng.set_broadening([])
         if name == "C4":
             o = xc.make_opts("voigt_w4", "fp32", W.cutoff)
             gs = torch.ones((len(conds), W.n_points), dtype=torch.float64, device=dev)
