@@ -30,7 +30,7 @@ _lock = threading.Lock()
 _lib = None
 
 PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4,
-            "doppler_binned": 5, "lorentz_binned": 6}
+            "doppler_binned": 5, "lorentz_binned": 6, "voigt_vv": 7}
 
 
 class Condition(C.Structure):
@@ -42,7 +42,8 @@ class Condition(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("profile", C.c_int), ("cutoff", C.c_double), ("width_mult", C.c_double),
                 ("n_gh", C.c_int), ("quantity", C.c_int), ("thr_mode", C.c_int), ("I_cut", C.c_double),
-                ("nu_crit", C.c_double), ("I_crit", C.c_double)]
+                ("nu_crit", C.c_double), ("I_crit", C.c_double), ("vv_split", C.c_double), ("vv_beta", C.c_int),
+                ("vv_norm", C.c_int)]
 
 
 QUANTITIES = {"absorption": 0, "emission": 1}
@@ -103,6 +104,8 @@ def lib():
         L.xo_emissivity.restype = d
         L.xo_threshold.argtypes = [d, d, C.POINTER(Opts)]
         L.xo_threshold.restype = d
+        L.xo_voigt_vv.argtypes = [d, d, d, d, d, i]
+        L.xo_voigt_vv.restype = d
         L.xo_gamma_mixture.argtypes = [i, i, vp, i, C.POINTER(Condition)]
         L.xo_gamma_mixture.restype = d
         L.xo_cross_section_broad.argtypes = [vp] * 6 + [C.c_size_t, vp, i, C.POINTER(Condition), d, d,
@@ -172,8 +175,10 @@ def make_condition(T: float, P: float, Q: float, dQdT: float = 0.0, mass_da: flo
 
 
 def make_opts(profile: str = "voigt_w4", cutoff: float = 25.0, width_mult: float = 0.0,
-              n_gh: int = 20, quantity: str = "absorption", threshold=None) -> Opts:
-    """threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit)."""
+              n_gh: int = 20, quantity: str = "absorption", threshold=None, vv_split: float = 4.0,
+              vv_beta: bool = False, vv_norm: bool = False) -> Opts:
+    """threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit).  vv_*: the
+    Vectorized Voigt ("voigt_vv"): exact zone, continuity factor beta, VVN normalisation."""
     mode, I_cut, nu_crit, I_crit = 0, 0.0, 0.0, 0.0
     if threshold is not None:
         if threshold[0] == "constant":
@@ -182,7 +187,8 @@ def make_opts(profile: str = "voigt_w4", cutoff: float = 25.0, width_mult: float
             mode, nu_crit, I_crit = 2, float(threshold[1]), float(threshold[2])
         else:
             raise ValueError(f"unknown threshold {threshold[0]!r}")
-    return Opts(PROFILES[profile], cutoff, width_mult, n_gh, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit)
+    return Opts(PROFILES[profile], cutoff, width_mult, n_gh, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit,
+                float(vv_split), int(bool(vv_beta)), int(bool(vv_norm)))
 
 
 def intensity(nu, elower, A, g_up, cond: Condition) -> float:
@@ -192,6 +198,11 @@ def intensity(nu, elower, A, g_up, cond: Condition) -> float:
 def emissivity(nu, elower, A, g_up, cond: Condition) -> float:
     """Eq. (e:emiss) times the photon energy h c nu: erg/s/sr per molecule."""
     return lib().xo_emissivity(float(nu), float(elower), float(A), float(g_up), C.byref(cond))
+
+
+def voigt_vv(D, alpha, gamma, nu_l, split=4.0, beta=False):
+    """Eq. (e:fast-v): Vectorized Voigt of a line at nu_l."""
+    return lib().xo_voigt_vv(float(D), float(alpha), float(gamma), float(nu_l), float(split), int(bool(beta)))
 
 
 def gamma_mixture(j_lo, j_up, broadeners, cond: Condition) -> float:

@@ -14,6 +14,13 @@
  *   eps_fi        Eq. (e:emiss) LTE emissivity from the upper state (E' = E'' + nu),
  *                 with the photon energy h c nu so that it comes out in the unit the
  *                 text gives (erg/s/sr per molecule; the printed formula omits h c)
+ *   VV / VVN      Sec. "Vectorized Voigt approximation", Eq. (e:fast-v), (e:beta): the w4
+ *                 Voigt within `split` (4 cm^-1) of the centre, beyond it the reference
+ *                 profile -- the Voigt of a line at 1 cm^-1 (alpha_ref = alpha / nu), same
+ *                 gamma -- times beta (1, or the ratio that makes it continuous at split),
+ *                 at the line's own offsets; VVN (Sec. "Binned Vectorized Voigt") divides
+ *                 I by Sigma = h sum_k f(nu_k - nu), the sum over the line's cut window on
+ *                 the grid's lattice (also past the grid ends), so that each line's area is I
  *   broadening    Sec. "Broadening parameters" (.broad): per broadener a constant
  *                 (gamma_0, n_L), or a table by J'' (a0) or by (J'', J') (a1), with the
  *                 broadener's defaults for a line whose quantum numbers it does not
@@ -71,7 +78,7 @@ static const double XO_LN2 = 0.69314718055994530942;
 double xo_c2(void) { return XO_H * (XO_C_SI * 100.0) / XO_KB; } /* cm K */
 
 enum { XO_DOPPLER = 0, XO_LORENTZ = 1, XO_VOIGT_W4 = 2, XO_GH_BINNED = 3, XO_GH_SAMPLED = 4,
-       XO_DOPPLER_BINNED = 5, XO_LORENTZ_BINNED = 6 };
+       XO_DOPPLER_BINNED = 5, XO_LORENTZ_BINNED = 6, XO_VOIGT_VV = 7 };
 
 /* ---------------------------------------------------------------------- */
 /* Partition function, Eq. (e:pf), and its temperature derivative          */
@@ -108,6 +115,9 @@ typedef struct {
     int quantity;                /* 0: absorption, Eq. (e:int); 1: emission, Eq. (e:emiss) */
     int thr_mode;                /* 0: none; 1: constant I_cut; 2: HITRAN dynamic (nu_crit, I_crit) */
     double I_cut, nu_crit, I_crit;
+    double vv_split;             /* XO_VOIGT_VV: the exact-Voigt zone |nu - nu_fi| <= vv_split */
+    int vv_beta;                 /* 1: beta of Eq. (e:beta), 0: beta = 1 */
+    int vv_norm;                 /* 1: VVN, the line area renormalised to I */
 } xo_opts;
 
 /* Eq. (e:int): I = g' A / (8 pi c nu^2) * exp(-c2 E''/T) * (1 - exp(-c2 nu/T)) / Q(T) */
@@ -535,6 +545,37 @@ static int cross_section_impl(const double *nu, const float *elower, const float
                               const int16_t *g_up, size_t n_lines, const xo_condition *cond, double nu_A,
                               double h, long long n_pts, const xo_opts *o, double *sigma, int nthreads);
 
+/* Eq. (e:fast-v): the Vectorized Voigt of a line at nu_l, offset D */
+double xo_voigt_vv(double D, double alpha, double gamma, double nu_l, double split, int beta_mode)
+{
+    if (fabs(D) <= split) return xo_voigt_w4(D, alpha, gamma);
+    double a_ref = alpha / nu_l;   /* alpha_D is proportional to nu: its value at 1 cm^-1 */
+    double beta = beta_mode ? xo_voigt_w4(split, alpha, gamma) / xo_voigt_w4(split, a_ref, gamma) : 1.0;
+    return beta * xo_voigt_w4(D, a_ref, gamma);
+}
+
+/* the profile value of a line (every profile; VV needs the line position) */
+static double line_value(const xo_opts *o, double D, double h, double al, double ga, double nul, int ngh,
+                         const double *xg, const double *wg)
+{
+    if (o->profile == XO_VOIGT_VV) return xo_voigt_vv(D, al, ga, nul, o->vv_split, o->vv_beta);
+    return profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, NULL, NULL);
+}
+
+/* VVN: Sigma = h sum_k f(nu_k - nu) over the lattice points nu_A + k h within the cut */
+static double vv_norm(const xo_opts *o, double nul, double al, double ga, double cut, double nu_A, double h)
+{
+    long long k0 = (long long)floor((nul - cut - nu_A) / h) - 1;
+    long long k1 = (long long)floor((nul + cut - nu_A) / h) + 1;
+    double s = 0.0, c = 0.0;
+    for (long long k = k0; k <= k1; ++k) {
+        double D = (nu_A + (double)k * h) - nul;
+        if (fabs(D) > cut) continue;
+        neumaier_add(&s, &c, xo_voigt_vv(D, al, ga, nul, o->vv_split, o->vv_beta));
+    }
+    return (s + c) * h;
+}
+
 int xo_cross_section(const double *nu, const float *elower, const float *A, const float *gamma_ref,
                      const float *n_T, const int16_t *g_up, size_t n_lines,
                      const xo_condition *cond, double nu_A, double h, long long n_pts,
@@ -583,6 +624,10 @@ static int cross_section_impl(const double *nu, const float *elower, const float
             double al = xo_alpha_doppler(nul, cond);
             double ga = line_gamma(gsrc, l, cond);
             double cut = line_cut(o, al, ga);
+            if (o->profile == XO_VOIGT_VV && o->vv_norm) {
+                double sn = vv_norm(o, nul, al, ga, cut, nu_A, h);
+                Ifi = sn > 0.0 ? Ifi / sn : 0.0;
+            }
             long long k0 = grid_floor_index(nul - cut, nu_A, h) - 1;
             long long k1 = grid_floor_index(nul + cut, nu_A, h) + 1;
             if (k0 < 0) k0 = 0;
@@ -591,7 +636,7 @@ static int cross_section_impl(const double *nu, const float *elower, const float
                 double xk = nu_A + (double)k * h;
                 double D = xk - nul;
                 if (fabs(D) > cut) continue;
-                double v = profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, NULL, NULL);
+                double v = line_value(o, D, h, al, ga, nul, ngh, xg, wg);
                 neumaier_add(&s[k], &c[k], Ifi * v);
             }
         }
@@ -650,7 +695,11 @@ int xo_cross_section_points(const double *nu, const float *elower, const float *
             if (fabs(D) > cut) continue;
             double Ifi = line_strength(o, nu[l], elower[l], A[l], g_up[l], cond);
             if (Ifi < 0.0) continue;   /* below the intensity threshold */
-            neumaier_add(&s, &c, Ifi * profile_eval(o->profile, D, h, al, ga, ngh, xg, wg, NULL, NULL));
+            if (o->profile == XO_VOIGT_VV && o->vv_norm) {
+                double sn = vv_norm(o, nu[l], al, ga, cut, nu_A, h);
+                Ifi = sn > 0.0 ? Ifi / sn : 0.0;
+            }
+            neumaier_add(&s, &c, Ifi * line_value(o, D, h, al, ga, nu[l], ngh, xg, wg));
         }
         out[i] = s + c;
     }
@@ -697,7 +746,7 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
     const double c2 = xo_c2();
     double xg[200], wg[200];
     int ngh = 0;
-    if (o->quantity != 0 || o->thr_mode != 0) return -4;   /* absorption, no threshold */
+    if (o->quantity != 0 || o->thr_mode != 0 || o->profile == XO_VOIGT_VV) return -4;   /* absorption, no threshold */
     if (o->profile == XO_GH_BINNED || o->profile == XO_GH_SAMPLED) {
         ngh = o->n_gh;
         if (xo_gauss_hermite(ngh, xg, wg) != 0) return -1;

@@ -161,6 +161,73 @@ def test_threshold_leaves_out_exactly_the_weak_lines(oracle_lib, quantity):
                                                                     L["g_up"][0], cond), rtol=1e-13)
 
 
+# --------------------------------------------- Vectorized Voigt, Eqs. (e:fast-v), (e:beta)
+def test_vectorized_voigt_zones(oracle_lib):
+    """Within `split` of the centre the Voigt of the line itself; beyond it the Voigt of a line at
+    1 cm^-1 (Doppler HWHM alpha / nu, the same gamma), both against scipy's Voigt to w4's
+    accuracy; with a wide Doppler width the wing visibly differs from the line's own Voigt."""
+    LN2S = math.sqrt(2 * LN2)
+    nu, a, g = 30000.0, 0.2, 0.01
+    for D in (0.0, 0.3, -2.5, 3.99):
+        v = oracle_lib.voigt_vv(D, a, g, nu)
+        assert v == pytest.approx(sp.voigt_profile(D, a / LN2S, g), rel=1.2e-4)
+    for D in (4.01, -6.0, 20.0):
+        v = oracle_lib.voigt_vv(D, a, g, nu)
+        ref = sp.voigt_profile(D, a / nu / LN2S, g)
+        assert v == pytest.approx(ref, rel=1.2e-4)
+        own = sp.voigt_profile(D, a / LN2S, g)
+        if abs(D) < 10:
+            assert abs(own / ref - 1) > 1e-3    # alpha_ref, not alpha, shapes the wing
+    # beta makes the profile continuous at the split point; beta = 1 leaves a jump
+    left = oracle_lib.voigt_vv(4.0, a, g, nu, beta=True)
+    right = oracle_lib.voigt_vv(4.0 * (1 + 1e-13), a, g, nu, beta=True)
+    assert right == pytest.approx(left, rel=1e-9)
+    assert oracle_lib.voigt_vv(4.0 * (1 + 1e-13), a, g, nu) != pytest.approx(left, rel=1e-4)
+    # a custom split moves the switch
+    assert oracle_lib.voigt_vv(3.0, a, g, nu, split=2.0) == pytest.approx(sp.voigt_profile(3.0, a / nu / LN2S, g),
+                                                                           rel=1.2e-4)
+
+
+def test_vvn_conserves_each_line_area(oracle_lib):
+    """VVN: h sum_k sigma_k equals the summed intensities for lines whose cut lies inside the
+    grid, on fine and coarse grids alike; without normalisation the sampled area differs."""
+    L = xs.gen_lines(35, 0, 40, 1000.0, 1010.0)
+    cond = oracle_lib.make_condition(1900.0, 1.0, 500.0)
+    I = sum(oracle_lib.intensity(L["nu"][l], L["elower"][l], L["A"][l], L["g_up"][l], cond) for l in range(40))
+    for h in (0.01, 0.3, 1.0):
+        N = int(round(30.0 / h)) + 1
+        on = oracle_lib.cross_section(L, cond, 990.0, h, N, oracle_lib.make_opts("voigt_vv", 8.0, vv_norm=True),
+                                      nthreads=2)
+        assert on.sum() * h == pytest.approx(I, rel=1e-12)
+        if h == 1.0:
+            off = oracle_lib.cross_section(L, cond, 990.0, h, N, oracle_lib.make_opts("voigt_vv", 8.0), nthreads=2)
+            assert abs(off.sum() * h / I - 1) > 1e-3
+
+
+def test_cross_section_bruteforce_vectorized_voigt(oracle_lib):
+    L = _tiny_lines(6, seed=5, lo=3000.0, hi=3001.0)
+    T, P, Q = 2500.0, 0.3, 900.0
+    cond = oracle_lib.make_condition(T, P, Q)
+    nu_A, h, N, cut = 2993.5, 0.05, 281, 6.0
+    sig = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("voigt_vv", cut, vv_split=1.5))
+    c2, c_cm = 1.438776877503933802, 2.99792458e10
+    out = np.zeros(N)
+    for k in range(N):
+        xk = nu_A + k * h
+        for l in range(6):
+            nu = float(L["nu"][l]); D = xk - nu
+            if abs(D) > cut:
+                continue
+            I = (float(L["g_up"][l]) * float(L["A"][l]) / (8 * math.pi * c_cm * nu * nu)
+                 * math.exp(-c2 * float(L["elower"][l]) / T) * (1 - math.exp(-c2 * nu / T)) / Q)
+            al = nu / 2.99792458e8 * math.sqrt(2 * 1.380649e-23 * T * LN2 / (18 * 1.66053906660e-27))
+            ga = float(L["gamma_ref"][l]) * (296.0 / T) ** float(L["n_T"][l]) * P
+            a_use = al if abs(D) <= 1.5 else al / nu
+            out[k] += I * sp.voigt_profile(D, a_use / math.sqrt(2 * LN2), ga)
+    m = out > 1e-6 * out.max()
+    assert np.max(np.abs(sig[m] - out[m]) / out[m]) < 1.2e-4
+
+
 # --------------------------------------------- .broad broadening and mixtures
 def _read_broad(path):
     rows = {}
