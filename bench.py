@@ -260,7 +260,7 @@ def secondary_measurements(xc, torch, dev):
     C1 (1e5 lines, FP64 plain and FP32), C2 (1e7 lines, width-limited cut, Voigt w4
     FP64 plain and FP32; GH binned, binned Gaussian and binned Lorentzian FP32; Voigt w4 FP32
     emission and with the HITRAN threshold, whose eval count still includes the lines it
-    leaves out, and with a two-broadener mixture), C4 (1e7 lines, 2x2 conditions: FP32
+    leaves out, and with a two-broadener mixture; the Vectorized Voigt with beta), C4 (1e7 lines, 2x2 conditions: FP32
     forward and FP32 adjoint).  Values are evals/s over the exact eval count."""
     out = {}
     for name in ("C1", "C2", "C4"):
@@ -278,12 +278,14 @@ def secondary_measurements(xc, torch, dev):
         if name == "C2":
             cases += [("voigt_gh_binned", "fp32", {}), ("doppler_binned", "fp32", {}), ("lorentz_binned", "fp32", {}),
                       ("voigt_w4", "fp32", {"quantity": "emission"}),
-                      ("voigt_w4", "fp32", {"threshold": ("hitran", 2000.0, 1e-29)})]
+                      ("voigt_w4", "fp32", {"threshold": ("hitran", 2000.0, 1e-29)}),
+                      ("voigt_vv", "fp32", {"vv_beta": True})]
         for prof, prec, kw in cases:
             o = xc.make_opts(prof, prec, W.cutoff, W.cutoff_width_mult, W.n_gh, **kw)
             ev = eng.count_evals(conds, grid, o)
             ms = _timed(torch, lambda: eng.cross_section_batched(conds, grid, o, sig))
-            tag = "_emission" if kw.get("quantity") == "emission" else ("_hitran_threshold" if "threshold" in kw else "")
+            tag = "_emission" if kw.get("quantity") == "emission" else ("_hitran_threshold" if "threshold" in kw else
+                                                                         ("_beta" if kw.get("vv_beta") else ""))
             res[f"{prof}_{prec}{tag}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
         if name == "C2":
             # Lorentz widths from a two-broadener mixture (an a0 table by J'' and a constant)

@@ -52,7 +52,18 @@ enum {
     XC_VOIGT_GH_BINNED = 3,  /* Eq. (e:sigma:quad): bin-averaged Gauss-Hermite (area-conserving) */
     XC_VOIGT_GH_SAMPLED = 4, /* Eq. (e:V-quad): Gauss-Hermite sum sampled at the grid point */
     XC_DOPPLER_BINNED = 5,   /* Eq. (eqn:sig_ij): Gaussian averaged over each grid bin (erf) */
-    XC_LORENTZ_BINNED = 6    /* Eq. (eqn:sig_lor-2): Lorentzian averaged over each grid bin (arctan) */
+    XC_LORENTZ_BINNED = 6,   /* Eq. (eqn:sig_lor-2): Lorentzian averaged over each grid bin (arctan) */
+    XC_VOIGT_VV = 7          /* Eq. (e:fast-v): Vectorized Voigt -- the w4 Voigt within vv_split of the
+                                centre, beyond it the Voigt of a line at 1 cm^-1 (Doppler HWHM
+                                alpha / nu, the same gamma) times beta, at the line's own offsets */
+};
+
+/* xc_opts.vv_flags (XC_VOIGT_VV) */
+enum {
+    XC_VV_BETA = 1,      /* beta of Eq. (e:beta): the wing scaled to be continuous at vv_split (else 1) */
+    XC_VV_NORMALISE = 2  /* VVN (Sec. "Binned Vectorized Voigt"): each line's intensity divided by
+                            h sum_k f(nu_k - nu), the sum over its cut window on the grid's lattice
+                            (also past the grid ends), so that every line's area is I */
 };
 
 /* arithmetic of the profile evaluation */
@@ -132,7 +143,7 @@ typedef struct {
  * (inclusive), cut_l = cutoff, or min(cutoff, width_mult * max(alpha_l, gamma_l))
  * when width_mult > 0 (Sec. 3.10 "Off-set").  n_gh: Gauss-Hermite nodes (1..64). */
 typedef struct {
-    int profile;        /* XC_DOPPLER .. XC_LORENTZ_BINNED */
+    int profile;        /* XC_DOPPLER .. XC_VOIGT_VV */
     int precision;      /* XC_FP64_PLAIN or XC_FP32 */
     double cutoff;      /* cm^-1, > 0 */
     double width_mult;  /* 0 = fixed cut */
@@ -143,6 +154,8 @@ typedef struct {
     double I_cut;       /* constant threshold, >= 0, in the unit of the quantity */
     double nu_crit;     /* HITRAN threshold: > 0, cm^-1 (the paper's default 2000) */
     double I_crit;      /* HITRAN threshold: >= 0, in the unit of the quantity (default 1e-29) */
+    double vv_split;    /* XC_VOIGT_VV: half-width of the exact zone, cm^-1 (0: the paper's 4) */
+    int vv_flags;       /* XC_VV_* bits */
 } xc_opts;
 
 /* Library version string (static storage). */

@@ -24,7 +24,7 @@ __all__ = [
 LIB_PATH = _build.LIB
 XC_MEM_HOST, XC_MEM_DEVICE = 0, 1
 PROFILES = {"doppler": 0, "lorentz": 1, "voigt_w4": 2, "voigt_gh_binned": 3, "voigt_gh_sampled": 4,
-            "doppler_binned": 5, "lorentz_binned": 6}
+            "doppler_binned": 5, "lorentz_binned": 6, "voigt_vv": 7}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "XC_OK", 1: "XC_EINVAL", 2: "XC_ENOMEM", 3: "XC_ECUDA", 4: "XC_ETIMEOUT", 5: "XC_EUNSUPPORTED"}
 EXPORTED_SYMBOLS = [
@@ -61,7 +61,7 @@ class XcOpts(C.Structure):
     _fields_ = [("profile", C.c_int), ("precision", C.c_int), ("cutoff", C.c_double),
                 ("width_mult", C.c_double), ("n_gh", C.c_int), ("flags", C.c_int),
                 ("quantity", C.c_int), ("threshold", C.c_int), ("I_cut", C.c_double),
-                ("nu_crit", C.c_double), ("I_crit", C.c_double)]
+                ("nu_crit", C.c_double), ("I_crit", C.c_double), ("vv_split", C.c_double), ("vv_flags", C.c_int)]
 
 
 QUANTITIES = {"absorption": 0, "emission": 1}
@@ -184,10 +184,13 @@ XC_OPT_NO_TENSOR_CORES = 1
 
 def make_opts(profile: str = "voigt_w4", precision: str = "fp64", cutoff: float = 25.0,
               width_mult: float = 0.0, n_gh: int = 20, tensor_cores: bool = True,
-              quantity: str = "absorption", threshold=None) -> XcOpts:
+              quantity: str = "absorption", threshold=None, vv_split: float = 0.0, vv_beta: bool = False,
+              vv_norm: bool = False) -> XcOpts:
     """tensor_cores=False keeps the FP32 Voigt w4 far wings on the CUDA cores.
     quantity: "absorption" (Eq. e:int) or "emission" (Eq. e:emiss, times h c nu).
-    threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit)."""
+    threshold: None, ("constant", I_cut) or ("hitran", nu_crit, I_crit).
+    vv_*: the Vectorized Voigt ("voigt_vv"): exact-zone half-width (0: 4 cm^-1), continuity
+    factor beta, VVN area normalisation."""
     mode, I_cut, nu_crit, I_crit = 0, 0.0, 0.0, 0.0
     if threshold is not None:
         mode = THRESHOLDS[threshold[0]]
@@ -196,7 +199,8 @@ def make_opts(profile: str = "voigt_w4", precision: str = "fp64", cutoff: float 
         else:
             nu_crit, I_crit = float(threshold[1]), float(threshold[2])
     return XcOpts(PROFILES[profile], PRECISIONS[precision], float(cutoff), float(width_mult), int(n_gh),
-                  0 if tensor_cores else XC_OPT_NO_TENSOR_CORES, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit)
+                  0 if tensor_cores else XC_OPT_NO_TENSOR_CORES, QUANTITIES[quantity], mode, I_cut, nu_crit, I_crit,
+                  float(vv_split), (1 if vv_beta else 0) | (2 if vv_norm else 0))
 
 
 _LINE_FIELDS = [("nu", np.float64), ("elower", np.float32), ("A", np.float32), ("gamma_ref", np.float32),

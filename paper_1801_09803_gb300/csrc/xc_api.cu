@@ -155,7 +155,7 @@ xc_status check_grid(const xc_grid *g) {
 
 xc_status check_opts(const xc_opts *o) {
     if (!o) { set_error("NULL opts"); return XC_EINVAL; }
-    if (o->profile < XC_DOPPLER || o->profile > XC_LORENTZ_BINNED) {
+    if (o->profile < XC_DOPPLER || o->profile > XC_VOIGT_VV) {
         set_error("unknown profile %d", o->profile);
         return XC_EUNSUPPORTED;
     }
@@ -180,6 +180,10 @@ xc_status check_opts(const xc_opts *o) {
     }
     if (o->threshold == XC_THRESHOLD_CONSTANT && !(o->I_cut >= 0.0 && isfinite(o->I_cut))) {
         set_error("I_cut must be finite and >= 0");
+        return XC_EINVAL;
+    }
+    if (!(o->vv_split >= 0.0) || !isfinite(o->vv_split) || (o->vv_flags & ~(XC_VV_BETA | XC_VV_NORMALISE))) {
+        set_error("vv_split must be finite and >= 0, vv_flags XC_VV_* bits");
         return XC_EINVAL;
     }
     if (o->threshold == XC_THRESHOLD_HITRAN &&
@@ -313,9 +317,15 @@ xc_status cross_section_f64(xc_handle *h, const CondDev *dcond, const xc_grid *g
         ghx = h->gh.as<double>();
         ghw = ghx + 64;
     }
+    const double vv_split = o->vv_split > 0.0 ? o->vv_split : 4.0;
+    const int vv_beta = (o->vv_flags & XC_VV_BETA) ? 1 : 0;
+    if (o->profile == XC_VOIGT_VV && (o->vv_flags & XC_VV_NORMALISE)) {
+        XC_TRY(launch_vv_norm64(h->nu, I, al, ga, cut, n, g->nu_A, g->step, vv_split, vv_beta, s));
+        h->launches += 1;
+    }
     stage_begin(h, ST_PROFILE, s);
     XC_TRY(launch_gather_f64(o->profile, h->nu, I, al, ga, cut, lo, hi, n_win, g->nu_A, g->step, g->n, ghx, ghw,
-                             ghx ? o->n_gh : 0, sig, s));
+                             ghx ? o->n_gh : 0, sig, s, vv_split, vv_beta));
     stage_end(h, ST_PROFILE, s);
     h->launches += 3;
     return XC_OK;

@@ -63,6 +63,8 @@ struct CParam {
     int row;            // output row (the caller's condition index)
     float dbound;       // upper bound of the far radius D4 over all lines (grid steps)
     float emis;         // 1: emission (pref = abundance h c / (4 pi Q) * scale), 0: absorption
+    float vv_split;     // Vectorized Voigt: half-width of the exact zone (cm^-1)
+    int vv_beta;        // Vectorized Voigt: 1 = continuity factor beta, 0 = beta 1
 };
 
 struct GeomStats {
@@ -163,7 +165,7 @@ __device__ double cond_width_key(const CondDev &d) {
 // Per-condition constants, stored in order of increasing profile width (stable), so that
 // the conditions sharing a tile have similar far-wing radii; row keeps the caller's index.
 __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs, CParam *cp, double step,
-                          int quantity, const unsigned *gmax_bits) {
+                          int quantity, const unsigned *gmax_bits, float vv_split, int vv_beta) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cond) return;
     const CondDev d = conds[c];
@@ -203,6 +205,8 @@ __global__ void k_cparams(const CondDev *conds, int n_cond, const GeomStats *gs,
     p.nshift = (float)d.n_shift;
     p.row = c;
     p.emis = emis ? 1.f : 0.f;
+    p.vv_split = vv_split;
+    p.vv_beta = vv_beta;
     {
         // D4 <= ceil(sqrt(max(C k4, t2))) + 1 grows with both widths; t2 <= (15 a_h / sqrt ln2)^2.
         // Upper bounds of the widths from the line statistics (|n| <= nT_max), with margin.
@@ -415,6 +419,8 @@ __device__ __forceinline__ W4Zone w4_zone(float ah, float gh) {
 
 // S = (p0, p1, p2, D) of the 3-term far-wing series; D = D4 (the tensor-core kernel's
 // radius) when that kernel takes the far wings (d4), else D3
+__device__ __noinline__ float w4_value_f32(float delta, const float4 &B);
+
 template <int PROF>
 __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
                                             float4 *A, float4 *B, float *thr2, float4 *S, bool d4 = false) {
@@ -434,6 +440,8 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     }
     // left out by the intensity threshold for this condition (decided in FP64)
     if (L.keep && !((L.keep[l * (size_t)L.keep_words + (c.row >> 5)] >> (c.row & 31)) & 1u)) I = 0.f;
+    // VVN: this (line, condition)'s area normalisation (computed in FP64)
+    if (L.vv_scale) I *= L.vv_scale[l * (size_t)L.vv_stride + c.row];
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ah, gh;                                                              // widths in grid steps
     if (L.gamma_lc) {
@@ -467,6 +475,21 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         *A = make_float4(qd, I * kSqrtLn2OverPi * rcp_approx(al), 0.f, 0.f);
     } else if (PROF == XC_VOIGT_GH_SAMPLED) {
         *A = make_float4(ah / kSqrtLn2f, fmaxf(gh * gh, 1e-30f), I * kPiM32 * gh * inv_h, 0.f);
+    } else if (PROF == XC_VOIGT_VV) {
+        // B: the line's own w4 Voigt (a, y, Pv); A: the reference wing -- the Voigt of a line at
+        // 1 cm^-1, Doppler HWHM alpha / nu: a_ref = a nu, y_ref = a_ref g, amplitude Pv nu, times
+        // beta (Eq. e:beta) when asked -- and the exact zone's half-width in grid steps
+        const float a = kSqrtLn2f * rcp_approx(ah), y = a * gh;
+        const float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
+        const float ar = a * nu, yr = ar * gh;
+        const float sp = c.vv_split * inv_h;
+        float Pw = Pv * nu;
+        if (c.vv_beta) {
+            const float rw = w4_value_f32(sp, make_float4(ar, yr, 1.f, 0.f));
+            Pw = rw > 0.f ? w4_value_f32(sp, make_float4(a, y, Pv, 0.f)) / rw : 0.f;
+        }
+        *A = make_float4(ar, yr, Pw, sp);
+        *B = make_float4(a, y, Pv, 0.f);
     } else if (PROF == XC_DOPPLER_BINNED) {
         // Eq. (eqn:sig_ij) in grid steps: x+- = (sqrt(ln2)/ah) (delta +- 1/2), I/(2h)
         *A = make_float4(kSqrtLn2f * rcp_approx(ah), 0.5f * I * inv_h, 0.f, 0.f);
@@ -524,6 +547,9 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
             s = fmaf(s_w[j], rcp_approx(fmaf(e, e, A.y)), s);
         }
         return A.z * s;
+    } else if (PROF == XC_VOIGT_VV) {
+        // Eq. (e:fast-v): the line's own Voigt in the exact zone, the reference wing beyond it
+        return fabsf(delta) <= A.w ? w4_value_f32(delta, B) : w4_value_f32(delta, make_float4(A.x, A.y, A.z, 0.f));
     } else if (PROF == XC_DOPPLER_BINNED) {
         // erf(x+) - erf(x-) on the side |delta| of the (symmetric) profile, as
         // erfc(x-) - erfc(x+): no difference of two numbers near 1 in the wings
@@ -606,7 +632,7 @@ __device__ __forceinline__ float4 load_consts(const unsigned char *base, int idx
 
 template <int PROF, int R, int CG>
 struct SmemLayout {
-    static constexpr bool kHasB = (PROF == XC_VOIGT_W4);
+    static constexpr bool kHasB = (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV);
     static constexpr size_t kA = (size_t)SCH * CG * ConstLayout<PROF>::kBytes;
     static constexpr size_t kB = kHasB ? (size_t)SCH * CG * sizeof(float4) : 0;
     static constexpr size_t kMetaI = (size_t)SCH * sizeof(int4);
@@ -746,7 +772,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                         line_consts<PROF>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
                                           &t2, &S, p.tc_far != 0);
                     } else {  // padding condition: contributes exactly 0
-                        if (PROF == XC_VOIGT_W4) A = make_float4(1.f, 1.f, 0.f, 0.f);
+                        if (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV) A = make_float4(1.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_BINNED) A = make_float4(0.f, 1.f, 1.f, 0.f);
                         else A = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -1672,6 +1698,8 @@ static const Variant kVariants[] = {
     XC_VARIANT(XC_DOPPLER_BINNED, 8, 1),
     XC_VARIANT(XC_LORENTZ_BINNED, 4, 16), XC_VARIANT(XC_LORENTZ_BINNED, 8, 4),
     XC_VARIANT(XC_LORENTZ_BINNED, 8, 1),
+    XC_VARIANT(XC_VOIGT_VV, 4, 16), XC_VARIANT(XC_VOIGT_VV, 8, 4),
+    XC_VARIANT(XC_VOIGT_VV, 8, 1),
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1720,6 +1748,7 @@ struct Plan {
     float4 *tc_geo = nullptr, *tc_phys = nullptr;
     uint32_t *keep = nullptr;                   // intensity-threshold decisions (with a threshold)
     float *gamma_lc = nullptr;                  // widths per (line, condition) (broadener mixture)
+    float *vv_scale = nullptr;                  // VVN factors per (line, condition)
     unsigned *gmax = nullptr;                   // their per-condition maxima (float bits)
 };
 
@@ -1743,7 +1772,9 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     size_t o_clo = carve((size_t)pl->n_win_core * 4), o_chi = carve((size_t)pl->n_win_core * 4);
     size_t o_blo = 0, o_bhi = 0, o_tcc = 0, o_geo = 0, o_phys = 0, o_keep = 0;
     if (a.opts.threshold != XC_THRESHOLD_NONE) o_keep = carve(n * (size_t)((n_cond_call + 31) / 32) * 4);
-    size_t o_glc = 0, o_gmax = 0;
+    size_t o_glc = 0, o_gmax = 0, o_vvs = 0;
+    const bool vvn = a.opts.profile == XC_VOIGT_VV && (a.opts.vv_flags & XC_VV_NORMALISE);
+    if (vvn) o_vvs = carve(n * (size_t)n_cond_call * 4);
     if (a.L.n_broad > 0) {
         o_glc = carve(n * (size_t)n_cond_call * 4);
         o_gmax = carve((size_t)n_cond_call * 4);
@@ -1774,6 +1805,7 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
     pl->core_lo = (unsigned *)(b + o_clo);
     pl->core_hi = (unsigned *)(b + o_chi);
     if (a.opts.threshold != XC_THRESHOLD_NONE) pl->keep = (uint32_t *)(b + o_keep);
+    if (vvn) pl->vv_scale = (float *)(b + o_vvs);
     if (a.L.n_broad > 0) {
         pl->gamma_lc = (float *)(b + o_glc);
         pl->gmax = (unsigned *)(b + o_gmax);
@@ -1816,8 +1848,17 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
                                         per_cond_cut ? a.opts.width_mult : 0.0,
                                         per_cond_cut ? a.conds_dev + c0 : nullptr, pl.n_abs, pl.f, pl.ka, pl.kb,
                                         pl.gs, pl.tc ? pl.tc_geo : nullptr, pl.tc ? pl.tc_phys : nullptr);
+    const double vv_split = a.opts.vv_split > 0.0 ? a.opts.vv_split : 4.0;
+    const int vv_beta = (a.opts.vv_flags & XC_VV_BETA) ? 1 : 0;
     k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(a.conds_dev + c0, nc, pl.gs, pl.cp, a.grid.step, a.opts.quantity,
-                                            pl.gmax);
+                                            pl.gmax, (float)vv_split, vv_beta);
+    if (pl.vv_scale) {
+        BT_TRY(launch_vv_norm32(L, n, a.conds_dev + c0, nc, a.grid.nu_A, a.grid.step, a.opts.cutoff,
+                                per_cond_cut ? a.opts.width_mult : 0.0, vv_split, vv_beta, pl.vv_scale, s));
+        L.vv_scale = pl.vv_scale;
+        L.vv_stride = nc;
+        *launches += 1;
+    }
     if (pl.keep) {
         const int words = (nc + 31) / 32;
         BT_TRY(launch_line_keep(a.L, n, a.conds_dev + c0, nc, strength_sel(a.opts), pl.keep, words, s));
@@ -1938,6 +1979,16 @@ std::string shape_key(const BatchedArgs &a, int nc) {
              a.opts.profile, a.n_lines, nc, (long long)a.grid.n, a.grid.nu_A, a.grid.step, a.opts.cutoff,
              a.opts.width_mult, a.opts.n_gh, a.opts.flags, use_tc(a, nc) ? 1 : 0, a.opts.quantity,
              a.opts.threshold, a.opts.I_cut, a.opts.nu_crit, a.opts.I_crit);
+    if (a.opts.profile == XC_VOIGT_VV) {
+        char vb[64];
+        snprintf(vb, sizeof(vb), " vv%.17g/%d", a.opts.vv_split, a.opts.vv_flags);
+        std::string r = std::string(buf) + vb;
+        if (a.L.n_broad > 0) {
+            snprintf(vb, sizeof(vb), " b%d@%p", a.L.n_broad, (const void *)a.L.bgam);
+            r += vb;
+        }
+        return r;
+    }
     if (a.L.n_broad > 0) {
         char bb[64];
         snprintf(bb, sizeof(bb), " b%d@%p", a.L.n_broad, (const void *)a.L.bgam);
@@ -2345,7 +2396,7 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
         set_error("the allocation-free entry point computes the FP32 kernel with a fixed cut");
         return XC_EUNSUPPORTED;
     }
-    if (opts->profile < XC_DOPPLER || opts->profile > XC_LORENTZ_BINNED || !(opts->cutoff > 0.0)) {
+    if (opts->profile < XC_DOPPLER || opts->profile > XC_VOIGT_VV || !(opts->cutoff > 0.0)) {
         set_error("bad opts");
         return XC_EINVAL;
     }
@@ -2359,6 +2410,10 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
     }
     if (opts->quantity != XC_ABSORPTION || opts->threshold != XC_THRESHOLD_NONE) {
         set_error("emission and intensity thresholds: use xc_cross_section_batched");
+        return XC_EUNSUPPORTED;
+    }
+    if (opts->profile == XC_VOIGT_VV) {
+        set_error("the Vectorized Voigt: use xc_cross_section_batched");
         return XC_EUNSUPPORTED;
     }
     for (size_t i = 0; i < n_cond; ++i) {

@@ -69,6 +69,9 @@ struct LinesDev {
     // at gamma_lc[l * gamma_stride + c], computed in FP64
     const float *gamma_lc = nullptr;
     int gamma_stride = 0;
+    // FP32 kernels with VVN: intensity factor of line l, condition row c at vv_scale[l * nc + c]
+    const float *vv_scale = nullptr;
+    int vv_stride = 0;
 };
 
 struct CondDev {  // mirrors xc_condition plus resolved Q
@@ -263,6 +266,23 @@ __device__ inline Cx<R> w4_eval(R x, R y, Cx<R> *dF) {
     }
 }
 
+// unit-area Voigt by w4: sqrt(ln2/pi)/alpha Re w(x + iy), x = sqrt(ln2) D/alpha, y = sqrt(ln2) gamma/alpha
+__device__ inline double voigt64(double D, double al, double ga) {
+    double ia = kSqrtLn2 / al;
+    Cx<double> w = w4_eval<double>(D * ia, ga * ia, nullptr);
+    return 0.46971863934982566 / al * w.re;
+}
+
+// Eq. (e:fast-v): the Voigt within split of the centre, beyond it the Voigt of a line at 1 cm^-1
+// (Doppler HWHM alpha / nu) times beta (Eq. e:beta, or 1)
+__device__ inline double voigt_vv64(double D, double al, double ga, double nul, double split, int beta) {
+    if (fabs(D) <= split) return voigt64(D, al, ga);
+    const double ar = al / nul;
+    const double b = beta ? voigt64(split, al, ga) / voigt64(split, ar, ga) : 1.0;
+    return b * voigt64(D, ar, ga);
+}
+
+
 
 // ---------------------------------------------------------------------------
 // Host-side helpers
@@ -323,7 +343,16 @@ cudaError_t launch_count_evals(const LinesDev &L, size_t n, const CondDev *conds
 cudaError_t launch_gather_f64(int profile, const double *nu, const double *I, const double *alpha,
                               const double *gamma, const double *cut, const int64_t *win_lo,
                               const int64_t *win_hi, int64_t n_win, double nu_A, double step, int64_t n_pts,
-                              const double *ghx, const double *ghw, int ngh, double *sigma, cudaStream_t s);
+                              const double *ghx, const double *ghw, int ngh, double *sigma, cudaStream_t s,
+                              double vv_split = 4.0, int vv_beta = 0);
+// VVN: I[l] /= h sum_k f_VV(nu_k - nu_l) over the line's cut window on the grid lattice
+cudaError_t launch_vv_norm64(const double *nu, double *I, const double *alpha, const double *gamma,
+                             const double *cut, size_t n, double nu_A, double step, double vv_split, int vv_beta,
+                             cudaStream_t s);
+// VVN for the FP32 kernels: scale[l * nc + c] = 1 / (h sum_k f_VV) of line l, condition c
+cudaError_t launch_vv_norm32(const LinesDev &L, size_t n, const CondDev *conds, int nc, double nu_A, double step,
+                             double cutoff, double width_mult, double vv_split, int vv_beta, float *scale,
+                             cudaStream_t s);
 cudaError_t launch_gh_nodes(int n, double *x, double *w, cudaStream_t s);
 
 }  // namespace xc

@@ -181,6 +181,48 @@ cudaError_t launch_line_gamma(const LinesDev &L, size_t n, const CondDev *conds,
     return cudaGetLastError();
 }
 
+// VVN for the FP32 kernels, one warp per (line, condition): 1 / (h sum_k f_VV) over the
+// lattice points within the line's cut (fixed, or width-limited as the kernels take it)
+__global__ void __launch_bounds__(256) k_vv_norm32(LinesDev L, size_t n, const CondDev *__restrict__ conds, int nc,
+                                                   double nu_A, double step, double cutoff, double width_mult,
+                                                   double split, int beta, float *scale) {
+    const int lane = threadIdx.x & 31;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
+    const size_t pairs = n * (size_t)nc;
+    for (size_t q = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < pairs; q += warps) {
+        const size_t l = q / (size_t)nc;
+        const int c = (int)(q % (size_t)nc);
+        const CondDev cd = conds[c];
+        const double nul = L.nu[l];
+        const double al = alpha_coef(cd.T, cd.mass_da) * nul;
+        const double ga = L.n_broad > 0 ? mixture_gamma64(L, l, cd)
+                                        : cd.gamma_scale * (double)L.gamma_ref[l] *
+                                              exp(((double)L.n_T[l] + cd.n_shift) * log(cd.T_ref / cd.T)) *
+                                              (cd.P / cd.P_ref);
+        const double cut = width_mult > 0.0 ? fmin(width_mult * fmax(al, ga), cutoff) : cutoff;
+        const int64_t k0 = (int64_t)floor((nul - cut - nu_A) / step) - 1;
+        const int64_t k1 = (int64_t)floor((nul + cut - nu_A) / step) + 1;
+        double sum = 0.0;
+        for (int64_t k = k0 + lane; k <= k1; k += 32) {
+            const double D = __dsub_rn(grid_x(nu_A, step, k), nul);
+            if (fabs(D) <= cut) sum += voigt_vv64(D, al, ga, nul, split, beta);
+        }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) scale[q] = sum > 0.0 ? (float)(1.0 / (sum * step)) : 0.f;
+    }
+}
+
+cudaError_t launch_vv_norm32(const LinesDev &L, size_t n, const CondDev *conds, int nc, double nu_A, double step,
+                             double cutoff, double width_mult, double vv_split, int vv_beta, float *scale,
+                             cudaStream_t s) {
+    if (n == 0 || nc == 0) return cudaSuccess;
+    size_t blocks = (n * (size_t)nc + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_vv_norm32<<<(unsigned)blocks, 256, 0, s>>>(L, n, conds, nc, nu_A, step, cutoff, width_mult, vv_split, vv_beta,
+                                                 scale);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_line_keep(const LinesDev &L, size_t n, const CondDev *conds, int nc, const StrengthSel &sel,
                              uint32_t *keep, int words, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

@@ -15,8 +15,11 @@ constexpr int G64_THREADS = 256;
 
 template <int PROF>
 __device__ inline double profile64(double D, double step, double al, double ga, const double *ghx,
-                                   const double *ghw, int ngh) {
-    if (PROF == XC_DOPPLER) {
+                                   const double *ghw, int ngh, double nul = 0.0, double split = 4.0,
+                                   int beta = 0) {
+    if (PROF == XC_VOIGT_VV) {
+        return voigt_vv64(D, al, ga, nul, split, beta);
+    } else if (PROF == XC_DOPPLER) {
         // Eq. (e:Gauss): sqrt(ln2/pi)/alpha exp(-D^2 ln2/alpha^2)
         double r = D / al;
         return 0.46971863934982566 / al * exp(-kLn2 * r * r);
@@ -70,7 +73,8 @@ __global__ void __launch_bounds__(G64_THREADS) k_gather_f64(const double *__rest
                                                             double step, int64_t n_pts,
                                                             const double *__restrict__ ghx_g,
                                                             const double *__restrict__ ghw_g, int ngh,
-                                                            double *__restrict__ sigma) {
+                                                            double *__restrict__ sigma, double vv_split,
+                                                            int vv_beta) {
     __shared__ double s_nu[G64_THREADS], s_I[G64_THREADS], s_a[G64_THREADS], s_g[G64_THREADS],
         s_c[G64_THREADS];
     __shared__ double s_ghx[64], s_ghw[64];
@@ -99,7 +103,9 @@ __global__ void __launch_bounds__(G64_THREADS) k_gather_f64(const double *__rest
         if (active) {
             for (int i = 0; i < cnt; ++i) {
                 double D = __dsub_rn(xk, s_nu[i]);
-                if (fabs(D) <= s_c[i]) acc += s_I[i] * profile64<PROF>(D, step, s_a[i], s_g[i], s_ghx, s_ghw, ngh);
+                if (fabs(D) <= s_c[i])
+                    acc += s_I[i] * profile64<PROF>(D, step, s_a[i], s_g[i], s_ghx, s_ghw, ngh, s_nu[i], vv_split,
+                                                    vv_beta);
             }
         }
     }
@@ -109,41 +115,59 @@ __global__ void __launch_bounds__(G64_THREADS) k_gather_f64(const double *__rest
 cudaError_t launch_gather_f64(int profile, const double *nu, const double *I, const double *alpha,
                               const double *gamma, const double *cut, const int64_t *win_lo,
                               const int64_t *win_hi, int64_t n_win, double nu_A, double step, int64_t n_pts,
-                              const double *ghx, const double *ghw, int ngh, double *sigma, cudaStream_t s) {
+                              const double *ghx, const double *ghw, int ngh, double *sigma, cudaStream_t s,
+                              double vv_split, int vv_beta) {
     if (n_win <= 0) return cudaSuccess;
     dim3 grid((unsigned)n_win), block(G64_THREADS);
+#define XC_G64(P) k_gather_f64<P><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A, step, \
+                                                        n_pts, ghx, ghw, ngh, sigma, vv_split, vv_beta)
     switch (profile) {
-    case XC_DOPPLER:
-        k_gather_f64<XC_DOPPLER><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A, step,
-                                                       n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_LORENTZ:
-        k_gather_f64<XC_LORENTZ><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A, step,
-                                                       n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_VOIGT_W4:
-        k_gather_f64<XC_VOIGT_W4><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A, step,
-                                                        n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_VOIGT_GH_BINNED:
-        k_gather_f64<XC_VOIGT_GH_BINNED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
-                                                               step, n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_VOIGT_GH_SAMPLED:
-        k_gather_f64<XC_VOIGT_GH_SAMPLED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
-                                                                step, n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_DOPPLER_BINNED:
-        k_gather_f64<XC_DOPPLER_BINNED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
-                                                              step, n_pts, ghx, ghw, ngh, sigma);
-        break;
-    case XC_LORENTZ_BINNED:
-        k_gather_f64<XC_LORENTZ_BINNED><<<grid, block, 0, s>>>(nu, I, alpha, gamma, cut, win_lo, win_hi, nu_A,
-                                                              step, n_pts, ghx, ghw, ngh, sigma);
-        break;
+    case XC_DOPPLER: XC_G64(XC_DOPPLER); break;
+    case XC_LORENTZ: XC_G64(XC_LORENTZ); break;
+    case XC_VOIGT_W4: XC_G64(XC_VOIGT_W4); break;
+    case XC_VOIGT_GH_BINNED: XC_G64(XC_VOIGT_GH_BINNED); break;
+    case XC_VOIGT_GH_SAMPLED: XC_G64(XC_VOIGT_GH_SAMPLED); break;
+    case XC_DOPPLER_BINNED: XC_G64(XC_DOPPLER_BINNED); break;
+    case XC_LORENTZ_BINNED: XC_G64(XC_LORENTZ_BINNED); break;
+    case XC_VOIGT_VV: XC_G64(XC_VOIGT_VV); break;
     default:
         return cudaErrorInvalidValue;
     }
+#undef XC_G64
+    return cudaGetLastError();
+}
+
+// VVN normalisation, one warp per line: Sigma = h sum_k f_VV over the lattice points
+// nu_A + k h within the line's cut (the grid extended past its ends), summed in FP64 in a
+// fixed order (strided lanes, then a butterfly), then I /= Sigma
+__global__ void __launch_bounds__(256) k_vv_norm64(const double *__restrict__ nu, double *__restrict__ I,
+                                                   const double *__restrict__ alpha,
+                                                   const double *__restrict__ gamma, const double *__restrict__ cut,
+                                                   size_t n, double nu_A, double step, double split, int beta) {
+    const int lane = threadIdx.x & 31;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
+    for (size_t l = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); l < n; l += warps) {
+        const double nul = nu[l], al = alpha[l], ga = gamma[l], c = cut[l];
+        if (!(c >= 0.0)) continue;   // a line the intensity threshold left out
+        const int64_t k0 = (int64_t)floor((nul - c - nu_A) / step) - 1;
+        const int64_t k1 = (int64_t)floor((nul + c - nu_A) / step) + 1;
+        double sum = 0.0;
+        for (int64_t k = k0 + lane; k <= k1; k += 32) {
+            const double D = __dsub_rn(grid_x(nu_A, step, k), nul);
+            if (fabs(D) <= c) sum += voigt_vv64(D, al, ga, nul, split, beta);
+        }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) I[l] = sum > 0.0 ? I[l] / (sum * step) : 0.0;
+    }
+}
+
+cudaError_t launch_vv_norm64(const double *nu, double *I, const double *alpha, const double *gamma,
+                             const double *cut, size_t n, double nu_A, double step, double vv_split, int vv_beta,
+                             cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t blocks = (n + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_vv_norm64<<<(unsigned)blocks, 256, 0, s>>>(nu, I, alpha, gamma, cut, n, nu_A, step, vv_split, vv_beta);
     return cudaGetLastError();
 }
 

@@ -507,6 +507,41 @@ def test_broadener_mixture(eng, xc, oracle_lib):
     assert metrics(plain, r0)[0] < TOL64
 
 
+@pytest.mark.parametrize("beta,norm", [(False, False), (True, False), (False, True), (True, True)])
+def test_vectorized_voigt(eng, xc, oracle_lib, beta, norm):
+    """Eq. (e:fast-v) with beta = 1 or Eq. (e:beta), and VVN: FP64 and the FP32 batched sweep
+    (6 conditions) against the oracle; the exact zone 1.5 cm^-1, so the reference wing
+    carries most points."""
+    L = xs.gen_lines(113, 0, 2000, 3000.0, 3040.0)
+    E, g = xs.gen_states(113, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    nu_A, step, n, cut, split = 2990.0, 0.05, 1301, 8.0, 1.5
+    TP = [(2500.0, 0.3), (800.0, 1.0), (1500.0, 0.05), (3000.0, 3.0), (400.0, 0.5), (2000.0, 0.01)]
+    grid = xc.make_grid(nu_A, step, n)
+    kw = dict(vv_split=split, vv_beta=beta, vv_norm=norm)
+
+    def ref(j):
+        Q, dQ = oracle_lib.partition_function(E, g, TP[j][0])
+        c = oracle_lib.make_condition(TP[j][0], TP[j][1], Q, dQ)
+        return oracle_lib.cross_section(L, c, nu_A, step, n, oracle_lib.make_opts("voigt_vv", cut, **kw),
+                                        nthreads=NTHREADS)
+
+    refs = {j: ref(j) for j in (0, 3, 5)}
+    for j in (0, 3):
+        got = eng.cross_section(xc.make_condition(*TP[j]), grid, xc.make_opts("voigt_vv", "fp64", cut, **kw))
+        m64, b64 = metrics(got, refs[j])
+        assert m64 < TOL64 and b64 < TOL64, (j, m64, b64)
+    got = eng.cross_section_batched([xc.make_condition(T, P) for T, P in TP], grid,
+                                    xc.make_opts("voigt_vv", "fp32", cut, **kw))
+    worst = (0.0, 0.0)
+    for j, r in refs.items():
+        mr, band = metrics(got[j], r)
+        worst = (max(worst[0], mr), max(worst[1], band))
+    print(f"vectorized voigt beta={beta} norm={norm}: fp32 worst max rel {worst[0]:.3g}, band {worst[1]:.3g}")
+    assert worst[0] < TOL32 and worst[1] < TOL32_BAND
+
+
 def test_c1_full_size(eng, xc, oracle_lib):
     """The single-condition FP64 workload at full size: 1e5 lines, 200001 points."""
     W = xs.WORKLOADS["C1"]
