@@ -421,7 +421,10 @@ __device__ __forceinline__ W4Zone w4_zone(float ah, float gh) {
 // radius) when that kernel takes the far wings (d4), else D3
 __device__ __noinline__ float w4_value_f32(float delta, const float4 &B);
 
-template <int PROF>
+// EXT: the options that change a line's constants per (line, condition) -- emission,
+// intensity thresholds, broadener mixtures, VVN -- are honoured; without them (EXT = false)
+// the Voigt-w4 hot kernels carry none of their checks
+template <int PROF, bool EXT = true>
 __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const CParam &c, float h, float inv_h,
                                             float4 *A, float4 *B, float *thr2, float4 *S, bool d4 = false) {
     const float nu = (float)L.nu[l];
@@ -430,7 +433,7 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     float z = fmaf(E, c.kT_hi, E * c.kT_lo);
     float boltz = exp2_neg(z);
     float I;
-    if (c.emis != 0.f) {
+    if (EXT && c.emis != 0.f) {
         // Eq. (e:emiss) times h c nu: the upper state's Boltzmann factor as exp(-c2 E''/T)
         // exp(-c2 nu/T), each to ~1 ulp
         I = c.pref * ((float)L.g_up[l] * L.A[l]) * nu * boltz * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo));
@@ -439,12 +442,12 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         I = c.pref * ((float)L.g_up[l] * L.A[l]) * rcp_approx(nu * nu) * boltz * stim;
     }
     // left out by the intensity threshold for this condition (decided in FP64)
-    if (L.keep && !((L.keep[l * (size_t)L.keep_words + (c.row >> 5)] >> (c.row & 31)) & 1u)) I = 0.f;
+    if (EXT && L.keep && !((L.keep[l * (size_t)L.keep_words + (c.row >> 5)] >> (c.row & 31)) & 1u)) I = 0.f;
     // VVN: this (line, condition)'s area normalisation (computed in FP64)
-    if (L.vv_scale) I *= L.vv_scale[l * (size_t)L.vv_stride + c.row];
+    if (EXT && L.vv_scale) I *= L.vv_scale[l * (size_t)L.vv_stride + c.row];
     float al = c.acoef * nu;                                                   // Eq. e:alphaD
     float ah, gh;                                                              // widths in grid steps
-    if (L.gamma_lc) {
+    if (EXT && L.gamma_lc) {
         // broadener mixture: the width of this (line, condition), computed in FP64
         ah = __fmul_rn(c.acoef * nu, inv_h);
         gh = __fmul_rn(L.gamma_lc[l * (size_t)L.gamma_stride + c.row], inv_h);
@@ -671,7 +674,7 @@ __device__ __forceinline__ void w4_series_pair(f32x2 (&acc)[R / 2][CG], int c, c
     }
 }
 
-template <int PROF, int R, int CG>
+template <int PROF, int R, int CG, bool EXT = true>
 __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherParams p) {
     constexpr unsigned kAllConds = CG >= 32 ? 0xffffffffu : ((1u << CG) - 1u);
     using Lay = SmemLayout<PROF, R, CG>;
@@ -769,7 +772,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     float4 A, B = make_float4(0.f, 0.f, 0.f, -1.f);
                     float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                     if (cc < p.n_cond) {
-                        line_consts<PROF>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
+                        line_consts<PROF, EXT>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
                                           &t2, &S, p.tc_far != 0);
                     } else {  // padding condition: contributes exactly 0
                         if (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV) A = make_float4(1.f, 1.f, 0.f, 0.f);
@@ -1206,15 +1209,18 @@ __device__ __forceinline__ int tc_b_index(int n, int k) {
 
 // series coefficients (p0, p1, p2) and far radius D4 of a (line, condition), p3 in *p3;
 // D4 is the same value line_consts gives (same inputs, same rounded operations)
+template <bool EXT>
 __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, const CParam &c, float inv_h,
                                                    float *p3, float ga_lc) {
     const float nu = ph.x, E = ph.y;
     const float z = fmaf(E, c.kT_hi, E * c.kT_lo);
-    const float I = c.emis != 0.f
-                        ? c.pref * (ph.z * (nu * nu * nu)) * exp2_neg(z) * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo))
-                        : c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
+    float I;
+    if (EXT && c.emis != 0.f)
+        I = c.pref * (ph.z * (nu * nu * nu)) * exp2_neg(z) * exp2_neg(fmaf(nu, c.kT_hi, nu * c.kT_lo));
+    else
+        I = c.pref * ph.z * exp2_neg(z) * (-expm1f(-c.c2T * nu));
     float ah, gh;
-    if (ga_lc >= 0.f) {   // broadener mixture: this (line, condition)'s width (see line_consts)
+    if (EXT && ga_lc >= 0.f) {   // broadener mixture: this (line, condition)'s width (see line_consts)
         ah = __fmul_rn(c.acoef * nu, inv_h);
         gh = __fmul_rn(ga_lc, inv_h);
     } else {
@@ -1230,6 +1236,7 @@ __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, c
     return make_float4(P, P * c1, P * c2, zn.D4);
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     float *sB = reinterpret_cast<float *>(smem);                           // [blk][buf][hi, lo][768]
@@ -1347,9 +1354,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
                     const size_t lg = (size_t)lo + (size_t)(l0 + lB);
-                    const float ga_lc = p.gamma_lc ? p.gamma_lc[lg * (size_t)p.gamma_stride + cpr.row] : -1.f;
-                    S = tc_series_consts(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3, ga_lc);
-                    if (p.keep && !((p.keep[lg * (size_t)p.keep_words + (cpr.row >> 5)] >> (cpr.row & 31)) & 1u)) {
+                    const float ga_lc =
+                        (EXT && p.gamma_lc) ? p.gamma_lc[lg * (size_t)p.gamma_stride + cpr.row] : -1.f;
+                    S = tc_series_consts<EXT>(sPhys[b * TC_L + lB], sNT[b * TC_L + lB], cpr, p.inv_h, &p3, ga_lc);
+                    if (EXT && p.keep && !((p.keep[lg * (size_t)p.keep_words + (cpr.row >> 5)] >> (cpr.row & 31)) & 1u)) {
                         S.x = S.y = S.z = 0.f;   // left out by the intensity threshold
                         p3 = 0.f;
                     }
@@ -1680,12 +1688,17 @@ struct Variant {
     int profile, R, CG;
     GatherFn fn;
     size_t smem;
+    bool ext;   // honours the per-(line, condition) options (see line_consts)
 };
 
-#define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG>, SmemLayout<P, R, CG>::total}
+#define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, true>, SmemLayout<P, R, CG>::total, true}
+#define XC_VARIANT_PLAIN(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, false>, SmemLayout<P, R, CG>::total, false}
 static const Variant kVariants[] = {
-    XC_VARIANT(XC_VOIGT_W4, 4, 16), XC_VARIANT(XC_VOIGT_W4, 2, 32), XC_VARIANT(XC_VOIGT_W4, 4, 8),
-    XC_VARIANT(XC_VOIGT_W4, 8, 8),  XC_VARIANT(XC_VOIGT_W4, 8, 4),  XC_VARIANT(XC_VOIGT_W4, 8, 2),
+    // Voigt w4: the plain hot kernels, and the shapes that carry the per-(line, condition) options
+    XC_VARIANT_PLAIN(XC_VOIGT_W4, 4, 16), XC_VARIANT_PLAIN(XC_VOIGT_W4, 2, 32), XC_VARIANT_PLAIN(XC_VOIGT_W4, 4, 8),
+    XC_VARIANT_PLAIN(XC_VOIGT_W4, 8, 8),  XC_VARIANT_PLAIN(XC_VOIGT_W4, 8, 4),  XC_VARIANT_PLAIN(XC_VOIGT_W4, 8, 2),
+    XC_VARIANT_PLAIN(XC_VOIGT_W4, 8, 1),
+    XC_VARIANT(XC_VOIGT_W4, 4, 16), XC_VARIANT(XC_VOIGT_W4, 4, 8), XC_VARIANT(XC_VOIGT_W4, 8, 4),
     XC_VARIANT(XC_VOIGT_W4, 8, 1),
     XC_VARIANT(XC_LORENTZ, 4, 16),  XC_VARIANT(XC_LORENTZ, 8, 8),   XC_VARIANT(XC_LORENTZ, 8, 4),
     XC_VARIANT(XC_LORENTZ, 8, 1),
@@ -1702,6 +1715,13 @@ static const Variant kVariants[] = {
     XC_VARIANT(XC_VOIGT_VV, 8, 1),
 };
 static const int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+static_assert(sizeof(kVariants) / sizeof(kVariants[0]) <= 64, "configure_variant tracks at most 64 variants");
+
+// the call uses an option that changes constants per (line, condition)
+bool needs_ext(const BatchedArgs &a) {
+    return a.opts.quantity != XC_ABSORPTION || a.opts.threshold != XC_THRESHOLD_NONE || a.L.n_broad > 0 ||
+           (a.opts.profile == XC_VOIGT_VV && (a.opts.vv_flags & XC_VV_NORMALISE));
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -1932,7 +1952,10 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.h = gp.h;
         tp.inv_h = gp.inv_h;
         tp.sigma = gp.sigma;
-        k_far_tc<<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
+        if (needs_ext(a))
+            k_far_tc<true><<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
+        else
+            k_far_tc<false><<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
         if (ev && a.ev_tc1) BT_TRY(cudaEventRecordWithFlags(a.ev_tc1, s, cudaEventRecordExternal));
         *launches += 2;
     }
@@ -2013,11 +2036,14 @@ static char g_tc_diag[160] = "";
 int tc_grid_size(int n_tiles) {
     if (g_tc_per_sm < 0) {
         int ps = 0;
-        cudaError_t e1 = cudaFuncSetAttribute((const void *)k_far_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)TC_SMEM);
-        cudaError_t e2 = e1 == cudaSuccess
-                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, (const void *)k_far_tc, TC_T, TC_SMEM)
-                             : e1;
+        cudaError_t e1 = cudaFuncSetAttribute((const void *)k_far_tc<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        if (e1 == cudaSuccess)
+            e1 = cudaFuncSetAttribute((const void *)k_far_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TC_SMEM);
+        cudaError_t e2 = e1 == cudaSuccess ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                                 &ps, (const void *)k_far_tc<false>, TC_T, TC_SMEM)
+                                           : e1;
         // The occupancy query answers 1 for this kernel (it does not model tensor-memory
         // allocation); residency is bounded by shared memory (TC_SMEM admits 2 CTAs), by
         // registers, and by the 512 TMEM columns of an SM (2 x 256).  Extra CTAs would
@@ -2026,9 +2052,10 @@ int tc_grid_size(int n_tiles) {
         int dev0 = 0, smem_sm = 0;
         cudaGetDevice(&dev0);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev0);
-        int by_regs = 1, by_smem = 1;
-        if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc) == cudaSuccess && fa.numRegs > 0)
-            by_regs = 65536 / (fa.numRegs * TC_T);
+        int by_regs = 1, by_smem = 1, regs = 0;
+        if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc<false>) == cudaSuccess) regs = fa.numRegs;
+        if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc<true>) == cudaSuccess) regs = std::max(regs, fa.numRegs);
+        if (regs > 0) by_regs = 65536 / (regs * TC_T);
         if (smem_sm > 0) by_smem = smem_sm / (int)(TC_SMEM + 1024);
         const int mine = std::max(1, std::min((int)(512 / TC_COLS), std::min(by_regs, by_smem)));
         snprintf(g_tc_diag, sizeof(g_tc_diag), "query %d (%s), registers %d, shared memory %d", ps,
@@ -2090,6 +2117,7 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
         for (int i = 0; i < kNumVariants; ++i) {
             const Variant &v = kVariants[i];
             if (v.profile != a.opts.profile) continue;
+            if (v.profile == XC_VOIGT_W4 && v.ext != needs_ext(a)) continue;
             if (a.opts.width_mult > 0.0 && v.CG != 1) continue;  // per-condition cut: one condition per tile
             if (pass == 0 && a.opts.width_mult <= 0.0 && st->force_R == 0) {
                 if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
@@ -2450,7 +2478,9 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
     const Variant *v = nullptr;
     int want_cg = nc >= 16 ? 16 : (nc >= 8 ? 8 : (nc >= 4 ? 4 : 1));
     for (int i = 0; i < kNumVariants && !v; ++i)
-        if (kVariants[i].profile == opts->profile && kVariants[i].CG == want_cg) v = &kVariants[i];
+        if (kVariants[i].profile == opts->profile && kVariants[i].CG == want_cg &&
+            (kVariants[i].profile != XC_VOIGT_W4 || !kVariants[i].ext))   // no per-(line, condition) options here
+            v = &kVariants[i];
     for (int i = 0; i < kNumVariants && !v; ++i)  // profiles compiled with fewer group sizes
         if (kVariants[i].profile == opts->profile && kVariants[i].CG <= want_cg) v = &kVariants[i];
     if (!v) { set_error("no kernel variant for this profile"); return XC_EUNSUPPORTED; }
