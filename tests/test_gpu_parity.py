@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here; the FP32 bound is w4 region-boundary jumps plus FP32 rounding):
   FP64 path: max relative error <= 1e-5 over bins above 1e-6 of the peak
              (measured ~1e-12: only the rounding of exp/pow differs).
   FP32 path: max relative error <= 2e-4 over bins above 1e-6 of the peak and
