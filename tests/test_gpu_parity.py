@@ -597,6 +597,74 @@ def test_edge_cases(eng, xc, oracle_lib):
                           xc.make_opts("voigt_gh_binned", "fp32", 1.0, n_gh=0))
 
 
+def test_option_errors(eng, xc):
+    """Bad option values are EINVAL; the paths that do not implement an option refuse it
+    with EUNSUPPORTED (the adjoint, the allocation-free entry point); reloading the lines
+    drops a broadener mixture."""
+    import ctypes as C
+    L = xs.gen_lines(114, 0, 500, 1000.0, 1005.0)
+    E, g = xs.gen_states(114, 500)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    cond, grid = xc.make_condition(900.0, 1.0), xc.make_grid(999.0, 0.01, 701)
+
+    def status(fn):
+        try:
+            fn()
+        except xc.XcError as e:
+            return e.status
+        return 0
+
+    bad = []
+    o = xc.make_opts("voigt_vv", "fp64", 3.0); o.vv_split = -1.0; bad.append(o)
+    o = xc.make_opts("voigt_vv", "fp64", 3.0); o.vv_flags = 4; bad.append(o)
+    o = xc.make_opts("voigt_w4", "fp64", 3.0); o.quantity = 2; bad.append(o)
+    o = xc.make_opts("voigt_w4", "fp64", 3.0); o.threshold = 3; bad.append(o)
+    bad.append(xc.make_opts("voigt_w4", "fp64", 3.0, threshold=("hitran", 0.0, 1e-29)))
+    bad.append(xc.make_opts("voigt_w4", "fp64", 3.0, threshold=("constant", -1.0)))
+    o = xc.make_opts("voigt_w4", "fp64", 3.0); o.profile = 8; bad.append(o)
+    for o in bad:
+        assert status(lambda: eng.cross_section(cond, grid, o)) in (1, 5), (o.profile, o.quantity, o.threshold)
+    # broadening misuse
+    a1 = xc.make_broadener("a1", 1.0, 0.05, 0.5, {(3, 4): (0.06, 0.6)})
+    assert status(lambda: eng.set_broadening([a1])) == 1                      # a1 needs J'
+    dup = xc.make_broadener("a0", 1.0, 0.05, 0.5, {2: (0.06, 0.6), 3: (0.07, 0.6)})
+    dup._keep[0][:] = 2                                                       # two rows keyed J'' = 2
+    assert status(lambda: eng.set_broadening([dup])) == 1
+    neg = xc.make_broadener("constant", -0.5, 0.05, 0.5)
+    assert status(lambda: eng.set_broadening([neg])) == 1
+    many = [xc.make_broadener("constant", 0.1, 0.05, 0.5)] * 9
+    assert status(lambda: eng.set_broadening(many)) == 1
+    # the adjoint refuses emission, thresholds and the Vectorized Voigt
+    gs = np.ones((1, grid.n))
+    for o in (xc.make_opts("voigt_w4", "fp64", 3.0, quantity="emission"),
+              xc.make_opts("voigt_w4", "fp64", 3.0, threshold=("constant", 1e-30)),
+              xc.make_opts("voigt_vv", "fp64", 3.0)):
+        assert status(lambda: eng.cross_section_vjp([cond], grid, o, gs)) == 5
+    # the allocation-free entry point refuses them too (and the binned profiles)
+    o_ = np.argsort(L["nu"], kind="stable")
+    dl = {k: torch.from_numpy(v[o_]).cuda() for k, v in L.items()}
+    dE, dg = torch.from_numpy(E).cuda(), torch.from_numpy(g).cuda()
+    out = torch.zeros((1, grid.n), dtype=torch.float64, device="cuda:0")
+    Ls = xc.XcLines(dl["nu"].data_ptr(), dl["elower"].data_ptr(), dl["A"].data_ptr(), dl["gamma_ref"].data_ptr(),
+                    dl["n_T"].data_ptr(), dl["g_up"].data_ptr(), dl["j_lo"].data_ptr(), xc.XC_MEM_DEVICE)
+    arr = (xc.XcCondition * 1)(cond)
+    for o in (xc.make_opts("voigt_w4", "fp32", 3.0, quantity="emission"),
+              xc.make_opts("voigt_w4", "fp32", 3.0, threshold=("hitran", 2000.0, 1e-29)),
+              xc.make_opts("voigt_vv", "fp32", 3.0), xc.make_opts("doppler_binned", "fp32", 3.0)):
+        rc = xc.lib().xc_cross_section_batched_static(C.byref(Ls), len(o_), dE.data_ptr(), dg.data_ptr(), len(E),
+                                                      arr, 1, C.byref(grid), C.byref(o), out.data_ptr(), None)
+        assert rc == 5, (o.profile, rc)
+    # a mixture belongs to the lines it was set for
+    plain = eng.cross_section(cond, grid, xc.make_opts("voigt_w4", "fp64", 3.0))
+    eng.set_broadening([xc.make_broadener("constant", 1.0, 0.2, 0.5)])
+    wide = eng.cross_section(cond, grid, xc.make_opts("voigt_w4", "fp64", 3.0))
+    assert not np.allclose(wide, plain, rtol=1e-3, atol=0)
+    eng.load_lines(L)
+    again = eng.cross_section(cond, grid, xc.make_opts("voigt_w4", "fp64", 3.0))
+    assert np.array_equal(again, plain)
+
+
 def test_deterministic_and_memory_kinds_agree(eng, xc):
     L = xs.gen_lines(111, 0, 20000, 0.0, 100.0)
     E, g = xs.gen_states(111, 1000)
