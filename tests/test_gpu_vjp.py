@@ -122,14 +122,14 @@ def test_vjp_c4_against_central_differences(eng, xc):
         Pm[c] *= 1 - h
         fdp = (loss(T0, Pp)[0] - loss(T0, Pm)[0]) / (2 * h * P0[c])
         for r in (r64, r32):
-            assert float(r["dT"][c]) == pytest.approx(fd, rel=1e-4), (c, float(r["dT"][c]), fd)
-            assert float(r["dP"][c]) == pytest.approx(fdp, rel=1e-4), (c, float(r["dP"][c]), fdp)
+            assert float(r["dT"][c]) == pytest.approx(fd, rel=1e-4, abs=0), (c, float(r["dT"][c]), fd)
+            assert float(r["dP"][c]) == pytest.approx(fdp, rel=1e-4, abs=0), (c, float(r["dP"][c]), fdp)
     fds = (loss(T0, P0, s=1 + h)[0] - loss(T0, P0, s=1 - h)[0]) / (2 * h)
     dn = 1e-4
     fdn = (loss(T0, P0, dn=dn)[0] - loss(T0, P0, dn=-dn)[0]) / (2 * dn)
     for r in (r64, r32):
-        assert float(r["d_gamma_scale"][0]) == pytest.approx(fds, rel=1e-4)
-        assert float(r["d_n_shift"][0]) == pytest.approx(fdn, rel=1e-4)
+        assert float(r["d_gamma_scale"][0]) == pytest.approx(fds, rel=1e-4, abs=0)
+        assert float(r["d_n_shift"][0]) == pytest.approx(fdn, rel=1e-4, abs=0)
 
 
 def test_vjp_c4_subset_against_oracle(eng, xc, oracle_lib):
@@ -178,4 +178,4 @@ def test_autograd_function(eng, xc):
     assert torch.allclose(T.grad, r["dT"].cpu(), rtol=1e-10, atol=0)
     assert torch.allclose(P.grad, r["dP"].cpu(), rtol=1e-10, atol=0)
     assert float(T.grad.abs().min()) > 0
-    assert float(s.grad) == pytest.approx(float(r["d_gamma_scale"][0]))
+    assert float(s.grad) == pytest.approx(float(r["d_gamma_scale"][0]), abs=0)

@@ -32,15 +32,15 @@ def test_partition_two_level_and_limits(oracle_lib):
     for T in (50.0, 296.0, 3000.0):
         Q, dQ = oracle_lib.partition_function(E, g, T)
         x = c2 * 1234.5 / T
-        assert Q == pytest.approx(3 + 7 * math.exp(-x), rel=1e-14)
-        assert dQ == pytest.approx(7 * math.exp(-x) * x / T, rel=1e-13)
+        assert Q == pytest.approx(3 + 7 * math.exp(-x), rel=1e-14, abs=0)
+        assert dQ == pytest.approx(7 * math.exp(-x) * x / T, rel=1e-13, abs=0)
     # T -> infinity: every state counts fully
     Es, gs = xs.gen_states(5, 5000)
     Q, _ = oracle_lib.partition_function(Es, gs, 1e14)
-    assert Q == pytest.approx(gs.sum(), rel=1e-8)
+    assert Q == pytest.approx(gs.sum(), rel=1e-8, abs=0)
     # T -> 0: only the ground level (E = 0) survives
     Q0, _ = oracle_lib.partition_function(E, g, 1.0)
-    assert Q0 == pytest.approx(3.0, rel=1e-14)
+    assert Q0 == pytest.approx(3.0, rel=1e-14, abs=0)
 
 
 def test_partition_derivative_matches_finite_difference(oracle_lib):
@@ -50,7 +50,7 @@ def test_partition_derivative_matches_finite_difference(oracle_lib):
         Qp, _ = oracle_lib.partition_function(E, g, T + h)
         Qm, _ = oracle_lib.partition_function(E, g, T - h)
         _, dQ = oracle_lib.partition_function(E, g, T)
-        assert dQ == pytest.approx((Qp - Qm) / (2 * h), rel=1e-7)
+        assert dQ == pytest.approx((Qp - Qm) / (2 * h), rel=1e-7, abs=0)
 
 
 # --------------------------------------------- intensity, Eq. (e:int)
@@ -69,25 +69,25 @@ def test_intensity_equals_einstein_population_difference(oracle_lib):
         nu_pop = gu * math.exp(-c2 * Eu / T) / Q
         expect = A * gu / (8 * math.pi * c_cm * nu ** 2 * gl) * (nl - gl / gu * nu_pop)
         cond = oracle_lib.make_condition(T, 1.0, Q)
-        assert oracle_lib.intensity(nu, El, A, gu, cond) == pytest.approx(expect, rel=1e-12)
+        assert oracle_lib.intensity(nu, El, A, gu, cond) == pytest.approx(expect, rel=1e-12, abs=0)
 
 
 def test_intensity_structure(oracle_lib):
     cond = oracle_lib.make_condition(1000.0, 1.0, 345.0)
     base = oracle_lib.intensity(2000.0, 1000.0, 1.0, 3.0, cond)
-    assert oracle_lib.intensity(2000.0, 1000.0, 2.0, 3.0, cond) == pytest.approx(2 * base, rel=1e-15)
-    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 6.0, cond) == pytest.approx(2 * base, rel=1e-15)
+    assert oracle_lib.intensity(2000.0, 1000.0, 2.0, 3.0, cond) == pytest.approx(2 * base, rel=1e-15, abs=0)
+    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 6.0, cond) == pytest.approx(2 * base, rel=1e-15, abs=0)
     # Boltzmann ratio between lower levels
     r = oracle_lib.intensity(2000.0, 3000.0, 1.0, 3.0, cond) / base
-    assert r == pytest.approx(math.exp(-1.438776877503934 * 2000.0 / 1000.0), rel=1e-13)
+    assert r == pytest.approx(math.exp(-1.438776877503934 * 2000.0 / 1000.0), rel=1e-13, abs=0)
     # abundance scales I linearly (Sec. 2.1 remark) and Q divides it
     c2 = oracle_lib.make_condition(1000.0, 1.0, 690.0, abundance=0.25)
-    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 3.0, c2) == pytest.approx(base / 8, rel=1e-15)
+    assert oracle_lib.intensity(2000.0, 1000.0, 1.0, 3.0, c2) == pytest.approx(base / 8, rel=1e-15, abs=0)
     # small c2 nu/T: (1 - e^{-x}) -> x, so I -> g A c2 /(8 pi c nu T Q) ; tests the expm1 branch
     hot = oracle_lib.make_condition(1e6, 1.0, 1.0)
     nu = 1e-3
     expect = 1.0 * 1.438776877503934 / (8 * math.pi * 2.99792458e10 * nu * 1e6)
-    assert oracle_lib.intensity(nu, 0.0, 1.0, 1.0, hot) == pytest.approx(expect, rel=1e-8)
+    assert oracle_lib.intensity(nu, 0.0, 1.0, 1.0, hot) == pytest.approx(expect, rel=1e-8, abs=0)
 
 
 # --------------------------------------------- emissivity, Eq. (e:emiss); thresholds
@@ -102,7 +102,7 @@ def test_emissivity_over_intensity_is_planck(oracle_lib):
         cond = oracle_lib.make_condition(T, 1.0, Q)
         B = 2 * h * c ** 2 * nu ** 3 / math.expm1(h * c * nu / (k * T))
         ratio = oracle_lib.emissivity(nu, El, A, g, cond) / oracle_lib.intensity(nu, El, A, g, cond)
-        assert ratio == pytest.approx(B, rel=1e-12)
+        assert ratio == pytest.approx(B, rel=1e-12, abs=0)
 
 
 def test_emissivity_from_upper_state_population(oracle_lib):
@@ -114,7 +114,7 @@ def test_emissivity_from_upper_state_population(oracle_lib):
     frac = gu * math.exp(-c2 * (El + nu) / T) / Q
     expect = frac * A * (sc.h * 1e7) * (sc.c * 100.0) * nu / (4 * math.pi)
     eps = oracle_lib.emissivity(nu, El, A, gu, oracle_lib.make_condition(T, 1.0, Q))
-    assert eps == pytest.approx(expect, rel=1e-12)
+    assert eps == pytest.approx(expect, rel=1e-12, abs=0)
 
 
 def test_hitran_dynamic_threshold(oracle_lib):
@@ -122,10 +122,10 @@ def test_hitran_dynamic_threshold(oracle_lib):
     I_crit nu/nu_crit where c2 nu >> T and to I_crit c2 nu^2 / (2 T nu_crit) where c2 nu << T."""
     o = oracle_lib.make_opts(threshold=("hitran", 2000.0, 1e-29))
     assert oracle_lib.threshold(2500.0, 296.0, o) == 1e-29
-    assert oracle_lib.threshold(1999.0, 50.0, o) == pytest.approx(1e-29 * 1999.0 / 2000.0, rel=1e-12)
+    assert oracle_lib.threshold(1999.0, 50.0, o) == pytest.approx(1e-29 * 1999.0 / 2000.0, rel=1e-12, abs=0)
     nu, T = 0.01, 3000.0
     c2 = 1.438776877503933802
-    assert oracle_lib.threshold(nu, T, o) == pytest.approx(1e-29 * c2 * nu * nu / (2 * T * 2000.0), rel=1e-9)
+    assert oracle_lib.threshold(nu, T, o) == pytest.approx(1e-29 * c2 * nu * nu / (2 * T * 2000.0), rel=1e-9, abs=0)
     assert oracle_lib.threshold(500.0, 1000.0, o) < oracle_lib.threshold(1000.0, 1000.0, o) < 1e-29
     assert oracle_lib.threshold(123.0, 1000.0, oracle_lib.make_opts(threshold=("constant", 3e-25))) == 3e-25
     assert oracle_lib.threshold(123.0, 1000.0, oracle_lib.make_opts()) == 0.0
@@ -170,22 +170,22 @@ def test_vectorized_voigt_zones(oracle_lib):
     nu, a, g = 30000.0, 0.2, 0.01
     for D in (0.0, 0.3, -2.5, 3.99):
         v = oracle_lib.voigt_vv(D, a, g, nu)
-        assert v == pytest.approx(sp.voigt_profile(D, a / LN2S, g), rel=1.2e-4)
+        assert v == pytest.approx(sp.voigt_profile(D, a / LN2S, g), rel=1.2e-4, abs=0)
     for D in (4.01, -6.0, 20.0):
         v = oracle_lib.voigt_vv(D, a, g, nu)
         ref = sp.voigt_profile(D, a / nu / LN2S, g)
-        assert v == pytest.approx(ref, rel=1.2e-4)
+        assert v == pytest.approx(ref, rel=1.2e-4, abs=0)
         own = sp.voigt_profile(D, a / LN2S, g)
         if abs(D) < 10:
             assert abs(own / ref - 1) > 1e-3    # alpha_ref, not alpha, shapes the wing
     # beta makes the profile continuous at the split point; beta = 1 leaves a jump
     left = oracle_lib.voigt_vv(4.0, a, g, nu, beta=True)
     right = oracle_lib.voigt_vv(4.0 * (1 + 1e-13), a, g, nu, beta=True)
-    assert right == pytest.approx(left, rel=1e-9)
-    assert oracle_lib.voigt_vv(4.0 * (1 + 1e-13), a, g, nu) != pytest.approx(left, rel=1e-4)
+    assert right == pytest.approx(left, rel=1e-9, abs=0)
+    assert oracle_lib.voigt_vv(4.0 * (1 + 1e-13), a, g, nu) != pytest.approx(left, rel=1e-4, abs=0)
     # a custom split moves the switch
     assert oracle_lib.voigt_vv(3.0, a, g, nu, split=2.0) == pytest.approx(sp.voigt_profile(3.0, a / nu / LN2S, g),
-                                                                           rel=1.2e-4)
+                                                                           rel=1.2e-4, abs=0)
 
 
 def test_vvn_conserves_each_line_area(oracle_lib):
@@ -198,7 +198,7 @@ def test_vvn_conserves_each_line_area(oracle_lib):
         N = int(round(30.0 / h)) + 1
         on = oracle_lib.cross_section(L, cond, 990.0, h, N, oracle_lib.make_opts("voigt_vv", 8.0, vv_norm=True),
                                       nthreads=2)
-        assert on.sum() * h == pytest.approx(I, rel=1e-12)
+        assert on.sum() * h == pytest.approx(I, rel=1e-12, abs=0)
         if h == 1.0:
             off = oracle_lib.cross_section(L, cond, 990.0, h, N, oracle_lib.make_opts("voigt_vv", 8.0), nthreads=2)
             assert abs(off.sum() * h / I - 1) > 1e-3
@@ -249,10 +249,10 @@ def test_broad_a0_table_from_the_paper(oracle_lib):
     b = oracle_lib.make_broadener("a0", 1.0, 0.07, 0.5, rows)
     ref = oracle_lib.make_condition(296.0, 1.0, 1.0)
     for j, (g0, n) in rows.items():
-        assert oracle_lib.gamma_mixture(j, j + 1, [b], ref) == pytest.approx(g0, rel=1e-15)
+        assert oracle_lib.gamma_mixture(j, j + 1, [b], ref) == pytest.approx(g0, rel=1e-15, abs=0)
         hot = oracle_lib.make_condition(1184.0, 2.0, 1.0)   # T_ref / T = 1/4
-        assert oracle_lib.gamma_mixture(j, j, [b], hot) == pytest.approx(g0 * 0.25 ** n * 2.0, rel=1e-14)
-    assert oracle_lib.gamma_mixture(10, 11, [b], ref) == pytest.approx(0.07, rel=1e-15)
+        assert oracle_lib.gamma_mixture(j, j, [b], hot) == pytest.approx(g0 * 0.25 ** n * 2.0, rel=1e-14, abs=0)
+    assert oracle_lib.gamma_mixture(10, 11, [b], ref) == pytest.approx(0.07, rel=1e-15, abs=0)
 
 
 def test_broad_a1_and_mixture_are_weighted_single_broadeners(oracle_lib):
@@ -264,13 +264,13 @@ def test_broad_a1_and_mixture_are_weighted_single_broadeners(oracle_lib):
         c = oracle_lib.make_condition(T, P, 1.0, gamma_scale=1.1, n_shift=0.05)
         for (jl, ju), (g0, n) in (((3, 4), (0.08, 0.7)), ((3, 2), (0.06, 0.4)), ((3, 3), (0.05, 0.6))):
             expect = 0.7 * oracle_lib.gamma_lorentz(g0, n, c) + 0.3 * oracle_lib.gamma_lorentz(0.03, 0.25, c)
-            assert oracle_lib.gamma_mixture(jl, ju, [a1, cst], c) == pytest.approx(expect, rel=1e-14)
+            assert oracle_lib.gamma_mixture(jl, ju, [a1, cst], c) == pytest.approx(expect, rel=1e-14, abs=0)
     # two halves of one broadener are that broadener
     half = oracle_lib.make_broadener("constant", 0.5, 0.03, 0.25)
     one = oracle_lib.make_broadener("constant", 1.0, 0.03, 0.25)
     c = oracle_lib.make_condition(700.0, 3.0, 1.0)
     assert oracle_lib.gamma_mixture(0, 1, [half, half], c) == pytest.approx(oracle_lib.gamma_mixture(0, 1, [one], c),
-                                                                            rel=1e-15)
+                                                                            rel=1e-15, abs=0)
 
 
 def test_cross_section_with_a0_broadening_equals_per_line_widths(oracle_lib):
@@ -295,19 +295,19 @@ def test_doppler_hwhm_textbook_constant(oracle_lib):
     # alpha_D = 3.581e-7 * nu * sqrt(T / M[g/mol])  (the usual practical form)
     for T, nu in ((296.0, 1000.0), (3000.0, 10000.0)):
         cond = oracle_lib.make_condition(T, 1.0, 1.0, mass_da=18.0)
-        assert oracle_lib.alpha_doppler(nu, cond) == pytest.approx(3.5812e-7 * nu * math.sqrt(T / 18.0), rel=2e-4)
+        assert oracle_lib.alpha_doppler(nu, cond) == pytest.approx(3.5812e-7 * nu * math.sqrt(T / 18.0), rel=2e-4, abs=0)
     c1 = oracle_lib.make_condition(400.0, 1.0, 1.0)
     c4 = oracle_lib.make_condition(1600.0, 1.0, 1.0)
-    assert oracle_lib.alpha_doppler(2000.0, c4) == pytest.approx(2 * oracle_lib.alpha_doppler(2000.0, c1), rel=1e-15)
+    assert oracle_lib.alpha_doppler(2000.0, c4) == pytest.approx(2 * oracle_lib.alpha_doppler(2000.0, c1), rel=1e-15, abs=0)
 
 
 def test_lorentz_hwhm_scaling(oracle_lib):
     ref = oracle_lib.make_condition(296.0, 1.0, 1.0)
-    assert oracle_lib.gamma_lorentz(0.07, 0.5, ref) == pytest.approx(0.07, rel=1e-15)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, ref) == pytest.approx(0.07, rel=1e-15, abs=0)
     hot = oracle_lib.make_condition(592.0, 3.0, 1.0)
-    assert oracle_lib.gamma_lorentz(0.07, 0.5, hot) == pytest.approx(0.07 * 3.0 / math.sqrt(2.0), rel=1e-14)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, hot) == pytest.approx(0.07 * 3.0 / math.sqrt(2.0), rel=1e-14, abs=0)
     sc = oracle_lib.make_condition(592.0, 1.0, 1.0, gamma_scale=1.05, n_shift=0.25)
-    assert oracle_lib.gamma_lorentz(0.07, 0.5, sc) == pytest.approx(1.05 * 0.07 * 0.5 ** 0.75, rel=1e-14)
+    assert oracle_lib.gamma_lorentz(0.07, 0.5, sc) == pytest.approx(1.05 * 0.07 * 0.5 ** 0.75, rel=1e-14, abs=0)
 
 
 # --------------------------------------------- profiles
@@ -315,14 +315,14 @@ def test_gauss_is_normal_pdf_with_hwhm(oracle_lib):
     a = 0.037
     sig = a / math.sqrt(2 * LN2)
     for D in (0.0, 0.01, -0.05, 0.2):
-        assert oracle_lib.gauss(D, a) == pytest.approx(st.norm.pdf(D, scale=sig), rel=1e-13)
-    assert oracle_lib.gauss(a, a) == pytest.approx(0.5 * oracle_lib.gauss(0.0, a), rel=1e-14)
+        assert oracle_lib.gauss(D, a) == pytest.approx(st.norm.pdf(D, scale=sig), rel=1e-13, abs=0)
+    assert oracle_lib.gauss(a, a) == pytest.approx(0.5 * oracle_lib.gauss(0.0, a), rel=1e-14, abs=0)
 
 
 def test_lorentz_is_cauchy_pdf(oracle_lib):
     g = 0.061
     for D in (0.0, 0.03, -1.0, 24.9):
-        assert oracle_lib.lorentz(D, g) == pytest.approx(st.cauchy.pdf(D, scale=g), rel=1e-13)
+        assert oracle_lib.lorentz(D, g) == pytest.approx(st.cauchy.pdf(D, scale=g), rel=1e-13, abs=0)
 
 
 def test_w4_against_faddeeva(oracle_lib):
@@ -381,12 +381,12 @@ def test_voigt_is_library_voigt_and_limits(oracle_lib):
     a, g = 0.02, 0.03
     sig = a / math.sqrt(2 * LN2)
     for D in (0.0, 0.01, 0.05, -0.3, 5.0, 24.0):
-        assert oracle_lib.voigt_w4(D, a, g) == pytest.approx(sp.voigt_profile(D, sig, g), rel=1.2e-4)
+        assert oracle_lib.voigt_w4(D, a, g) == pytest.approx(sp.voigt_profile(D, sig, g), rel=1.2e-4, abs=0)
     # gamma -> 0: Gaussian ; alpha -> 0: Lorentzian (Eqs. e:Gauss, e:lor)
     for D in (0.0, 0.01, 0.03):
-        assert oracle_lib.voigt_w4(D, a, 1e-9) == pytest.approx(oracle_lib.gauss(D, a), rel=1.2e-4)
+        assert oracle_lib.voigt_w4(D, a, 1e-9) == pytest.approx(oracle_lib.gauss(D, a), rel=1.2e-4, abs=0)
     for D in (0.0, 0.01, 0.3):
-        assert oracle_lib.voigt_w4(D, 1e-7, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1.2e-4)
+        assert oracle_lib.voigt_w4(D, 1e-7, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1.2e-4, abs=0)
     assert oracle_lib.voigt_w4(0.037, a, g) == oracle_lib.voigt_w4(-0.037, a, g)
 
 
@@ -402,9 +402,9 @@ def test_gauss_hermite_nodes(oracle_lib):
         xr, wr = np.polynomial.hermite.hermgauss(n)
         assert np.allclose(x, xr, atol=1e-13, rtol=0)
         assert np.allclose(w, wr, rtol=1e-11, atol=1e-300)
-        assert w.sum() == pytest.approx(math.sqrt(math.pi), rel=1e-14)
+        assert w.sum() == pytest.approx(math.sqrt(math.pi), rel=1e-14, abs=0)
         for k in range(0, 2 * n, 2):  # exact for polynomials of degree <= 2n-1
-            assert np.dot(w, x ** k) == pytest.approx(math.gamma(k / 2 + 0.5), rel=1e-10)
+            assert np.dot(w, x ** k) == pytest.approx(math.gamma(k / 2 + 0.5), rel=1e-10, abs=0)
 
 
 def test_gh_sampled_voigt_converges_to_voigt(oracle_lib):
@@ -412,9 +412,9 @@ def test_gh_sampled_voigt_converges_to_voigt(oracle_lib):
     a, g = 0.02, 0.03
     sig = a / math.sqrt(2 * LN2)
     for D in (0.0, 0.02, 0.1, 1.0):
-        assert oracle_lib.voigt_gh(D, a, g, 30) == pytest.approx(sp.voigt_profile(D, sig, g), rel=2e-3)
+        assert oracle_lib.voigt_gh(D, a, g, 30) == pytest.approx(sp.voigt_profile(D, sig, g), rel=2e-3, abs=0)
     val, _ = si.quad(lambda D: oracle_lib.voigt_gh(D, a, g, 20), -np.inf, np.inf, limit=400)
-    assert val == pytest.approx(1.0, rel=1e-8)
+    assert val == pytest.approx(1.0, rel=1e-8, abs=0)
 
 
 def test_gh_binned_telescopes_and_matches_bin_average(oracle_lib):
@@ -426,12 +426,12 @@ def test_gh_binned_telescopes_and_matches_bin_average(oracle_lib):
     top, bot = (K + 0.5) * h, -(K + 0.5) * h
     expect = sum(w[j] * (math.atan((top - a * x[j] / math.sqrt(LN2)) / g)
                          - math.atan((bot - a * x[j] / math.sqrt(LN2)) / g)) for j in range(20)) / math.pi ** 1.5
-    assert tot == pytest.approx(expect, rel=1e-12)
+    assert tot == pytest.approx(expect, rel=1e-12, abs=0)
     # bin average of the exact Voigt, within the quadrature error of 20 nodes
     sig = a / math.sqrt(2 * LN2)
     for D in (0.0, 0.01, 0.05, 0.5):
         ex, _ = si.quad(lambda u: sp.voigt_profile(u, sig, g), D - h / 2, D + h / 2)
-        assert oracle_lib.voigt_gh_binned(D, h, a, g, 20) == pytest.approx(ex / h, rel=5e-3)
+        assert oracle_lib.voigt_gh_binned(D, h, a, g, 20) == pytest.approx(ex / h, rel=5e-3, abs=0)
 
 
 @pytest.mark.parametrize("h", [0.004, 0.01, 0.1])
@@ -442,12 +442,12 @@ def test_binned_gauss_and_lorentz_are_bin_averages(oracle_lib, h):
     sig = a / math.sqrt(2 * LN2)
     for D in (0.0, 0.3 * h, -0.7 * h, 2.0 * h, 0.05, -0.12, 0.3):
         ex, _ = si.quad(lambda u: st.norm.pdf(u, scale=sig), D - h / 2, D + h / 2, epsabs=0, epsrel=1e-13)
-        assert oracle_lib.gauss_binned(D, h, a) == pytest.approx(ex / h, rel=1e-10)
+        assert oracle_lib.gauss_binned(D, h, a) == pytest.approx(ex / h, rel=1e-10, abs=0)
         ex, _ = si.quad(lambda u: st.cauchy.pdf(u, scale=g), D - h / 2, D + h / 2, epsabs=0, epsrel=1e-13)
-        assert oracle_lib.lorentz_binned(D, h, g) == pytest.approx(ex / h, rel=1e-10)
+        assert oracle_lib.lorentz_binned(D, h, g) == pytest.approx(ex / h, rel=1e-10, abs=0)
         # symmetric in D
-        assert oracle_lib.gauss_binned(-D, h, a) == pytest.approx(oracle_lib.gauss_binned(D, h, a), rel=1e-14)
-        assert oracle_lib.lorentz_binned(-D, h, g) == pytest.approx(oracle_lib.lorentz_binned(D, h, g), rel=1e-14)
+        assert oracle_lib.gauss_binned(-D, h, a) == pytest.approx(oracle_lib.gauss_binned(D, h, a), rel=1e-14, abs=0)
+        assert oracle_lib.lorentz_binned(-D, h, g) == pytest.approx(oracle_lib.lorentz_binned(D, h, g), rel=1e-14, abs=0)
 
 
 def test_binned_gauss_and_lorentz_conserve_area_on_coarse_grids(oracle_lib):
@@ -458,17 +458,17 @@ def test_binned_gauss_and_lorentz_conserve_area_on_coarse_grids(oracle_lib):
         K = 400
         for off in (0.0, 0.013):
             gb = sum(oracle_lib.gauss_binned(k * h + off, h, a) for k in range(-K, K + 1)) * h
-            assert gb == pytest.approx(1.0, rel=1e-13)
+            assert gb == pytest.approx(1.0, rel=1e-13, abs=0)
             lb = sum(oracle_lib.lorentz_binned(k * h + off, h, g) for k in range(-K, K + 1)) * h
             top, bot = (K + 0.5) * h + off, -(K + 0.5) * h + off
-            assert lb == pytest.approx((st.cauchy.cdf(top, scale=g) - st.cauchy.cdf(bot, scale=g)), rel=1e-12)
+            assert lb == pytest.approx((st.cauchy.cdf(top, scale=g) - st.cauchy.cdf(bot, scale=g)), rel=1e-12, abs=0)
     # the sampled Gaussian on the coarse grid (points 2.5 alpha either side) keeps ~6 %
     smp = sum(oracle_lib.gauss(k * 0.1 + 0.05, a) for k in range(-40, 41)) * 0.1
     assert smp < 0.1
     # narrow bins: the bin average tends to the sampled profile (error ~ h^2 f''/24)
     for D in (0.0, 0.01, 0.04):
-        assert oracle_lib.gauss_binned(D, 1e-5, a) == pytest.approx(oracle_lib.gauss(D, a), rel=1e-7)
-        assert oracle_lib.lorentz_binned(D, 1e-5, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1e-7)
+        assert oracle_lib.gauss_binned(D, 1e-5, a) == pytest.approx(oracle_lib.gauss(D, a), rel=1e-7, abs=0)
+        assert oracle_lib.lorentz_binned(D, 1e-5, g) == pytest.approx(oracle_lib.lorentz(D, g), rel=1e-7, abs=0)
 
 
 def test_binned_lorentz_is_one_node_binned_gauss_hermite(oracle_lib):
@@ -477,7 +477,7 @@ def test_binned_lorentz_is_one_node_binned_gauss_hermite(oracle_lib):
     g, h = 0.015, 0.01
     for D in (0.0, 0.004, 0.05, 1.3):
         assert oracle_lib.voigt_gh_binned(D, h, 1e-300, g, 20) == pytest.approx(
-            oracle_lib.lorentz_binned(D, h, g), rel=1e-13)
+            oracle_lib.lorentz_binned(D, h, g), rel=1e-13, abs=0)
 
 
 # --------------------------------------------- full cross sections
@@ -582,12 +582,12 @@ def test_sampled_area_equals_intensity(oracle_lib):
     h = 0.001
     nu_A, N = 1990.0, 20001
     s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("doppler", 5.0))
-    assert s.sum() * h == pytest.approx(I, rel=1e-9)
+    assert s.sum() * h == pytest.approx(I, rel=1e-9, abs=0)
     s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("lorentz", 5.0))
-    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=1e-6)
+    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=1e-6, abs=0)
     s = oracle_lib.cross_section(L, cond, nu_A, h, N, oracle_lib.make_opts("voigt_gh_binned", 5.0))
     # binned GH conserves the area of the truncated profile exactly (telescoping), ~ I atan-limited
-    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=2e-5)
+    assert s.sum() * h == pytest.approx(I * 2 / math.pi * math.atan(5.0 / ga), rel=2e-5, abs=0)
 
 
 def test_threads_are_deterministic_and_agree(oracle_lib):
@@ -662,8 +662,8 @@ def test_vjp_matches_central_differences(oracle_lib, profile):
         a = gref.copy(); a[l] = v
         return loss(T, P, gref=a)
     fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
-    assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4)
-    assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12)
+    assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4, abs=0)
+    assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12, abs=0)
     # the adjoint covers absorption without a threshold only
     for o2 in (oracle_lib.make_opts(profile, cut, quantity="emission"),
                oracle_lib.make_opts(profile, cut, threshold=("constant", 1e-30))):
