@@ -44,9 +44,6 @@ inline StrengthSel strength_sel(const xc_opts &o) {
     return s;
 }
 
-// w4 region-I constant (Humlicek 1982): w ~ t * 0.5641896 / (0.5 + t^2)
-constexpr double kW4c1 = 0.5641896;
-
 // Stage slots of the timing table (see xc_last_timings)
 enum Stage { ST_SORT = 0, ST_GATHER, ST_Q, ST_PARAMS, ST_RANGES, ST_PROFILE, ST_VJP, ST_FINISH, ST_COUNT };
 

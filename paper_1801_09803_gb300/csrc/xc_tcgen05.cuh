@@ -105,25 +105,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x = hi + lo with hi exactly representable in TF32 (round to nearest, ties away)
-__device__ __forceinline__ float tf32_hi(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // hi = x with the 13 low mantissa bits cleared (exact in TF32; one logic op), for
 // splits x = hi + lo whose lo enters the product too
 __device__ __forceinline__ float tf32_trunc(float x) {
     return __int_as_float(__float_as_int(x) & (int)0xffffe000);
-}
-
-// the same split on the FMA pipe (Veltkamp): hi keeps the leading 11 significant bits
-// (exact in TF32), lo = x - hi exactly; for |x| < 2^100
-__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
-    const float c = __fmul_rn(x, 8193.0f);   // 2^13 + 1
-    hi = __fsub_rn(c, __fsub_rn(c, x));
-    lo = __fsub_rn(x, hi);
 }
 
 }  // namespace tc
