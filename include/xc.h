@@ -17,7 +17,9 @@
  *     synchronise that stream before returning.
  *   - Units (paper Table t:units): wavenumber cm^-1, temperature K, pressure
  *     in units of P_ref, intensity cm/molecule, cross section
- *     cm^2/molecule = cm/(molecule cm^-1).
+ *     cm^2/molecule = cm/(molecule cm^-1); with XC_EMISSION the line strength is
+ *     an emissivity (erg/s/sr per molecule) and sigma its emission spectrum
+ *     (erg/s/sr per molecule per cm^-1).
  *   - Per-line arrays that the library returns are in the library's sorted
  *     order (ascending wavenumber, ties by input position);
  *     xc_get_permutation() maps sorted position -> input position.
