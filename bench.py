@@ -31,10 +31,11 @@ import xcsynth as xs  # noqa: E402
 
 METRIC = "line x gridpoint Voigt evals/s (FP32 batched, 32 conditions)"
 UNIT = "evals/s"
-# FP32 flops of one region-I w4 evaluation with the per-line constants hoisted:
-# t = u + E (1), D = u t + F (2), q = P u + PC (2), q / D (1), accumulate (2).
-# At the FMA/MUFU bound of 32 evals/clk/SM this is exactly the FP32 peak of 256 flops/clk/SM.
-ALG_FLOPS_PER_EVAL = 8
+# Algorithmic FP32 flops of one region-I w4 evaluation with the per-line constants
+# hoisted (about 10 operations and one reciprocal per line x point): the offset
+# delta = (k - n) - f (2), u = delta^2 (1), t = u + E (1), D = u t + F (2),
+# q = P u + PC (2), q / D (1), accumulate (1).
+ALG_FLOPS_PER_EVAL = 10
 # One tcgen05.mma of the far-wing kernel: M = 128 points, N = 32 conditions, K = 8.
 MMA_FLOPS = 2 * 128 * 32 * 8
 # TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU).
@@ -159,6 +160,25 @@ def make_workload(args, rank):
 
 
 # ---------------------------------------------------------------------------- reference arm
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_oracle_rate(W, lines, E, g, conds, budget_s=12.0, threads=None):
     """Time the FP64 oracle (as it stands) on a bounded sample: the first lines of the
     list, doubling until the run takes a few seconds; return evals/s."""
@@ -182,7 +202,8 @@ def cpu_oracle_rate(W, lines, E, g, conds, budget_s=12.0, threads=None):
         if dt > budget_s / 4 or n_try >= total:
             break
         n_try = min(total, n_try * 4 if dt < budget_s / 40 else n_try * 2)
-    return {"value": best[0], "unit": UNIT, "cores": threads, "kind": "oracle", "seconds": best[3],
+    return {"value": best[0], "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
+            "seconds": best[3],
             "sample": f"first {best[1]} lines of the {W.name} list, 1 of {len(conds)} conditions, "
                       f"full grid ({best[2]:.3g} evals in {best[3]:.1f} s)"}
 
@@ -236,7 +257,7 @@ def run_reference(args, dist, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(W, n, len(conds)),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                          "sample": r["sample"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -350,6 +371,7 @@ def run_xc(args, dist, rank, world, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     prof_ms, core_ms, sweep_ms, launches = [], [], [], 0
     kern = []   # per step: (far-wing tensor ms, CUDA-core ms, centre-zone ms, MMA count)
+    far_evals = []   # per step: evaluations the tensor-core far-wing kernel covered
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -360,6 +382,7 @@ def run_xc(args, dist, rank, world, local):
             core_ms.append(t["ranges_or_core"])
             sweep_ms.append(t["params_or_sweep"])
             kern.append(eng.sweep_kernels())
+            far_evals.append(eng.far_evals())
             launches += eng.last_launch_count()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -448,8 +471,11 @@ def run_xc(args, dist, rank, world, local):
         per_kernel = {"k_far_tc": far_ms, "k_gather_f32": main_ms, "k_core_w4_f32": cz_ms, "mma_per_launch": mma}
         pk, basis = peaks()
         tf32_peak = pk["bf16_tflops"] * TF32_PER_BF16
-        ach = mma * MMA_FLOPS / (far_ms / 1e3) / 1e12
-        dominant = max(per_kernel, key=lambda k: per_kernel[k] if k != "mma_per_launch" else -1)
+        nfar = far_evals[-1]
+        per_kernel["far_evals_per_launch"] = nfar
+        ach = nfar * ALG_FLOPS_PER_EVAL / (far_ms / 1e3) / 1e12
+        issued = mma * MMA_FLOPS / (far_ms / 1e3) / 1e12
+        dominant = max(("k_far_tc", "k_gather_f32", "k_core_w4_f32"), key=lambda k: per_kernel[k])
         traffic = None
         if args.workload == "C3" and not args.profile:
             traffic = TC_DRAM_READ_PER_LINE * n + TC_DRAM_WRITE_1M_PTS_32C * (nc / 32) * (W.n_points / 1e6)
@@ -459,8 +485,12 @@ def run_xc(args, dist, rank, world, local):
                                "scaled by the line count (profiles/k_far_tc_c3_1e6lines_32cond.md)",
               "kernel": "k_far_tc (tcgen05.mma kind::tf32, far wings)",
               "peak_basis": f"TF32 dense = {basis} BF16 burst {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal ratio)",
-              "flops": "executed MMA flops: MMAs per launch x 2 x 128 x 32 x 8", "kernel_ms": far_ms,
-              "dominant_kernel_of_sweep": dominant}
+              "flops": f"algorithmic: far-wing evaluations counted by the kernel ({nfar:.4g} per launch, "
+                       f"{nfar / evals:.3f} of the step's evals) x {ALG_FLOPS_PER_EVAL} flops per region-I eval",
+              "issued": {"value": issued, "unit": "TFLOP/s", "frac": issued / tf32_peak,
+                         "flops": "executed MMA flops: MMAs per launch x 2 x 128 x 32 x 8 (operand splits and "
+                                  "zero B entries included)"},
+              "kernel_ms": far_ms, "dominant_kernel_of_sweep": dominant}
     cpu = None
     if not args.no_cpu:
         cpu = cpu_oracle_rate(W, lines, E, g, conds_py)

@@ -67,6 +67,7 @@ struct xc_handle {
     float last_ms[ST_COUNT] = {};
     double kernel_ms[3] = {-1.0, -1.0, -1.0};   // last FP32 sweep: far-wing (tensor), main, centre zone
     int64_t tc_mma = 0;
+    int64_t tc_far_evals = 0;   // last FP32 sweep: evaluations the tensor-core kernel covered
     int64_t launches = 0;
     BatchedState batched;
 };
@@ -840,6 +841,7 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
             h->last_ms[ST_RANGES] = ms;
         // per kernel: far wings on the tensor cores (if they ran), CUDA-core kernel, centre zone
         h->tc_mma = batched_tc_mma_count(&h->batched);
+        h->tc_far_evals = batched_tc_far_evals(&h->batched);
         h->kernel_ms[0] = h->kernel_ms[1] = h->kernel_ms[2] = -1.0;
         if (h->tc_mma > 0) {
             if (cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE], h->ev[2 * ST_COUNT]) == cudaSuccess)
@@ -941,6 +943,14 @@ xc_status xc_last_sweep_kernels(xc_handle *h, double *ms_out, int64_t *mma_out) 
     if (!ms_out || !mma_out) { set_error("NULL out"); return XC_EINVAL; }
     for (int i = 0; i < 3; ++i) ms_out[i] = h->kernel_ms[i];
     *mma_out = h->tc_mma;
+    return XC_OK;
+}
+
+xc_status xc_last_far_evals(xc_handle *h, int64_t *far_evals_out) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (!far_evals_out) { set_error("NULL out"); return XC_EINVAL; }
+    *far_evals_out = h->tc_far_evals;
     return XC_OK;
 }
 

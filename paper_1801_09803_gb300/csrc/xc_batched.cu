@@ -1195,6 +1195,7 @@ struct TcParams {
     const unsigned *blk_lo, *blk_hi;   // per TC_T-point super-block: line range
     int *counter;
     int *status;                       // set to 1 if a wait ran out
+    unsigned long long *far_evals;     // (line, point, condition) evaluations covered, or nullptr
     int n_tiles, n_groups, n_cond;
     int64_t n_pts;
     float h, inv_h;
@@ -1279,7 +1280,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     const uint64_t desc_b0 = tc::smem_desc(sB_addr + (uint32_t)(blkh * 2 * TC_BT * TC_BTILE * 4), 128u, 256u);
 
     uint32_t uses[2] = {0u, 0u};   // commits per buffer (each block's barrier of it) so far
-    bool ok = true;
+    unsigned long long n_far = 0;  // this thread's far (line, point, condition) evaluations
+    // `ok` is per thread (its own bounded waits); `stop` is the CTA's agreement, taken at a
+    // barrier, that some wait ran out: from then on no MMA is issued and no output written
+    bool ok = true, stop = false;
     // The (line, condition) pair whose coefficients this thread computes each chunk, chosen
     // so that a warp's B entries of one term fill one 8 x 4 core matrix (32 consecutive
     // floats: conflict-free stores): conditions 8 (w % 4) .. + 7, lines 4 (w / 4) .. + 3.
@@ -1347,12 +1351,14 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             {
                 float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                 float p3 = 0.f;
-                float na = 0.f;
+                float na = 0.f, ka = 0.f, kb = -1.f;
                 bool live = false;
                 if (l0 + lB < nl && cc < p.n_cond) {
                     const float4 g = cGeo[lB];
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
+                    ka = g.z;
+                    kb = g.w;
                     const size_t lg = (size_t)lo + (size_t)(l0 + lB);
                     const float ga_lc =
                         (EXT && p.gamma_lc) ? p.gamma_lc[lg * (size_t)p.gamma_stride + cpr.row] : -1.f;
@@ -1370,6 +1376,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     // so the differences are exact and the test is the same
                     const float b0 = (float)(t0 + hb * TC_M);
                     const bool far = live && ((na - (b0 + (float)(TC_M - 1)) > S.w) || (b0 - na > S.w));
+                    // the block's points inside the line's cut (exact integers in float)
+                    if (far) n_far += (unsigned long long)fmaxf(0.f, fminf(b0 + (float)(TC_M - 1), kb) - fmaxf(b0, ka) + 1.f);
                     float *bt = sB + (size_t)(hb * 2 + b) * TC_BT * TC_BTILE + bix;
                     bt[0 * TC_BTILE] = far ? p0h : 0.f;
                     bt[1 * TC_BTILE] = far ? p0l : 0.f;
@@ -1428,7 +1436,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
-            __syncthreads();
+            if (__syncthreads_or(!ok)) {   // a buffer may still be in use: issue nothing more
+                stop = true;
+                break;
+            }
             if (issuer) {
                 tc::fence_after_sync();
                 const uint32_t a0 = tblk + 32u + (uint32_t)b * TC_ACOLS;
@@ -1465,6 +1476,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                 in_fold = 0;
             }
         }
+        // the last chunk's accumulator waits decide whether these sums are complete
+        if (stop || __syncthreads_or(!ok)) {
+            stop = true;
+            break;
+        }
         // ---- the super-block's far-wing sums: first writer of these outputs
         const int64_t k = (int64_t)t0 + tid;
         for (int c = 0; c < TC_N; ++c) {
@@ -1475,10 +1491,25 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
         }
     }
+    if (p.far_evals) {
+        for (int o = 16; o > 0; o >>= 1) n_far += __shfl_xor_sync(0xffffffffu, n_far, o);
+        if (lane == 0 && n_far) atomicAdd(p.far_evals, n_far);
+    }
+    if (stop) {
+        // after a wait ran out: before the tensor memory is released, wait (bounded again)
+        // for the last commit of each block's buffers, which covers every MMA issued before
+        // it; the status flag tells the host that this launch's output is not valid
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (uses[b] > 0u)
+#pragma unroll
+                for (int hb = 0; hb < TC_BLK; ++hb)
+                    (void)tc::mbar_wait(&mbar[hb * 2 + b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
+        if (tid == 0) atomicExch(p.status, 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, TC_COLS);
-    if (!ok) atomicExch(p.status, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1765,6 +1796,7 @@ struct Plan {
     int n_blk = 0, n_tc_tiles = 0;              // TC_T-point super-blocks, (super-block, group) tiles
     unsigned *blk_lo = nullptr, *blk_hi = nullptr;
     int *tc_counter = nullptr, *tc_status = nullptr;
+    unsigned long long *tc_far_evals = nullptr;
     float4 *tc_geo = nullptr, *tc_phys = nullptr;
     uint32_t *keep = nullptr;                   // intensity-threshold decisions (with a threshold)
     float *gamma_lc = nullptr;                  // widths per (line, condition) (broadener mixture)
@@ -1835,6 +1867,7 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->blk_hi = (unsigned *)(b + o_bhi);
         pl->tc_counter = (int *)(b + o_tcc);
         pl->tc_status = pl->tc_counter + 1;
+        pl->tc_far_evals = reinterpret_cast<unsigned long long *>(pl->tc_counter + 2);   // 8-byte aligned
         st->tc_blk_lo = pl->blk_lo;
         st->tc_blk_hi = pl->blk_hi;
         st->tc_n_blk = pl->n_blk;
@@ -1842,6 +1875,7 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->tc_geo = (float4 *)(b + o_geo);
         pl->tc_phys = (float4 *)(b + o_phys);
         st->tc_status = pl->tc_status;
+        st->tc_far_evals = pl->tc_far_evals;
     }
     return XC_OK;
 }
@@ -1931,7 +1965,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         // far wings on the tensor cores: first writer of every output of the sweep
         k_win_ranges32<<<(pl.n_blk + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
                                                               TC_T, a.opts.cutoff, pl.n_blk, pl.blk_lo, pl.blk_hi);
-        BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 2 * sizeof(int), s));
+        BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 4 * sizeof(int), s));   // counter, status, far-eval count
         TcParams tp;
         tp.geo = pl.tc_geo;
         tp.phys = pl.tc_phys;
@@ -1945,6 +1979,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.blk_hi = pl.blk_hi;
         tp.counter = pl.tc_counter;
         tp.status = pl.tc_status;
+        tp.far_evals = pl.tc_far_evals;
         tp.n_tiles = pl.n_tc_tiles;
         tp.n_groups = (nc + TC_N - 1) / TC_N;
         tp.n_cond = nc;
@@ -2020,21 +2055,47 @@ std::string shape_key(const BatchedArgs &a, int nc) {
     return buf;
 }
 
+// A kernel attribute set by cudaFuncSetAttribute holds for the current device's context
+// only, so the "already configured" flags are kept per device (and per variant), under a
+// lock because calls may come from several host threads.
+constexpr int kMaxDevices = 64;
+static std::mutex g_attr_mu;
+
 xc_status configure_variant(const Variant *v, int dev) {
-    static bool done[64] = {};
-    int idx = (int)(v - kVariants);
-    if (done[idx]) return XC_OK;
+    static bool done[kMaxDevices][64] = {};
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d beyond the %d this library tracks", dev, kMaxDevices);
+        return XC_EINVAL;
+    }
+    const int idx = (int)(v - kVariants);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (done[dev][idx]) return XC_OK;
     BT_TRY(cudaFuncSetAttribute((const void *)v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
-    done[idx] = true;
-    (void)dev;
+    done[dev][idx] = true;
     return XC_OK;
 }
 
-static int g_tc_per_sm = -1;
-static char g_tc_diag[160] = "";
+// far-wing kernel residency per SM and its diagnosis, per device (-1: not yet set up)
+static int g_tc_per_sm[kMaxDevices] = {};
+static bool g_tc_ready[kMaxDevices] = {};
+static char g_tc_diag[kMaxDevices][160] = {};
+
+int tc_per_sm(int dev) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    return (dev >= 0 && dev < kMaxDevices && g_tc_ready[dev]) ? g_tc_per_sm[dev] : 0;
+}
+
+std::string tc_diag(int dev) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    return (dev >= 0 && dev < kMaxDevices && g_tc_ready[dev]) ? std::string(g_tc_diag[dev]) : std::string();
+}
 
 int tc_grid_size(int n_tiles) {
-    if (g_tc_per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;   // rejected earlier by configure_variant
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (!g_tc_ready[dev]) {
         int ps = 0;
         cudaError_t e1 = cudaFuncSetAttribute((const void *)k_far_tc<false>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -2049,23 +2110,21 @@ int tc_grid_size(int n_tiles) {
         // registers, and by the 512 TMEM columns of an SM (2 x 256).  Extra CTAs would
         // only wait: the work queue is shared.
         cudaFuncAttributes fa;
-        int dev0 = 0, smem_sm = 0;
-        cudaGetDevice(&dev0);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev0);
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         int by_regs = 1, by_smem = 1, regs = 0;
         if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc<false>) == cudaSuccess) regs = fa.numRegs;
         if (cudaFuncGetAttributes(&fa, (const void *)k_far_tc<true>) == cudaSuccess) regs = std::max(regs, fa.numRegs);
         if (regs > 0) by_regs = 65536 / (regs * TC_T);
         if (smem_sm > 0) by_smem = smem_sm / (int)(TC_SMEM + 1024);
         const int mine = std::max(1, std::min((int)(512 / TC_COLS), std::min(by_regs, by_smem)));
-        snprintf(g_tc_diag, sizeof(g_tc_diag), "query %d (%s), registers %d, shared memory %d", ps,
+        snprintf(g_tc_diag[dev], sizeof(g_tc_diag[dev]), "query %d (%s), registers %d, shared memory %d", ps,
                  cudaGetErrorString(e2), by_regs, by_smem);
         cudaGetLastError();
-        g_tc_per_sm = mine;
+        g_tc_per_sm[dev] = mine;
+        g_tc_ready[dev] = true;
     }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    return std::max(1, std::min(num_sms(dev) * g_tc_per_sm, n_tiles));
+    return std::max(1, std::min(num_sms(dev) * g_tc_per_sm[dev], n_tiles));
 }
 
 int grid_size(const Variant *v, int dev, int n_tiles) {
@@ -2209,6 +2268,7 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     // the status word lives in the plan's scratch, which a later plan may reallocate:
     // it is valid only for the run that set it
     st->tc_status = nullptr;
+    st->tc_far_evals = nullptr;
     st->tc_blk_lo = st->tc_blk_hi = nullptr;
     st->tc_n_blk = st->tc_groups = 0;
     if (a.n_lines == 0 || a.n_cond == 0 || a.grid.n == 0) return XC_OK;
@@ -2221,9 +2281,11 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     if ((s = configure_variant(v, dev))) return s;
     {
         char lb[256];
-        if (use_tc(a, a.n_cond))
+        if (use_tc(a, a.n_cond)) {
+            const std::string dg = tc_diag(dev);
             snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points, far wings on tensor cores (%d CTAs/SM%s%s); ",
-                     v->profile, v->R, v->CG, GT * v->R, g_tc_per_sm, g_tc_diag[0] ? ", " : "", g_tc_diag);
+                     v->profile, v->R, v->CG, GT * v->R, tc_per_sm(dev), dg.empty() ? "" : ", ", dg.c_str());
+        }
         else
             snprintf(lb, sizeof(lb), "profile %d R=%d CG=%d W=%d points; ", v->profile, v->R, v->CG, GT * v->R);
         st->last_tuning = std::string(lb) + st->tune_log[tuned_key(st, a, a.n_cond)];
@@ -2304,6 +2366,16 @@ int64_t batched_tc_mma_count(BatchedState *st) {
     for (int i = 0; i < st->tc_n_blk; ++i) chunks += (int64_t)((hi[i] - lo[i] + TC_L - 1) / TC_L);
     // per chunk and 128-point block: 8 MMAs (M = 128, N = 32, K = 8)
     return chunks * st->tc_groups * TC_BLK * 8;
+}
+
+int64_t batched_tc_far_evals(BatchedState *st) {
+    if (!st->tc_far_evals) return 0;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, st->tc_far_evals, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)v;
 }
 
 void batched_invalidate(BatchedState *st) {

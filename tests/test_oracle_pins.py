@@ -653,16 +653,22 @@ def test_vjp_matches_central_differences(oracle_lib, profile):
     d = 1e-5
     fdn = (loss(T, P, dn=d) - loss(T, P, dn=-d)) / (2 * d)
     assert g["d_n_shift"] == pytest.approx(fdn, **tol)
-    # per-line gradients: perturb one line's gamma_ref (float64 copy so the step is exact)
-    # (line records are float32: use perturbed values that are exact float32 numbers)
-    l = 2
-    gref = L["gamma_ref"].copy()
-    vp = np.float32(gref[l] * (1 + 1e-4)); vm = np.float32(gref[l] * (1 - 1e-4))
-    def lg(v):
-        a = gref.copy(); a[l] = v
-        return loss(T, P, gref=a)
-    fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
-    assert g["d_gamma_ref_line"][l] == pytest.approx(fdl, rel=1e-4, abs=0)
+    # per-line gradients, every line: perturb that line's gamma_ref, then its n_T.  Line
+    # records are float32, so the perturbed values are exact float32 numbers and the step
+    # is their exact difference.  A gradient booked to the wrong line, or with a wrong
+    # sign or factor, fails here (the sum identity below would not see a wrong index).
+    for field, key in (("gamma_ref", "d_gamma_ref_line"), ("n_T", "d_n_line")):
+        base = L[field].copy()
+        for l in range(len(base)):
+            vp = np.float32(base[l] * (1 + 1e-4))
+            vm = np.float32(base[l] * (1 - 1e-4))
+
+            def lg(v):
+                a = base.copy()
+                a[l] = v
+                return loss(T, P, **({"gref": a} if field == "gamma_ref" else {"nl": a}))
+            fdl = (lg(vp) - lg(vm)) / (float(vp) - float(vm))
+            assert g[key][l] == pytest.approx(fdl, rel=1e-4, abs=0), (field, l, g[key][l], fdl)
     assert g["d_n_line"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12, abs=0)
     # the adjoint covers absorption without a threshold only
     for o2 in (oracle_lib.make_opts(profile, cut, quantity="emission"),
