@@ -361,6 +361,7 @@ def run_xc(args, dist, rank, world, local):
     # algorithmic work: pairs (line, grid point) inside the cut, summed over conditions
     eng.load_lines(dlines)
     evals = eng.count_evals(conds, grid, opts)
+    far_evals = eng.count_far_evals(conds, grid, opts)   # the tensor-core kernel's share (0 if it does not run)
 
     for _ in range(args.warmup):
         step_device()
@@ -371,7 +372,6 @@ def run_xc(args, dist, rank, world, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     prof_ms, core_ms, sweep_ms, launches = [], [], [], 0
     kern = []   # per step: (far-wing tensor ms, CUDA-core ms, centre-zone ms, MMA count)
-    far_evals = []   # per step: evaluations the tensor-core far-wing kernel covered
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -382,7 +382,6 @@ def run_xc(args, dist, rank, world, local):
             core_ms.append(t["ranges_or_core"])
             sweep_ms.append(t["params_or_sweep"])
             kern.append(eng.sweep_kernels())
-            far_evals.append(eng.far_evals())
             launches += eng.last_launch_count()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -471,7 +470,7 @@ def run_xc(args, dist, rank, world, local):
         per_kernel = {"k_far_tc": far_ms, "k_gather_f32": main_ms, "k_core_w4_f32": cz_ms, "mma_per_launch": mma}
         pk, basis = peaks()
         tf32_peak = pk["bf16_tflops"] * TF32_PER_BF16
-        nfar = far_evals[-1]
+        nfar = far_evals
         per_kernel["far_evals_per_launch"] = nfar
         ach = nfar * ALG_FLOPS_PER_EVAL / (far_ms / 1e3) / 1e12
         issued = mma * MMA_FLOPS / (far_ms / 1e3) / 1e12
@@ -485,7 +484,7 @@ def run_xc(args, dist, rank, world, local):
                                "scaled by the line count (profiles/k_far_tc_c3_1e6lines_32cond.md)",
               "kernel": "k_far_tc (tcgen05.mma kind::tf32, far wings)",
               "peak_basis": f"TF32 dense = {basis} BF16 burst {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal ratio)",
-              "flops": f"algorithmic: far-wing evaluations counted by the kernel ({nfar:.4g} per launch, "
+              "flops": f"algorithmic: the far-wing kernel's evaluations ({nfar:.4g} per launch, "
                        f"{nfar / evals:.3f} of the step's evals) x {ALG_FLOPS_PER_EVAL} flops per region-I eval",
               "issued": {"value": issued, "unit": "TFLOP/s", "frac": issued / tf32_peak,
                          "flops": "executed MMA flops: MMAs per launch x 2 x 128 x 32 x 8 (operand splits and "

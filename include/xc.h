@@ -336,12 +336,14 @@ xc_status xc_last_launch_count(xc_handle *h, int64_t *count_out);
  * N = 32, K = 8, kind::tf32) the tensor-core kernel issued, 0 if it did not run. */
 xc_status xc_last_sweep_kernels(xc_handle *h, double *ms_out, int64_t *mma_out);
 
-/* Algorithmic work of the tensor-core far-wing kernel in the last FP32 batched call
- * with timing enabled (xc_set_timing): the number of (line, grid point, condition)
- * evaluations inside the cut that it summed (its far pairs; each is one region-I w4
- * evaluation of Eq. e:Voigt), counted by the kernel itself.  0 if it did not run or
- * timing was off, -1 if the count could not be read. */
-xc_status xc_last_far_evals(xc_handle *h, int64_t *far_evals_out);
+/* Algorithmic work of the tensor-core far-wing kernel: the number of (line, grid point,
+ * condition) evaluations inside the cut (each one region-I w4 evaluation of Eq. e:Voigt)
+ * that xc_cross_section_batched with the same arguments sums on the tensor cores, found
+ * by a separate kernel that applies the far-wing kernel's own test to the same rounded
+ * values.  0 when the tensor-core kernel would not run (FP64, fewer than 16 conditions,
+ * a width-limited cut, another profile).  Host int64 output; synchronises `stream`. */
+xc_status xc_count_far_evals(xc_handle *h, const xc_condition *conds, size_t n_cond, const xc_grid *grid,
+                             const xc_opts *opts, int64_t *count_out, void *stream);
 
 /* Fix the tile shape of the FP32 CUDA-core kernel for later batched calls on this
  * handle: R grid points per thread and CG conditions per tile, one of the compiled

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
     "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static", "xc_set_tile_shape",
-    "xc_last_sweep_kernels", "xc_set_broadening", "xc_last_far_evals",
+    "xc_last_sweep_kernels", "xc_set_broadening", "xc_count_far_evals",
 ]
 
 
@@ -128,7 +128,8 @@ def lib(build_if_missing: bool = False):
         "xc_set_tile_shape": ([vp, i, i], i),
         "xc_set_broadening": ([vp, vp, i, vp, i, vp], i),
         "xc_last_sweep_kernels": ([vp, vp, C.POINTER(C.c_int64)], i),
-        "xc_last_far_evals": ([vp, C.POINTER(C.c_int64)], i),
+        "xc_count_far_evals": ([vp, C.POINTER(XcCondition), st, C.POINTER(XcGrid), C.POINTER(XcOpts),
+                                C.POINTER(C.c_int64), vp], i),
         "xc_cross_section_batched_static": ([C.POINTER(XcLines), st, vp, vp, st, C.POINTER(XcCondition), st,
                                              C.POINTER(XcGrid), C.POINTER(XcOpts), vp, vp], i),
     }
@@ -396,11 +397,12 @@ class Engine:
         _check(lib().xc_last_sweep_kernels(self._h, ms, C.byref(mma)))
         return ms[0], ms[1], ms[2], int(mma.value)
 
-    def far_evals(self) -> int:
-        """(line, point, condition) evaluations the tensor-core far-wing kernel covered in
-        the last timed FP32 batched call (0 if it did not run)."""
+    def count_far_evals(self, conds: Sequence[XcCondition], grid: XcGrid, opts: XcOpts) -> int:
+        """(line, point, condition) evaluations the tensor-core far-wing kernel takes in a
+        batched call with these arguments (0 when it would not run)."""
+        arr = (XcCondition * len(conds))(*conds)
         v = C.c_int64()
-        _check(lib().xc_last_far_evals(self._h, C.byref(v)))
+        _check(lib().xc_count_far_evals(self._h, arr, len(conds), C.byref(grid), C.byref(opts), C.byref(v), None))
         return int(v.value)
 
     def tuning(self) -> str:

@@ -67,7 +67,6 @@ struct xc_handle {
     float last_ms[ST_COUNT] = {};
     double kernel_ms[3] = {-1.0, -1.0, -1.0};   // last FP32 sweep: far-wing (tensor), main, centre zone
     int64_t tc_mma = 0;
-    int64_t tc_far_evals = 0;   // last FP32 sweep: evaluations the tensor-core kernel covered
     int64_t launches = 0;
     BatchedState batched;
 };
@@ -841,7 +840,6 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
             h->last_ms[ST_RANGES] = ms;
         // per kernel: far wings on the tensor cores (if they ran), CUDA-core kernel, centre zone
         h->tc_mma = batched_tc_mma_count(&h->batched);
-        h->tc_far_evals = batched_tc_far_evals(&h->batched);
         h->kernel_ms[0] = h->kernel_ms[1] = h->kernel_ms[2] = -1.0;
         if (h->tc_mma > 0) {
             if (cudaEventElapsedTime(&ms, h->ev[2 * ST_PROFILE], h->ev[2 * ST_COUNT]) == cudaSuccess)
@@ -946,12 +944,29 @@ xc_status xc_last_sweep_kernels(xc_handle *h, double *ms_out, int64_t *mma_out) 
     return XC_OK;
 }
 
-xc_status xc_last_far_evals(xc_handle *h, int64_t *far_evals_out) {
+xc_status xc_count_far_evals(xc_handle *h, const xc_condition *conds, size_t n_cond, const xc_grid *grid,
+                             const xc_opts *opts, int64_t *count_out, void *stream) {
     xc_status st = check_handle(h);
     if (st) return st;
-    if (!far_evals_out) { set_error("NULL out"); return XC_EINVAL; }
-    *far_evals_out = h->tc_far_evals;
-    return XC_OK;
+    if ((st = check_grid(grid)) || (st = check_opts(opts)) || (st = check_conds(conds, n_cond, h))) return st;
+    if (!count_out) { set_error("NULL out"); return XC_EINVAL; }
+    if (n_cond > 4096) { set_error("at most 4096 conditions per call"); return XC_EINVAL; }
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    *count_out = 0;
+    if (h->n_lines == 0 || n_cond == 0 || grid->n == 0 || opts->precision != XC_FP32) return XC_OK;
+    CondDev *dc = nullptr;
+    if ((st = resolve_conds(h, conds, n_cond, s, &dc))) return st;
+    BatchedArgs a;
+    a.L = lines_of(h);
+    a.n_lines = h->n_lines;
+    a.conds_dev = dc;
+    a.conds_host = conds;
+    a.n_cond = (int)n_cond;
+    a.grid = *grid;
+    a.opts = *opts;
+    a.stream = s;
+    return batched_count_far(&h->batched, a, count_out);
 }
 
 xc_status xc_set_tile_shape(xc_handle *h, int R, int CG) {

@@ -1171,7 +1171,7 @@ constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * TC_BT * TC_BTILE * sizeof(floa
 constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);           // compensated FP32 sums
 constexpr size_t TC_SMEM = 100 * 1024;    // B + sums + barriers; sized so that 2 CTAs (2 x 256 TMEM
                                           // columns) and never 3 share an SM
-static_assert(TC_SMEM_B + TC_SMEM_ACC + 128 + 4 * TC_L * 16 + 2 * TC_L * 4 + 8 <= TC_SMEM, "far-wing kernel shared memory");
+static_assert(TC_SMEM_B + TC_SMEM_ACC + 128 + 4 * TC_L * 16 + 2 * TC_L * 4 + 12 <= TC_SMEM, "far-wing kernel shared memory");
 
 // a chunk line with a cut covering the whole super-block [t0, t0 + TC_T) and its centre
 // at least one step outside it: no range test and no guard against u < 1 needed
@@ -1195,7 +1195,6 @@ struct TcParams {
     const unsigned *blk_lo, *blk_hi;   // per TC_T-point super-block: line range
     int *counter;
     int *status;                       // set to 1 if a wait ran out
-    unsigned long long *far_evals;     // (line, point, condition) evaluations covered, or nullptr
     int n_tiles, n_groups, n_cond;
     int64_t n_pts;
     float h, inv_h;
@@ -1252,12 +1251,14 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     float4 *sPhys = sGeo + 2 * TC_L;                                                     // [2][TC_L]
     float *sNT = reinterpret_cast<float *>(sPhys + 2 * TC_L);                            // [2][TC_L]
     int *sFast = reinterpret_cast<int *>(sNT + 2 * TC_L);                                // [2]
+    volatile int *sAbort = sFast + 2;                                                    // a wait ran out
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int blkh = tid / TC_M;                 // this thread's block within the CTA
     if (tid == 0) {
         for (int i = 0; i < 2 * TC_BLK; ++i) tc::mbar_init(&mbar[i], 1);
         tc::mbar_init_fence();
+        *sAbort = 0;
     }
     if (warp == 0) tc::tmem_alloc(sTmem, TC_COLS);
     for (int c = 0; c < TC_N; ++c) sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
@@ -1280,9 +1281,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     const uint64_t desc_b0 = tc::smem_desc(sB_addr + (uint32_t)(blkh * 2 * TC_BT * TC_BTILE * 4), 128u, 256u);
 
     uint32_t uses[2] = {0u, 0u};   // commits per buffer (each block's barrier of it) so far
-    unsigned long long n_far = 0;  // this thread's far (line, point, condition) evaluations
-    // `ok` is per thread (its own bounded waits); `stop` is the CTA's agreement, taken at a
-    // barrier, that some wait ran out: from then on no MMA is issued and no output written
+    // `ok` is per thread (its own bounded waits).  A thread whose wait ran out raises the
+    // shared flag before the next barrier; after that barrier every thread sees it (`stop`):
+    // no further MMA is issued and no further output is written.
     bool ok = true, stop = false;
     // The (line, condition) pair whose coefficients this thread computes each chunk, chosen
     // so that a warp's B entries of one term fill one 8 x 4 core matrix (32 consecutive
@@ -1351,14 +1352,12 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             {
                 float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                 float p3 = 0.f;
-                float na = 0.f, ka = 0.f, kb = -1.f;
+                float na = 0.f;
                 bool live = false;
                 if (l0 + lB < nl && cc < p.n_cond) {
                     const float4 g = cGeo[lB];
                     live = g.w >= g.z;   // non-empty cut range
                     na = g.x;
-                    ka = g.z;
-                    kb = g.w;
                     const size_t lg = (size_t)lo + (size_t)(l0 + lB);
                     const float ga_lc =
                         (EXT && p.gamma_lc) ? p.gamma_lc[lg * (size_t)p.gamma_stride + cpr.row] : -1.f;
@@ -1376,8 +1375,6 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     // so the differences are exact and the test is the same
                     const float b0 = (float)(t0 + hb * TC_M);
                     const bool far = live && ((na - (b0 + (float)(TC_M - 1)) > S.w) || (b0 - na > S.w));
-                    // the block's points inside the line's cut (exact integers in float)
-                    if (far) n_far += (unsigned long long)fmaxf(0.f, fminf(b0 + (float)(TC_M - 1), kb) - fmaxf(b0, ka) + 1.f);
                     float *bt = sB + (size_t)(hb * 2 + b) * TC_BT * TC_BTILE + bix;
                     bt[0 * TC_BTILE] = far ? p0h : 0.f;
                     bt[1 * TC_BTILE] = far ? p0l : 0.f;
@@ -1436,7 +1433,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
-            if (__syncthreads_or(!ok)) {   // a buffer may still be in use: issue nothing more
+            if (!ok) *sAbort = 1;
+            __syncthreads();
+            if (*sAbort) {   // a buffer may still be in use: issue nothing more
                 stop = true;
                 break;
             }
@@ -1476,29 +1475,26 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                 in_fold = 0;
             }
         }
-        // the last chunk's accumulator waits decide whether these sums are complete
-        if (stop || __syncthreads_or(!ok)) {
-            stop = true;
-            break;
-        }
-        // ---- the super-block's far-wing sums: first writer of these outputs
+        if (stop) break;
+        // ---- the super-block's far-wing sums: first writer of these outputs.  A thread's
+        // sums come from its own block's MMAs only, all covered by its own last wait: it
+        // writes them only if every wait of its own succeeded
         const int64_t k = (int64_t)t0 + tid;
         for (int c = 0; c < TC_N; ++c) {
             const int c2 = grp * TC_N + c;
-            if (k < p.n_pts && c2 < p.n_cond)
+            if (ok && k < p.n_pts && c2 < p.n_cond)
                 p.sigma[(size_t)p.cp[c2].row * (size_t)p.n_pts + (size_t)k] =
                     ((double)sSum[c * TC_T + tid] - (double)sCmp[c * TC_T + tid]) * p.cp[c2].inv_scale;
             sSum[c * TC_T + tid] = sCmp[c * TC_T + tid] = 0.f;
         }
     }
-    if (p.far_evals) {
-        for (int o = 16; o > 0; o >>= 1) n_far += __shfl_xor_sync(0xffffffffu, n_far, o);
-        if (lane == 0 && n_far) atomicAdd(p.far_evals, n_far);
-    }
-    if (stop) {
-        // after a wait ran out: before the tensor memory is released, wait (bounded again)
-        // for the last commit of each block's buffers, which covers every MMA issued before
-        // it; the status flag tells the host that this launch's output is not valid
+    if (!ok) *sAbort = 1;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (*sAbort) {
+        // a wait ran out: before the tensor memory is released, wait (bounded again) for the
+        // last commit of each block's buffers, which covers every MMA issued before it; the
+        // status flag tells the host that this launch's output is not valid
 #pragma unroll
         for (int b = 0; b < 2; ++b)
             if (uses[b] > 0u)
@@ -1506,10 +1502,51 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                 for (int hb = 0; hb < TC_BLK; ++hb)
                     (void)tc::mbar_wait(&mbar[hb * 2 + b], (uses[b] - 1u) & 1u, TC_WAIT_LIMIT);
         if (tid == 0) atomicExch(p.status, 1);
+        tc::fence_before_sync();
+        __syncthreads();
     }
-    tc::fence_before_sync();
-    __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, TC_COLS);
+}
+
+// The far-wing kernel's algorithmic work: for every (line, condition), the grid points
+// inside the line's cut that lie in a 128-point block far from it -- the same test on the
+// same rounded values as k_far_tc (the radius D4 from the line's widths, the integer line
+// position n): a block [b0, b0 + 127] is far when n - (b0 + 127) > D4 or b0 - n > D4.  The
+// far blocks are those wholly below n - D4 or above n + D4, so the count is two interval
+// lengths per pair.  Run on request (xc_count_far_evals), not inside the sweep.
+__global__ void k_far_count(const float4 *__restrict__ geo, const float4 *__restrict__ phys,
+                            const float *__restrict__ n_T, const CParam *__restrict__ cp, int nc,
+                            const float *gamma_lc, int gamma_stride, size_t n, float inv_h,
+                            unsigned long long *count) {
+    unsigned long long acc = 0;
+    const size_t total = n * (size_t)nc;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t l = i / (size_t)nc;
+        const CParam c = cp[i % (size_t)nc];
+        const float4 g = geo[l];
+        if (!(g.w >= g.z)) continue;   // empty cut range
+        const float4 ph = phys[l];
+        float ah, gh;
+        if (gamma_lc) {
+            ah = __fmul_rn(c.acoef * ph.x, inv_h);
+            gh = __fmul_rn(gamma_lc[l * (size_t)gamma_stride + c.row], inv_h);
+        } else {
+            line_widths(ph.x, ph.w, n_T[l], c, inv_h, &ah, &gh);
+        }
+        const double D = (double)w4_zone(ah, gh).D4;
+        const double na = (double)g.x, ka = (double)g.z, kb = (double)g.w;
+        double cnt = 0.0;
+        const double X = na - D - (double)(TC_M - 1);   // far-left: TC_M j < X
+        if (X > 0.0) {
+            const double KL = (double)TC_M * (ceil(X / TC_M) - 1.0) + (double)(TC_M - 1);
+            cnt += fmax(0.0, fmin(kb, KL) - ka + 1.0);
+        }
+        const double KR = (double)TC_M * (floor((na + D) / TC_M) + 1.0);   // far-right: TC_M j > n + D
+        cnt += fmax(0.0, kb - fmax(ka, KR) + 1.0);
+        acc += (unsigned long long)cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(count, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1796,7 +1833,6 @@ struct Plan {
     int n_blk = 0, n_tc_tiles = 0;              // TC_T-point super-blocks, (super-block, group) tiles
     unsigned *blk_lo = nullptr, *blk_hi = nullptr;
     int *tc_counter = nullptr, *tc_status = nullptr;
-    unsigned long long *tc_far_evals = nullptr;
     float4 *tc_geo = nullptr, *tc_phys = nullptr;
     uint32_t *keep = nullptr;                   // intensity-threshold decisions (with a threshold)
     float *gamma_lc = nullptr;                  // widths per (line, condition) (broadener mixture)
@@ -1867,7 +1903,6 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->blk_hi = (unsigned *)(b + o_bhi);
         pl->tc_counter = (int *)(b + o_tcc);
         pl->tc_status = pl->tc_counter + 1;
-        pl->tc_far_evals = reinterpret_cast<unsigned long long *>(pl->tc_counter + 2);   // 8-byte aligned
         st->tc_blk_lo = pl->blk_lo;
         st->tc_blk_hi = pl->blk_hi;
         st->tc_n_blk = pl->n_blk;
@@ -1875,7 +1910,6 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
         pl->tc_geo = (float4 *)(b + o_geo);
         pl->tc_phys = (float4 *)(b + o_phys);
         st->tc_status = pl->tc_status;
-        st->tc_far_evals = pl->tc_far_evals;
     }
     return XC_OK;
 }
@@ -1965,7 +1999,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         // far wings on the tensor cores: first writer of every output of the sweep
         k_win_ranges32<<<(pl.n_blk + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
                                                               TC_T, a.opts.cutoff, pl.n_blk, pl.blk_lo, pl.blk_hi);
-        BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 4 * sizeof(int), s));   // counter, status, far-eval count
+        BT_TRY(cudaMemsetAsync(pl.tc_counter, 0, 2 * sizeof(int), s));
         TcParams tp;
         tp.geo = pl.tc_geo;
         tp.phys = pl.tc_phys;
@@ -1979,7 +2013,6 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         tp.blk_hi = pl.blk_hi;
         tp.counter = pl.tc_counter;
         tp.status = pl.tc_status;
-        tp.far_evals = pl.tc_far_evals;
         tp.n_tiles = pl.n_tc_tiles;
         tp.n_groups = (nc + TC_N - 1) / TC_N;
         tp.n_cond = nc;
@@ -2268,7 +2301,6 @@ xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches)
     // the status word lives in the plan's scratch, which a later plan may reallocate:
     // it is valid only for the run that set it
     st->tc_status = nullptr;
-    st->tc_far_evals = nullptr;
     st->tc_blk_lo = st->tc_blk_hi = nullptr;
     st->tc_n_blk = st->tc_groups = 0;
     if (a.n_lines == 0 || a.n_cond == 0 || a.grid.n == 0) return XC_OK;
@@ -2368,14 +2400,40 @@ int64_t batched_tc_mma_count(BatchedState *st) {
     return chunks * st->tc_groups * TC_BLK * 8;
 }
 
-int64_t batched_tc_far_evals(BatchedState *st) {
-    if (!st->tc_far_evals) return 0;
-    unsigned long long v = 0;
-    if (cudaMemcpy(&v, st->tc_far_evals, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        return -1;
+xc_status batched_count_far(BatchedState *st, const BatchedArgs &a, int64_t *count) {
+    *count = 0;
+    const int nc = a.n_cond;
+    if (a.n_lines == 0 || nc == 0 || a.grid.n == 0 || !use_tc(a, nc)) return XC_OK;
+    const Variant *v = nullptr;
+    for (int i = 0; i < kNumVariants && !v; ++i)
+        if (kVariants[i].profile == XC_VOIGT_W4 && kVariants[i].R == 4) v = &kVariants[i];
+    Plan pl;
+    xc_status s = make_plan(st, a, v, nc, &pl, true);
+    if (s) return s;
+    cudaStream_t cs = a.stream;
+    const size_t n = a.n_lines;
+    unsigned gblocks = (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16));
+    BT_TRY(cudaMemsetAsync(pl.gs, 0, sizeof(GeomStats), cs));
+    if (pl.gamma_lc) {
+        BT_TRY(cudaMemsetAsync(pl.gmax, 0, (size_t)nc * 4, cs));
+        BT_TRY(launch_line_gamma(a.L, n, a.conds_dev, nc, pl.gamma_lc, pl.gmax, cs));
     }
-    return (int64_t)v;
+    k_line_geom<<<gblocks, 256, 0, cs>>>(a.L, n, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff, 0.0, nullptr,
+                                         pl.n_abs, pl.f, pl.ka, pl.kb, pl.gs, pl.tc_geo, pl.tc_phys);
+    k_cparams<<<(nc + 63) / 64, 64, 0, cs>>>(a.conds_dev, nc, pl.gs, pl.cp, a.grid.step, a.opts.quantity, pl.gmax,
+                                             4.f, 0);
+    unsigned long long *dcount = reinterpret_cast<unsigned long long *>(pl.tc_counter + 2);   // 8-byte aligned
+    BT_TRY(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), cs));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    k_far_count<<<num_sms(dev) * 8, 256, 0, cs>>>(pl.tc_geo, pl.tc_phys, a.L.n_T, pl.cp, nc, pl.gamma_lc, nc, n,
+                                                (float)(1.0 / a.grid.step), dcount);
+    BT_TRY(cudaGetLastError());
+    unsigned long long hc = 0;
+    BT_TRY(cudaMemcpyAsync(&hc, dcount, sizeof(hc), cudaMemcpyDeviceToHost, cs));
+    BT_TRY(cudaStreamSynchronize(cs));
+    *count = (int64_t)hc;
+    return XC_OK;
 }
 
 void batched_invalidate(BatchedState *st) {

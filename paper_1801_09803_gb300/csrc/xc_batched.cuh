@@ -71,7 +71,6 @@ struct BatchedState {
     std::map<std::string, std::string> tune_log; // shape key -> candidate predictions
     std::string last_tuning;                     // description of the last batched configuration
     int *tc_status = nullptr;                    // device word: a tensor-core wait ran out
-    unsigned long long *tc_far_evals = nullptr;  // device count: far-wing evaluations of the last run
     // the last run's tensor-core work: super-block line ranges (device) and shape
     const unsigned *tc_blk_lo = nullptr, *tc_blk_hi = nullptr;
     int tc_n_blk = 0, tc_groups = 0;
@@ -86,9 +85,9 @@ xc_status batched_check(BatchedState *st);
 // after the stream has synchronised: tcgen05.mma instructions the last run's tensor-core
 // kernel issued (0 if it did not run), from its super-block line ranges
 int64_t batched_tc_mma_count(BatchedState *st);
-// after the stream has synchronised: (line, grid point, condition) evaluations the last
-// run's tensor-core kernel covered (0 if it did not run, -1 if the count could not be read)
-int64_t batched_tc_far_evals(BatchedState *st);
+// (line, grid point, condition) evaluations the tensor-core far-wing kernel takes in a
+// batched call with these arguments (0 when that kernel would not run); synchronises
+xc_status batched_count_far(BatchedState *st, const BatchedArgs &a, int64_t *count);
 void batched_invalidate(BatchedState *st);
 void batched_release(BatchedState *st);
 

@@ -219,18 +219,20 @@ def test_tensor_core_partition_on_offset_grid(eng, xc, oracle_lib):
     try:
         tc = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0))
         far_ms, main_ms, cz_ms, mma = eng.sweep_kernels()
-        n_far = eng.far_evals()
         cu = eng.cross_section_batched(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0, tensor_cores=False))
         far2, main2, cz2, mma2 = eng.sweep_kernels()
-        n_far2 = eng.far_evals()
     finally:
         eng.set_timing(False)
     assert mma > 0 and far_ms > 0 and main_ms > 0 and cz_ms > 0
     assert mma2 == 0 and far2 < 0 and main2 > 0
-    # the far-wing kernel's own count of its evaluations: part of the algorithmic count
-    total = eng.count_evals(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0))
+    # the far-wing kernel's evaluations (its own test, counted separately): part of the
+    # algorithmic count, and none without the tensor cores
+    o = xc.make_opts("voigt_w4", "fp32", 10.0)
+    total = eng.count_evals(cx, grid, o)
+    n_far = eng.count_far_evals(cx, grid, o)
     print(f"far-wing evaluations {n_far} of {total} ({n_far / total:.3f})")
-    assert 0 < n_far <= total and n_far2 == 0
+    assert 0 < n_far <= total
+    assert eng.count_far_evals(cx, grid, xc.make_opts("voigt_w4", "fp32", 10.0, tensor_cores=False)) == 0
     m = cu > 1e-6 * cu.max(axis=1, keepdims=True)
     diff = float(np.max(np.abs(tc[m] - cu[m]) / cu[m]))
     full = np.where(m, np.abs(tc - cu) / np.where(m, cu, 1.0), 0.0)
