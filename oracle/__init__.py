@@ -146,6 +146,10 @@ def lib():
                                                        C.c_longlong, C.POINTER(Opts), vp,
                                                        vp, vp, vp, vp, vp, vp]
         L.xo_cross_section_vjp.restype = i
+        L.xo_cross_section_vjp_broad.argtypes = [vp] * 6 + [C.c_size_t, vp, i, C.POINTER(Condition), i, d, d,
+                                                             C.c_longlong, C.POINTER(Opts), vp,
+                                                             vp, vp, vp, vp, vp, vp]
+        L.xo_cross_section_vjp_broad.restype = i
         _lib = L
     return _lib
 
@@ -361,3 +365,30 @@ def cross_section_vjp(lines, conds: Sequence[Condition], nu_A, step, n_pts, opts
         raise RuntimeError(f"xo_cross_section_vjp failed: {rc}")
     return {"dT": dT, "dP": dP, "d_gamma_scale": float(dgs[0]), "d_n_shift": float(dns[0]),
             "d_gamma_ref_line": dgl, "d_n_line": dnl}
+
+
+def cross_section_vjp_broad(lines, j_up, broadeners, conds: Sequence[Condition], nu_A, step, n_pts, opts: Opts,
+                            grad_sigma: np.ndarray):
+    """The adjoint with every line's Lorentz HWHM from the broadener mixture: dT, dP per
+    condition, d_gamma_scale, d_n_shift, and per broadener d_gamma0 (dL/d of a scale on all
+    its gamma_0 values, at 1) and d_n (dL/d of a shift of all its n values, at 0)."""
+    nu = np.ascontiguousarray(lines["nu"], np.float64)
+    el = np.ascontiguousarray(lines["elower"], np.float32)
+    A = np.ascontiguousarray(lines["A"], np.float32)
+    jl = np.ascontiguousarray(lines["j_lo"], np.int16)
+    ju = np.ascontiguousarray(j_up, np.int16)
+    g = np.ascontiguousarray(lines["g_up"], np.int16)
+    nc, nb = len(conds), len(broadeners)
+    carr = (Condition * nc)(*conds)
+    arr = _broad_array(broadeners)
+    gs = np.ascontiguousarray(grad_sigma, np.float64).reshape(nc, int(n_pts))
+    dT, dP, dgs, dns = np.zeros(nc), np.zeros(nc), np.zeros(1), np.zeros(1)
+    dg0, dnb = np.zeros(nb), np.zeros(nb)
+    rc = lib().xo_cross_section_vjp_broad(_p(nu), _p(el), _p(A), _p(jl), _p(ju), _p(g), len(nu),
+                                          C.cast(arr, C.c_void_p), nb, carr, nc, float(nu_A), float(step),
+                                          int(n_pts), C.byref(opts), _p(gs), _p(dT), _p(dP), _p(dgs), _p(dns),
+                                          _p(dg0), _p(dnb))
+    if rc != 0:
+        raise RuntimeError(f"xo_cross_section_vjp_broad failed: {rc}")
+    return {"dT": dT, "dP": dP, "d_gamma_scale": float(dgs[0]), "d_n_shift": float(dns[0]),
+            "d_gamma0_broad": dg0, "d_n_broad": dnb}

@@ -734,14 +734,18 @@ long long xo_count_evals(const double *nu, const float *gamma_ref, const float *
 /*   dL/dT_c, dL/dP_c                         per condition               */
 /*   dL/d(gamma_scale), dL/d(n_shift)         global                      */
 /*   dL/d(gamma_ref_l), dL/d(n_l)             per line (summed over c)    */
+/* and, with a mixture of broadeners (gamma = sum_i gamma_i, each term of   */
+/* the form of Eq. e:gamma_L), per broadener i:                            */
+/*   dL/d(scale of all its gamma_0 values, at 1):   dgamma/d = gamma_i      */
+/*   dL/d(shift of all its n values, at 0):  dgamma/d = gamma_i ln(T_ref/T) */
 /* The cutoff is held fixed (its boundary terms are measure-zero).         */
 /* ---------------------------------------------------------------------- */
-int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, const float *gamma_ref,
-                         const float *n_T, const int16_t *g_up, size_t n_lines,
-                         const xo_condition *conds, int n_cond, double nu_A, double h, long long n_pts,
-                         const xo_opts *o, const double *grad_sigma,
-                         double *dT, double *dP, double *d_gscale, double *d_nshift,
-                         double *d_gref_line, double *d_n_line)
+static int cross_section_vjp_impl(const double *nu, const float *elower, const float *A, const xo_gsrc *gsrc,
+                                  const int16_t *g_up, size_t n_lines,
+                                  const xo_condition *conds, int n_cond, double nu_A, double h, long long n_pts,
+                                  const xo_opts *o, const double *grad_sigma,
+                                  double *dT, double *dP, double *d_gscale, double *d_nshift,
+                                  double *d_gref_line, double *d_n_line, double *d_g0_broad, double *d_n_broad)
 {
     const double c2 = xo_c2();
     double xg[200], wg[200];
@@ -751,9 +755,13 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
         ngh = o->n_gh;
         if (xo_gauss_hermite(ngh, xg, wg) != 0) return -1;
     }
+    const int nb = gsrc->nb;
+    if (nb > 8) return -1;
     double gs = 0.0, gn = 0.0;
     if (d_gref_line) memset(d_gref_line, 0, n_lines * sizeof(double));
     if (d_n_line) memset(d_n_line, 0, n_lines * sizeof(double));
+    if (d_g0_broad) memset(d_g0_broad, 0, (size_t)nb * sizeof(double));
+    if (d_n_broad) memset(d_n_broad, 0, (size_t)nb * sizeof(double));
     for (int c = 0; c < n_cond; ++c) {
         const xo_condition *cd = &conds[c];
         const double *g = grad_sigma + (size_t)c * (size_t)n_pts;
@@ -763,7 +771,24 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
             double nul = nu[l];
             double Ifi = xo_intensity(nul, elower[l], A[l], g_up[l], cd);
             double al = xo_alpha_doppler(nul, cd);
-            double ga = xo_gamma_lorentz(gamma_ref[l], n_T[l], cd);
+            /* Lorentz HWHM and dgamma/dT: the line's own (gamma_ref, n_T), or the sum of the
+             * mixture's terms gamma_i = s rho_i gamma_0,i (T_ref/T)^(n_i + n_shift) P/P_ref */
+            double ga, dgdT, gi[8];
+            if (nb > 0) {
+                ga = 0.0;
+                dgdT = 0.0;
+                for (int b = 0; b < nb; ++b) {
+                    double g0, nn;
+                    broad_lookup(&gsrc->b[b], gsrc->j_lo[l], gsrc->j_up ? gsrc->j_up[l] : 0, &g0, &nn);
+                    gi[b] = cd->gamma_scale * gsrc->b[b].fraction * g0 * pow(cd->T_ref / T, nn + cd->n_shift)
+                            * (cd->P / cd->P_ref);
+                    ga += gi[b];
+                    dgdT += -(nn + cd->n_shift) * gi[b] / T;
+                }
+            } else {
+                ga = xo_gamma_lorentz(gsrc->gamma_ref[l], gsrc->n_T[l], cd);
+                dgdT = -(gsrc->n_T[l] + cd->n_shift) * ga / T;
+            }
             double cut = line_cut(o, al, ga);
             long long k0 = grid_floor_index(nul - cut, nu_A, h) - 1;
             long long k1 = grid_floor_index(nul + cut, nu_A, h) + 1;
@@ -784,15 +809,20 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
                           - cd->dQdT / cd->Q;
             double dIdT = Ifi * dlnI;
             double dadT = al / (2.0 * T);
-            double ntot = n_T[l] + cd->n_shift;
-            double dgdT = -ntot * ga / T;
             sT += SI * dIdT + Sa * dadT + Sg * dgdT;
             sP += Sg * ga / cd->P;
             gs += Sg * ga / cd->gamma_scale;
-            double dgdn = ga * log(cd->T_ref / T);
-            gn += Sg * dgdn;
-            if (d_gref_line) d_gref_line[l] += Sg * ga / gamma_ref[l];
-            if (d_n_line) d_n_line[l] += Sg * dgdn;
+            double lnTr = log(cd->T_ref / T);
+            gn += Sg * ga * lnTr;
+            if (nb > 0) {
+                for (int b = 0; b < nb; ++b) {
+                    if (d_g0_broad) d_g0_broad[b] += Sg * gi[b];
+                    if (d_n_broad) d_n_broad[b] += Sg * gi[b] * lnTr;
+                }
+            } else {
+                if (d_gref_line) d_gref_line[l] += Sg * ga / gsrc->gamma_ref[l];
+                if (d_n_line) d_n_line[l] += Sg * ga * lnTr;
+            }
         }
         dT[c] = sT;
         dP[c] = sP;
@@ -800,4 +830,31 @@ int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, 
     if (d_gscale) *d_gscale = gs;
     if (d_nshift) *d_nshift = gn;
     return 0;
+}
+
+int xo_cross_section_vjp(const double *nu, const float *elower, const float *A, const float *gamma_ref,
+                         const float *n_T, const int16_t *g_up, size_t n_lines,
+                         const xo_condition *conds, int n_cond, double nu_A, double h, long long n_pts,
+                         const xo_opts *o, const double *grad_sigma,
+                         double *dT, double *dP, double *d_gscale, double *d_nshift,
+                         double *d_gref_line, double *d_n_line)
+{
+    xo_gsrc g = {gamma_ref, n_T, NULL, NULL, NULL, 0};
+    return cross_section_vjp_impl(nu, elower, A, &g, g_up, n_lines, conds, n_cond, nu_A, h, n_pts, o, grad_sigma,
+                                  dT, dP, d_gscale, d_nshift, d_gref_line, d_n_line, NULL, NULL);
+}
+
+/* the adjoint with every line's Lorentz HWHM from a mixture of .broad broadeners; per
+ * broadener, dL/d(scale of its gamma_0 values) and dL/d(shift of its n values) */
+int xo_cross_section_vjp_broad(const double *nu, const float *elower, const float *A, const int16_t *j_lo,
+                               const int16_t *j_up, const int16_t *g_up, size_t n_lines, const xo_broadener *b,
+                               int nb, const xo_condition *conds, int n_cond, double nu_A, double h,
+                               long long n_pts, const xo_opts *o, const double *grad_sigma,
+                               double *dT, double *dP, double *d_gscale, double *d_nshift,
+                               double *d_g0_broad, double *d_n_broad)
+{
+    if (nb < 1) return -1;
+    xo_gsrc g = {NULL, NULL, j_lo, j_up, b, nb};
+    return cross_section_vjp_impl(nu, elower, A, &g, g_up, n_lines, conds, n_cond, nu_A, h, n_pts, o, grad_sigma,
+                                  dT, dP, d_gscale, d_nshift, NULL, NULL, d_g0_broad, d_n_broad);
 }

@@ -290,6 +290,60 @@ def test_cross_section_with_a0_broadening_equals_per_line_widths(oracle_lib):
     assert np.allclose(a, ref, rtol=1e-14, atol=0) and ref.max() > 0
 
 
+@pytest.mark.parametrize("profile", ["voigt_w4", "lorentz", "voigt_gh_binned"])
+def test_vjp_with_broadener_mixture_matches_central_differences(oracle_lib, profile):
+    """Adjoint under a mixture of broadeners (an a0 table, an a1 table, a constant): dL/dT,
+    dL/dP, dL/d(gamma_scale), dL/d(n_shift), and per broadener dL/d(scale of its gamma_0
+    values) and dL/d(shift of its n values), each against central differences of the
+    forward with that broadener's table rows and defaults perturbed; the per-broadener
+    gradients also sum to the global ones (the two identities alone would not catch a
+    gradient booked to the wrong broadener)."""
+    L = xs.gen_lines(35, 0, 8, 1000.0, 1000.5)
+    j_up = (L["g_up"].astype(np.int32) - 1) // 2
+    E, gst = xs.gen_states(35, 400)
+    nu_A, h, N, cut = 999.0, 0.01, 251, 1.0
+    o = oracle_lib.make_opts(profile, cut, n_gh=10)
+    gs = np.random.default_rng(1).standard_normal(N)
+    a0 = {j: (0.07 - 0.001 * j, 0.7 - 0.01 * j) for j in range(0, 50, 3)}
+    a1 = {(int(jl), int(ju)): (0.05 + 0.002 * (k % 5), 0.55 + 0.03 * (k % 4))
+          for k, (jl, ju) in enumerate(zip(L["j_lo"][::2], j_up[::2]))}
+    spec = [("a0", 0.5, 0.06, 0.6, a0), ("a1", 0.3, 0.04, 0.5, a1), ("constant", 0.2, 0.03, 0.75, None)]
+
+    def mk(i_scale=None, s=1.0, i_shift=None, d=0.0):
+        bs = []
+        for i, (kind, rho, g0, n, tab) in enumerate(spec):
+            f = s if i == i_scale else 1.0
+            dn = d if i == i_shift else 0.0
+            t2 = None if tab is None else {k: (v[0] * f, v[1] + dn) for k, v in tab.items()}
+            bs.append(oracle_lib.make_broadener(kind, rho, g0 * f, n + dn, t2))
+        return bs
+
+    T, P = 1100.0, 0.6
+
+    def loss(T=T, P=P, gsc=1.0, nsh=0.0, **kw):
+        Q, dQ = oracle_lib.partition_function(E, gst, T)
+        c = oracle_lib.make_condition(T, P, Q, dQ, gamma_scale=gsc, n_shift=nsh)
+        return float(np.dot(gs, oracle_lib.cross_section_broad(L, j_up, mk(**kw), c, nu_A, h, N, o, nthreads=1)))
+
+    Q, dQ = oracle_lib.partition_function(E, gst, T)
+    c = oracle_lib.make_condition(T, P, Q, dQ)
+    g = oracle_lib.cross_section_vjp_broad(L, j_up, mk(), [c], nu_A, h, N, o, gs)
+    e = 1e-5
+    tol = dict(rel=2e-5, abs=0)
+    assert g["dT"][0] == pytest.approx((loss(T=T * (1 + e)) - loss(T=T * (1 - e))) / (2 * e * T), **tol)
+    assert g["dP"][0] == pytest.approx((loss(P=P * (1 + e)) - loss(P=P * (1 - e))) / (2 * e * P), **tol)
+    assert g["d_gamma_scale"] == pytest.approx((loss(gsc=1 + e) - loss(gsc=1 - e)) / (2 * e), **tol)
+    assert g["d_n_shift"] == pytest.approx((loss(nsh=e) - loss(nsh=-e)) / (2 * e), **tol)
+    for i in range(len(spec)):
+        fd_g0 = (loss(i_scale=i, s=1 + e) - loss(i_scale=i, s=1 - e)) / (2 * e)
+        fd_n = (loss(i_shift=i, d=e) - loss(i_shift=i, d=-e)) / (2 * e)
+        assert g["d_gamma0_broad"][i] == pytest.approx(fd_g0, **tol), (i, g["d_gamma0_broad"][i], fd_g0)
+        assert g["d_n_broad"][i] == pytest.approx(fd_n, **tol), (i, g["d_n_broad"][i], fd_n)
+        assert abs(g["d_gamma0_broad"][i]) > 1e-3 * abs(g["d_gamma_scale"])   # every broadener matters here
+    assert g["d_gamma0_broad"].sum() == pytest.approx(g["d_gamma_scale"], rel=1e-12, abs=0)
+    assert g["d_n_broad"].sum() == pytest.approx(g["d_n_shift"], rel=1e-12, abs=0)
+
+
 # --------------------------------------------- widths, Eqs. (e:alphaD), (e:gamma_L)
 def test_doppler_hwhm_textbook_constant(oracle_lib):
     # alpha_D = 3.581e-7 * nu * sqrt(T / M[g/mol])  (the usual practical form)
