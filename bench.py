@@ -331,6 +331,60 @@ def secondary_measurements(xc, torch, dev):
     return out
 
 
+def c5_measurement(xc, torch, dev):
+    """The maximum-size workload: 1e9 lines (nu in (0, 20000], 2000 K, 1 bar), grid 0..20000
+    step 0.01 (2 000 001 points), cut 25, generated on the device by the seeded generator
+    and loaded (device radix sort) through the C ABI.  FP32 (the batched kernel) is timed
+    over the whole grid; FP32 and the plain FP64 kernel are timed on the same 100 cm^-1
+    slice of the grid (10000..10100, every line loaded: the same line density), which
+    gives the FP32 / FP64 ratio without a 7-minute FP64 run; the two are compared there
+    (max relative difference above 1e-6 of the peak, and integrated band).  Device memory
+    is the free-memory drop while the lines, the sorted copy, the sort scratch and the
+    sweep's scratch are all held."""
+    W = xs.WORKLOADS["C5"]
+    free0, total = torch.cuda.mem_get_info(dev)
+    if free0 < 140e9:
+        return {"skipped": f"needs about 140 GB of free device memory ({free0 / 1e9:.0f} GB free)"}
+    t0 = time.time()
+    dl = xs.gen_lines_torch(W.seed, 0, W.n_lines, W.nu_lo, W.nu_hi, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+    E, g = xs.gen_states(W.seed, W.n_states)
+    eng = xc.Engine(dev.index or 0)
+    eng.set_timing(True)
+    eng.load_lines(dl)
+    tl = eng.timings()
+    eng.set_states(E, g)
+    c = xs.conditions_for(W)[0]
+    cond = [xc.make_condition(c["T"], c["P"], mass_da=W.mass_da)]
+    out = {"lines": W.n_lines, "generation_s": round(t_gen, 1), "sort_ms": tl["sort"], "gather_ms": tl["gather"]}
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    o32 = xc.make_opts("voigt_w4", "fp32", W.cutoff)
+    o64 = xc.make_opts("voigt_w4", "fp64", W.cutoff)
+    sig = torch.empty((1, W.n_points), dtype=torch.float64, device=dev)
+    ev = eng.count_evals(cond, grid, o32)
+    ms = _timed(torch, lambda: eng.cross_section_batched(cond, grid, o32, sig))
+    out["fp32_full_grid"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+    out["device_memory_gb"] = (free0 - torch.cuda.mem_get_info(dev)[0]) / 1e9
+    slice_grid = xc.make_grid(10000.0, W.step, 10001)
+    s32 = torch.empty((1, slice_grid.n), dtype=torch.float64, device=dev)
+    s64 = torch.empty_like(s32)
+    evs = eng.count_evals(cond, slice_grid, o32)
+    ms32 = _timed(torch, lambda: eng.cross_section_batched(cond, slice_grid, o32, s32))
+    ms64 = _timed(torch, lambda: eng.cross_section_batched(cond, slice_grid, o64, s64))
+    a, b = s32[0].cpu().numpy(), s64[0].cpu().numpy()
+    m = b > 1e-6 * b.max()
+    out["slice_10000_10100"] = {
+        "evals": evs, "fp32_ms": ms32, "fp64_ms": ms64, "fp32_evals_per_s": evs / (ms32 / 1e3),
+        "fp64_plain_evals_per_s": evs / (ms64 / 1e3), "fp32_over_fp64": ms64 / ms32,
+        "fp32_vs_fp64_max_rel": float(np.max(np.abs(a[m] - b[m]) / b[m])),
+        "fp32_vs_fp64_band": float(abs(a.sum() - b.sum()) / b.sum())}
+    eng.close()
+    del dl, sig, s32, s64
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_xc(args, dist, rank, world, local):
     import torch
     import paper_1801_09803_gb300 as xc
@@ -441,6 +495,7 @@ def run_xc(args, dist, rank, world, local):
     extras = None
     if not args.no_extras and rank == 0:
         extras = secondary_measurements(xc, torch, dev)
+        extras["C5"] = c5_measurement(xc, torch, dev)
 
     if rank != 0:
         return

@@ -219,7 +219,9 @@ typedef struct {
  * may be NULL when no broadener is a1); a line without a row takes gamma0 and n.
  * At most 8 broadeners; duplicate table keys, negative widths or fractions: EINVAL.
  * n_broadeners = 0 returns to the line list's widths, as does the next xc_load_lines.
- * Synchronises `stream`.  The adjoint does not support a mixture (EUNSUPPORTED). */
+ * Synchronises `stream`.  Under a mixture the adjoint returns dT, dP, dgamma_scale and dn_shift
+ * (xc_cross_section_vjp, per-line outputs NULL) and per-broadener gradients
+ * (xc_cross_section_vjp_broadening). */
 xc_status xc_set_broadening(xc_handle *h, const xc_broadener *b, int n_broadeners, const int16_t *j_up, int mem,
                             void *stream);
 
@@ -274,13 +276,31 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
  * all float64 in `mem`.  dT includes dQ/dT through Q (from the states, or the
  * condition's dQdT).  Profiles are recomputed, not stored; the cut is held
  * fixed.  opts->precision selects FP32 (default) or FP64 recomputation; the
- * reductions are FP64 and deterministic.  XC_DOPPLER, XC_LORENTZ, XC_VOIGT_W4
- * only (EUNSUPPORTED otherwise).  Not in the paper: the chain rule of
- * Eqs. (e:int), (e:alphaD), (e:gamma_L) and the profile. */
+ * per-condition and per-line reductions are FP64 and deterministic.  XC_DOPPLER,
+ * XC_LORENTZ, XC_VOIGT_W4 only (EUNSUPPORTED otherwise).  Under a broadener mixture
+ * (xc_set_broadening) the line list's gamma_ref and n_T are not used: d_gamma_ref_line
+ * and d_n_line must then be NULL (EINVAL otherwise).  Not in the paper: the chain rule
+ * of Eqs. (e:int), (e:alphaD), (e:gamma_L) and the profile. */
 xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n_cond,
                                const xc_grid *grid, const xc_opts *opts, const double *grad_sigma,
                                double *dT, double *dP, double *d_gamma_scale, double *d_n_shift,
                                double *d_gamma_ref_line, double *d_n_line, int mem, void *stream);
+
+/* The adjoint under the handle's mixture of broadeners (xc_set_broadening; EINVAL if none
+ * is set): gamma_L = gamma_scale P/P_ref sum_i gamma_i, gamma_i = rho_i gamma_0,i
+ * (T_ref/T)^(n_L,i + n_shift), each term Eq. (e:gamma_L), the sum Sec. "Mixtures of
+ * broadeners".  Besides dT, dP (n_cond each), d_gamma_scale and d_n_shift (scalars, each
+ * nullable) as in xc_cross_section_vjp, per broadener i (in the order given to
+ * xc_set_broadening; n_broadeners entries each, nullable):
+ *   d_gamma0_broad[i]  dL/d(a factor on all of broadener i's gamma_0 values, its table rows
+ *                      and its default, at 1) -- d gamma_L = gamma_i; dL/d rho_i is this / rho_i
+ *   d_n_broad[i]       dL/d(a shift of all its n_L values, at 0) -- d gamma_L = gamma_i ln(T_ref/T)
+ * Summed over broadeners they give gamma_scale dL/d(gamma_scale) and dL/d(n_shift).
+ * All arrays in `mem`; profiles, precisions and errors as xc_cross_section_vjp. */
+xc_status xc_cross_section_vjp_broadening(xc_handle *h, const xc_condition *conds, size_t n_cond,
+                                          const xc_grid *grid, const xc_opts *opts, const double *grad_sigma,
+                                          double *dT, double *dP, double *d_gamma_scale, double *d_n_shift,
+                                          double *d_gamma0_broad, double *d_n_broad, int mem, void *stream);
 
 /* Stage timing: when enabled, the library records CUDA events on the launch
  * stream around its kernels (as event nodes inside its CUDA graphs); xc_last_timings

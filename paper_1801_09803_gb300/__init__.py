@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "xc_get_permutation", "xc_set_states", "xc_partition_function", "xc_line_params", "xc_count_evals",
     "xc_cross_section", "xc_cross_section_batched", "xc_cross_section_vjp", "xc_set_timing", "xc_last_timings",
     "xc_get_tuning", "xc_last_launch_count", "xc_cross_section_batched_static", "xc_set_tile_shape",
-    "xc_last_sweep_kernels", "xc_set_broadening", "xc_count_far_evals",
+    "xc_last_sweep_kernels", "xc_set_broadening", "xc_count_far_evals", "xc_cross_section_vjp_broadening",
 ]
 
 
@@ -122,6 +122,8 @@ def lib(build_if_missing: bool = False):
                                       i, vp], i),
         "xc_cross_section_vjp": ([vp, C.POINTER(XcCondition), st, C.POINTER(XcGrid), C.POINTER(XcOpts), vp,
                                   vp, vp, vp, vp, vp, vp, i, vp], i),
+        "xc_cross_section_vjp_broadening": ([vp, C.POINTER(XcCondition), st, C.POINTER(XcGrid),
+                                             C.POINTER(XcOpts), vp, vp, vp, vp, vp, vp, vp, i, vp], i),
         "xc_set_timing": ([vp, i], i), "xc_last_timings": ([vp, vp], i),
         "xc_last_launch_count": ([vp, C.POINTER(C.c_int64)], i),
         "xc_get_tuning": ([vp, C.c_char_p, st], i),
@@ -373,6 +375,30 @@ class Engine:
                                           P(dP), P(ds), P(dn), P(dgl), P(dnl), mem, _stream_of(grad_sigma)))
         return {"dT": dT, "dP": dP, "d_gamma_scale": ds, "d_n_shift": dn, "d_gamma_ref_line": dgl,
                 "d_n_line": dnl}
+
+    def cross_section_vjp_broadening(self, conds: Sequence[XcCondition], grid: XcGrid, opts: XcOpts, grad_sigma,
+                                     n_broadeners: int):
+        """The adjoint under the handle's broadener mixture: dT, dP, d_gamma_scale, d_n_shift and
+        per broadener d_gamma0_broad (a factor on its gamma_0 values) and d_n_broad (a shift of
+        its n values).  Device outputs for a CUDA grad_sigma, host numpy otherwise."""
+        nc = len(conds)
+        arr = (XcCondition * nc)(*conds)
+        if _is_torch(grad_sigma) and grad_sigma.is_cuda:
+            import torch
+            z = lambda m: torch.zeros(m, dtype=torch.float64, device=grad_sigma.device)
+            mem = XC_MEM_DEVICE
+        else:
+            grad_sigma = np.ascontiguousarray(grad_sigma, np.float64)
+            z = np.zeros
+            mem = XC_MEM_HOST
+        out = {"dT": z(nc), "dP": z(nc), "d_gamma_scale": z(1), "d_n_shift": z(1),
+               "d_gamma0_broad": z(n_broadeners), "d_n_broad": z(n_broadeners)}
+        P = lambda a: _ptr(a)[0]
+        _check(lib().xc_cross_section_vjp_broadening(self._h, arr, nc, C.byref(grid), C.byref(opts), P(grad_sigma),
+                                                     P(out["dT"]), P(out["dP"]), P(out["d_gamma_scale"]),
+                                                     P(out["d_n_shift"]), P(out["d_gamma0_broad"]),
+                                                     P(out["d_n_broad"]), mem, _stream_of(grad_sigma)))
+        return out
 
     # ---------------------------------------------------------------- accounting
     def set_timing(self, on: bool = True):

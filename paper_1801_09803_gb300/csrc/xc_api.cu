@@ -855,10 +855,10 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
     return XC_OK;
 }
 
-xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n_cond, const xc_grid *grid,
-                               const xc_opts *opts, const double *grad_sigma, double *dT, double *dP,
-                               double *d_gamma_scale, double *d_n_shift, double *d_gamma_ref_line,
-                               double *d_n_line, int mem, void *stream) {
+static xc_status vjp_common(xc_handle *h, const xc_condition *conds, size_t n_cond, const xc_grid *grid,
+                            const xc_opts *opts, const double *grad_sigma, double *dT, double *dP,
+                            double *d_gamma_scale, double *d_n_shift, double *d_gamma_ref_line, double *d_n_line,
+                            double *d_gamma0_broad, double *d_n_broad, int mem, void *stream) {
     xc_status st = check_handle(h);
     if (st) return st;
     if ((st = check_grid(grid)) || (st = check_opts(opts)) || (st = check_conds(conds, n_cond, h))) return st;
@@ -870,9 +870,10 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
         set_error("the adjoint supports absorption without an intensity threshold");
         return XC_EUNSUPPORTED;
     }
-    if (h->n_broad > 0) {
-        set_error("the adjoint does not support a broadener mixture (xc_set_broadening)");
-        return XC_EUNSUPPORTED;
+    if (h->n_broad > 0 && (d_gamma_ref_line || d_n_line)) {
+        set_error("under a broadener mixture the line list's gamma_ref and n_T are not used: pass NULL per-line "
+                  "outputs (per-broadener gradients: xc_cross_section_vjp_broadening)");
+        return XC_EINVAL;
     }
     if (n_cond && (!grad_sigma || !dT || !dP)) { set_error("NULL grad_sigma / dT / dP"); return XC_EINVAL; }
     DeviceGuard dg(h->device);
@@ -899,6 +900,8 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
     a.d_n_shift = d_n_shift;
     a.d_gamma_ref_line = d_gamma_ref_line;
     a.d_n_line = d_n_line;
+    a.d_gamma0_broad = d_gamma0_broad;
+    a.d_n_broad = d_n_broad;
     a.timing = h->timing;
     a.ev_begin = h->ev[2 * ST_VJP];
     a.ev_end = h->ev[2 * ST_VJP + 1];
@@ -910,6 +913,28 @@ xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n
     XC_TRY(cudaStreamSynchronize(s));
     collect_timing(h, used);
     return XC_OK;
+}
+
+xc_status xc_cross_section_vjp(xc_handle *h, const xc_condition *conds, size_t n_cond, const xc_grid *grid,
+                               const xc_opts *opts, const double *grad_sigma, double *dT, double *dP,
+                               double *d_gamma_scale, double *d_n_shift, double *d_gamma_ref_line,
+                               double *d_n_line, int mem, void *stream) {
+    return vjp_common(h, conds, n_cond, grid, opts, grad_sigma, dT, dP, d_gamma_scale, d_n_shift, d_gamma_ref_line,
+                      d_n_line, nullptr, nullptr, mem, stream);
+}
+
+xc_status xc_cross_section_vjp_broadening(xc_handle *h, const xc_condition *conds, size_t n_cond,
+                                          const xc_grid *grid, const xc_opts *opts, const double *grad_sigma,
+                                          double *dT, double *dP, double *d_gamma_scale, double *d_n_shift,
+                                          double *d_gamma0_broad, double *d_n_broad, int mem, void *stream) {
+    xc_status st = check_handle(h);
+    if (st) return st;
+    if (h->n_broad <= 0) {
+        set_error("no broadener mixture is set (xc_set_broadening)");
+        return XC_EINVAL;
+    }
+    return vjp_common(h, conds, n_cond, grid, opts, grad_sigma, dT, dP, d_gamma_scale, d_n_shift, nullptr, nullptr,
+                      d_gamma0_broad, d_n_broad, mem, stream);
 }
 
 xc_status xc_set_timing(xc_handle *h, int enable) {

@@ -44,36 +44,9 @@ namespace xc {
 constexpr int GT = 256;          // threads per CTA
 constexpr int SCH = 64;          // lines per staged chunk
 constexpr int FOLD_CHUNKS = 8;   // FP32 -> FP64 fold period, in chunks (512 lines)
-constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 region-I constant / sqrt(pi)
-constexpr float kSqrtLn2f = 0.8325546111576977f;
-constexpr float kSqrtLn2OverPi = 0.46971863934982566f;  // sqrt(ln2/pi)
 constexpr float kPiM32 = 0.17958712212516656f;          // pi^(-3/2)
 constexpr float kFarU3 = 1.f / 0.003f;                   // 3-term far-wing series from u >= C / 0.003
 constexpr float kFarU4 = 1.f / 0.012f;                   // 4-term far-wing series from u >= C / 0.012
-
-struct CParam {
-    double inv_scale;   // 1 / scale (power of two)
-    float kT_hi, kT_lo; // c2 log2(e) / T as a float pair
-    float c2T;          // c2 / T
-    float pref;         // abundance / (8 pi c Q) * scale
-    float acoef;        // alpha / nu
-    float log2Tr;       // log2(T_ref / T)
-    float pscale;       // gamma_scale * P / P_ref
-    float nshift;
-    int row;            // output row (the caller's condition index)
-    float dbound;       // upper bound of the far radius D4 over all lines (grid steps)
-    float emis;         // 1: emission (pref = abundance h c / (4 pi Q) * scale), 0: absorption
-    float vv_split;     // Vectorized Voigt: half-width of the exact zone (cm^-1)
-    int vv_beta;        // Vectorized Voigt: 1 = continuity factor beta, 0 = beta 1
-};
-
-struct GeomStats {
-    unsigned int gA_nu2_bits;  // max g A / nu^2 (float bits; values >= 0)
-    unsigned int gA_nu_bits;   // max g A / nu
-    unsigned int nu_bits;      // max nu (float, rounded up)
-    unsigned int gref_bits;    // max |gamma_ref|
-    unsigned int nT_bits;      // max |n_T|
-};
 
 struct GatherParams {
     LinesDev L;
@@ -95,8 +68,6 @@ struct GatherParams {
                                // 128-point block) pairs with span_far; evaluate the rest, add
     double *sigma;
 };
-
-__device__ __forceinline__ float rcp_approx(float x) { return recip(x); }
 
 // Two FP32 values in one 64-bit register pair, for the packed f32x2 arithmetic of
 // sm_100-class GPUs: one instruction issue performs two FP32 adds / multiplies /
@@ -136,21 +107,6 @@ __device__ __forceinline__ f32x2 rcp2(f32x2 a) {
     upk2(a, x, y);
     return pk2(rcp_approx(x), rcp_approx(y));
 }
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// 2^(-z) for z >= 0 with the argument split into integer and fraction
-__device__ __forceinline__ float exp2_neg(float z) {
-    float zi = rintf(z);
-    float zf = z - zi;
-    if (zi > 125.f) return 0.f;
-    float b = ex2_approx(-zf);
-    return b * __int_as_float((127 - (int)zi) << 23);
-}
-
 // ---------------------------------------------------------------------------
 // per-condition constants
 // ---------------------------------------------------------------------------
@@ -319,6 +275,20 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
     }
 }
 
+cudaError_t launch_fp32_setup(const LinesDev &L, size_t n, const CondDev *conds, int nc, const xc_grid &grid,
+                              double cutoff, int *n_abs, float *f, int *ka, int *kb, GeomStats *gs, CParam *cp,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GeomStats), s);
+    if (e != cudaSuccess) return e;
+    if (n) {
+        const unsigned gb = (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16));
+        k_line_geom<<<gb, 256, 0, s>>>(L, n, grid.nu_A, grid.step, grid.n, cutoff, 0.0, nullptr, n_abs, f, ka, kb,
+                                       gs, nullptr, nullptr);
+    }
+    if (nc) k_cparams<<<(nc + 63) / 64, 64, 0, s>>>(conds, nc, gs, cp, grid.step, XC_ABSORPTION, nullptr, 4.f, 0);
+    return cudaGetLastError();
+}
+
 // window -> line range for a fixed maximum cut
 __global__ void k_win_ranges32(const double *__restrict__ nu, int64_t n, double nu_A, double step, int64_t n_pts,
                                int W, double cutmax, int n_win, unsigned *lo, unsigned *hi) {
@@ -374,15 +344,6 @@ __global__ void k_nodes_to_float(const double *x, const double *w, int n, float 
 //   GHS: A = {sh, G', P, 0}
 //   GHB: A = {sh, g', G' - 1/4, P}
 // ---------------------------------------------------------------------------
-// Doppler and Lorentz half-widths in grid steps (Eqs. e:alphaD, e:gamma_L)
-__device__ __forceinline__ void line_widths(float nu, float gref, float nT, const CParam &c, float inv_h, float *ah,
-                                            float *gh) {
-    float al = c.acoef * nu;
-    float ga = c.pscale * gref * ex2_approx((nT + c.nshift) * c.log2Tr);
-    *ah = __fmul_rn(al, inv_h);
-    *gh = __fmul_rn(ga, inv_h);
-}
-
 // Voigt w4 zones of a (line, condition) from its widths in grid steps: x = a |delta|,
 // y, the region-I threshold u >= t2 (t2 < 0: region I everywhere) and the far radius D.
 // Explicitly rounded operations: every kernel that splits work by these gets the same bits.

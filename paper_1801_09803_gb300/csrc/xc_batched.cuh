@@ -9,6 +9,61 @@
 
 namespace xc {
 
+constexpr float kKappa = (float)(0.5641896 / 1.772453850905516027);  // w4 region-I constant / sqrt(pi)
+constexpr float kSqrtLn2f = 0.8325546111576977f;
+constexpr float kSqrtLn2OverPi = 0.46971863934982566f;  // sqrt(ln2/pi)
+
+// Per-condition constants of the FP32 kernels (and the FP32 adjoint), in grid units
+struct CParam {
+    double inv_scale;   // 1 / scale (power of two)
+    float kT_hi, kT_lo; // c2 log2(e) / T as a float pair
+    float c2T;          // c2 / T
+    float pref;         // abundance / (8 pi c Q) * scale
+    float acoef;        // alpha / nu
+    float log2Tr;       // log2(T_ref / T)
+    float pscale;       // gamma_scale * P / P_ref
+    float nshift;
+    int row;            // output row (the caller's condition index)
+    float dbound;       // upper bound of the far radius D4 over all lines (grid steps)
+    float emis;         // 1: emission (pref = abundance h c / (4 pi Q) * scale), 0: absorption
+    float vv_split;     // Vectorized Voigt: half-width of the exact zone (cm^-1)
+    int vv_beta;        // Vectorized Voigt: 1 = continuity factor beta, 0 = beta 1
+};
+
+struct GeomStats {
+    unsigned int gA_nu2_bits;  // max g A / nu^2 (float bits; values >= 0)
+    unsigned int gA_nu_bits;   // max g A / nu
+    unsigned int nu_bits;      // max nu (float, rounded up)
+    unsigned int gref_bits;    // max |gamma_ref|
+    unsigned int nT_bits;      // max |n_T|
+};
+
+__device__ __forceinline__ float rcp_approx(float x) { return recip(x); }
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 2^(-z) for z >= 0 with the argument split into integer and fraction
+__device__ __forceinline__ float exp2_neg(float z) {
+    float zi = rintf(z);
+    float zf = z - zi;
+    if (zi > 125.f) return 0.f;
+    float b = ex2_approx(-zf);
+    return b * __int_as_float((127 - (int)zi) << 23);
+}
+
+// Doppler and Lorentz half-widths in grid steps (Eqs. e:alphaD, e:gamma_L)
+__device__ __forceinline__ void line_widths(float nu, float gref, float nT, const CParam &c, float inv_h, float *ah,
+                                            float *gh) {
+    float al = c.acoef * nu;
+    float ga = c.pscale * gref * ex2_approx((nT + c.nshift) * c.log2Tr);
+    *ah = __fmul_rn(al, inv_h);
+    *gh = __fmul_rn(ga, inv_h);
+}
+
 struct BatchedArgs {
     LinesDev L{};
     size_t n_lines = 0;
@@ -42,6 +97,7 @@ struct VjpArgs {
     const double *grad_sigma = nullptr;
     double *dT = nullptr, *dP = nullptr, *d_gamma_scale = nullptr, *d_n_shift = nullptr;
     double *d_gamma_ref_line = nullptr, *d_n_line = nullptr;
+    double *d_gamma0_broad = nullptr, *d_n_broad = nullptr;   // per broadener of a mixture (nullable)
     bool timing = false;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
 };
@@ -78,6 +134,12 @@ struct BatchedState {
 };
 
 xc_status batched_run(BatchedState *st, const BatchedArgs &a, int64_t *launches);
+// per-line grid geometry for a fixed cut (integer position n_abs, fraction f, inclusive
+// cut range [ka, kb]) and the per-condition FP32 constants (in order of increasing
+// profile width, each with its caller's row), as the batched FP32 kernels make them
+cudaError_t launch_fp32_setup(const LinesDev &L, size_t n, const CondDev *conds, int nc, const xc_grid &grid,
+                              double cutoff, int *n_abs, float *f, int *ka, int *kb, GeomStats *gs, CParam *cp,
+                              cudaStream_t s);
 xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches);
 // after the stream has synchronised: XC_ETIMEOUT if the tensor-core kernel reported a
 // wait that ran out (its results are then not valid), else XC_OK

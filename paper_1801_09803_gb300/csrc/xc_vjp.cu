@@ -12,12 +12,33 @@
 // with dlnI/dT = c2 E''/T^2 - (c2 nu/T^2)/(exp(c2 nu/T) - 1) - Q'/Q.
 //
 // Layout: one warp per line (grid-stride), lanes stride over the line's grid
-// points, lane c holds the FP64 constants of condition c (<= 32 per launch).
+// points, lane c holds the constants of condition c (<= 32 per launch).
 // Per-condition scalars are reduced warp -> block in fixed order, written as
 // block partials and summed in block order by a second kernel, so the result
-// is deterministic.  Region I of w4 uses its rational form and closed-form
-// derivatives; points in regions II-IV evaluate the complex w4 and its exact
-// derivative F'(t).
+// is deterministic.
+//
+// Two kernels.  k_vjp_lines<PROF> recomputes everything in FP64 (the FP64
+// path, and the reference of the finite-difference checks).  k_vjp32<PROF> is the
+// FP32 path: GB300 runs FP64 at a small fraction of its FP32 rate, so every
+// per-point and per-line quantity is FP32 there and only the per-condition
+// accumulators and the per-line outputs are FP64.  It works in grid units
+// (delta = k - nu/step, widths a = alpha/step, g = gamma/step) on the line
+// geometry and condition constants of the forward FP32 kernels:
+//   * w4 region I (the bulk of the points): V = kappa g R, R = (u + C)/((C - u)^2
+//     + 4 g^2 u), u = delta^2, b = a^2/(2 ln 2), C = b + g^2, kappa = 0.5641896/sqrt(pi);
+//     three sums of g_k times A0 = R, A1 = dR/dC = (1 - 2 (C - u) R')/D with R' = R,
+//     and A2 = u R / D (D the denominator), from which
+//       sum g V = kappa g S0,   sum g dV/da = kappa g (a/ln 2) S1,
+//       sum g dV/dg = kappa (S0 + 2 g^2 (S1 - 4 S2));
+//   * regions II-IV (a band around the centre): V = sqrt(ln2/pi)/a Re F,
+//     dV/dg = (ln2/sqrt(pi))/a^2 Re F', dV/da = -sqrt(ln2/pi)/a^2 Re(F + t F'), with
+//     F + t F' = d(tF)/dt written so that no cancellation is left: its numerator and
+//     that of F' expanded once, at compile time, into polynomials whose leading terms
+//     cancel exactly in the coefficients (in FP32 the forms
+//     F + x dF/dx + y dF/dy and (N'D - ND')/D^2 lose up to 1e-3 of the derivative
+//     sums to cancellation in these regions);
+//   * per-point FP32 terms are summed in FP32 over 8 points, then into compensated
+//     (Kahan) sums; the warp reduction of the sums is compensated too (TwoSum).
 #include <math.h>
 
 #include <algorithm>
@@ -29,10 +50,11 @@ namespace xc {
 constexpr int VT = 256;
 constexpr int VW = VT / 32;
 constexpr int VMAXC = 32;
-constexpr double kKappa64 = 0.5641896 / 1.772453850905516027;
+constexpr int VMAXB = 8;   // broadeners of a mixture (the limit of xc_set_broadening)
 
 struct VjpLineCond {  // per (line, condition), FP64
     double I, al, ga, dlnI, dga_dP, dga_ds, dga_dgr, lnTr, T;
+    double ntga;   // sum over the width's terms of (n + n_shift) gamma: -T dgamma/dT
 };
 
 __device__ inline VjpLineCond line_cond64(const LinesDev &L, size_t l, const CondDev &c) {
@@ -53,36 +75,26 @@ __device__ inline VjpLineCond line_cond64(const LinesDev &L, size_t l, const Con
     r.dga_dgr = c.gamma_scale * tn * (c.P / c.P_ref);
     r.dlnI = kC2 * (double)L.elower[l] * inv_T * inv_T - (x * inv_T) / expm1(x) - c.dQdT / c.Q;
     r.T = c.T;
+    r.ntga = ((double)L.n_T[l] + c.n_shift) * r.ga;
+    if (L.n_broad > 0) {
+        // a mixture of broadeners: gamma = gamma_scale P/P_ref sum_i rho_i gamma_0,i (T_ref/T)^(n_i + n_shift)
+        double gu = 0.0, ngu = 0.0;
+        for (int i = 0; i < L.n_broad; ++i) {
+            const double ni = L.bn[(size_t)i * L.bstride + l] + c.n_shift;
+            const double gi = L.bgam[(size_t)i * L.bstride + l] * exp(ni * r.lnTr);
+            gu += gi;
+            ngu += ni * gi;
+        }
+        r.ga = c.gamma_scale * gu * (c.P / c.P_ref);
+        r.dga_dP = c.gamma_scale * gu / c.P_ref;
+        r.dga_ds = gu * (c.P / c.P_ref);
+        r.dga_dgr = 0.0;
+        r.ntga = c.gamma_scale * ngu * (c.P / c.P_ref);
+    }
     return r;
 }
 
 __device__ inline double shfl64(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-// Re w and its partial derivatives d/dx, d/dy (x >= 0) in w4's regions I and II,
-// from their real forms: region I is one pair of Lorentzians (nodes +-1/sqrt2),
-// region II two pairs (nodes +-sqrt(Q_m), Q_m = (3 -+ sqrt 6)/2):
-//   Re w = y sum_m A_m (X + Y + Q_m) / ((X + Y - Q_m)^2 + 4 Q_m Y),  X = x^2, Y = y^2.
-__device__ inline float w4_re_grad_12(float x, float y, float *dx, float *dy) {
-    constexpr double a = 1.410474, b = 0.5641896, s6 = 2.449489742783178098;
-    const bool r1 = x + y >= 15.f;
-    const float Qm[2] = {r1 ? 0.5f : (float)((3.0 - s6) / 2.0), (float)((3.0 + s6) / 2.0)};
-    const float Am[2] = {r1 ? 0.5641896f : (float)((a - b * ((3.0 - s6) / 2.0)) / s6),
-                         r1 ? 0.f : (float)(-(a - b * ((3.0 + s6) / 2.0)) / s6)};
-    const float X = x * x, Y = y * y;
-    float S = 0.f, SX = 0.f, SY = 0.f;
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        float N = X + Y + Qm[m], t = X + Y - Qm[m];
-        float D = fmaf(t, t, 4.f * Qm[m] * Y);
-        float rD = 1.f / D, rD2 = rD * rD;
-        S = fmaf(Am[m] * N, rD, S);
-        SX = fmaf(Am[m], (D - 2.f * N * t) * rD2, SX);                    // d(N/D)/dX
-        SY = fmaf(Am[m], (D - N * (2.f * t + 4.f * Qm[m])) * rD2, SY);    // d(N/D)/dY
-    }
-    *dx = y * SX * 2.f * x;
-    *dy = S + y * SY * 2.f * y;
-    return y * S;
-}
 
 // compensated FP32 sum (Kahan): the running compensation keeps the rounding of every
 // addition, so the sum is good to a few FP32 ulps of its terms whatever its length
@@ -125,25 +137,23 @@ __device__ inline void prof_deriv64(double D, double al, double ga, double *V, d
     }
 }
 
-template <int PROF, bool F64>
+template <int PROF>
 __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const CondDev *__restrict__ conds, int nc,
                                                   double nu_A, double step, int64_t n_pts, double cutoff,
                                                   double width_mult, const double *__restrict__ g64,
-                                                  const float *__restrict__ g32, double *block_part /*[blk][nc][4]*/,
-                                                  double *d_gref_line, double *d_n_line, int accumulate) {
+                                                  double *block_part /*[blk][nc][4 + 2 nb]*/, double *d_gref_line,
+                                                  double *d_n_line, int accumulate) {
     __shared__ double s_part[VW][VMAXC][4];
+    __shared__ double s_broad[VW][VMAXC][2 * VMAXB];   // mixture: per broadener, scale and n-shift sums
+    const int nb = L.n_broad, NQ = 4 + 2 * nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double accT = 0.0, accP = 0.0, accS = 0.0, accN = 0.0;  // lane c: condition c
     const CondDev cme = conds[lane < nc ? lane : 0];
+    for (int q = 0; q < 2 * nb; ++q) s_broad[warp][lane][q] = 0.0;
     for (size_t l = (size_t)blockIdx.x * VW + warp; l < n; l += (size_t)gridDim.x * VW) {
         const double nu = L.nu[l];
         VjpLineCond mine = line_cond64(L, l, cme);
         double line_gr = 0.0, line_n = 0.0;
-        // grid position of the line
-        const double dpos = (nu - nu_A) / step;
-        const double fl = floor(dpos);
-        const float ff = (float)(dpos - fl);
-        const int64_t nabs = (int64_t)fl;
         int64_t ka0 = 0, kb0 = -1;
         if (!(width_mult > 0.0)) line_k_range(nu, cutoff, nu_A, step, n_pts, &ka0, &kb0);
         for (int c = 0; c < nc; ++c) {
@@ -151,104 +161,14 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
             int64_t ka = ka0, kb = kb0;
             if (width_mult > 0.0) line_k_range(nu, fmin(width_mult * fmax(al, ga), cutoff), nu_A, step, n_pts, &ka, &kb);
             double SI = 0.0, Sa = 0.0, Sg = 0.0;
-            if (F64) {
-                for (int64_t k = ka + lane; k <= kb; k += 32) {
-                    double D = __dsub_rn(grid_x(nu_A, step, k), nu);
-                    double V, dVa, dVg;
-                    prof_deriv64<PROF>(D, al, ga, &V, &dVa, &dVg);
-                    double g = g64[(size_t)c * n_pts + k];
-                    SI += g * V;
-                    Sa += g * dVa;
-                    Sg += g * dVg;
-                }
-            } else {
-                const float h = (float)step;
-                const float alf = (float)al, gaf = (float)ga;
-                const float g2 = gaf * gaf;
-                const float b = alf * alf * (float)(0.5 / 0.6931471805599453);
-                const float bg = b + g2;
-                const float a_sc = (float)kSqrtLn2 / alf;      // x = a |D|
-                const float yv = a_sc * gaf;
-                const float thr = yv < 15.f ? (15.f - yv) / a_sc : -1.f;  // region I iff |D| >= thr
-                const float thr2 = thr > 0.f ? thr * thr : -1.f;
-                // FP32 terms in compensated (Kahan) FP32 sums: as accurate as folding them into
-                // FP64 and free of FP64 instructions, which run at a small fraction of the FP32
-                // rate on this GPU.  Centre points of w4 regions III/IV, which carry the largest
-                // terms of sums that cancel (the derivatives of a unit-area profile integrate to
-                // zero), are evaluated and added in FP64.
-                double C0 = 0.0, C1 = 0.0, C2 = 0.0;
-                KahanF s0, s1, s2, c0, c1, c2;
-                const float *gc = g32 + (size_t)c * n_pts;
-                for (int64_t kb8 = ka + lane; kb8 <= kb; kb8 += 32 * 8) {
-#pragma unroll 4
-                    for (int j = 0; j < 8; ++j) {
-                        const int64_t k = kb8 + 32 * j;
-                        if (k > kb) break;
-                        float D = ((float)(k - nabs) - ff) * h;
-                        float u = D * D;
-                        float g = gc[k];
-                        if (PROF == XC_VOIGT_W4) {
-                            if (u >= thr2) {
-                                float t = bg - u;
-                                float Dn = fmaf(t, t, 4.f * g2 * u);
-                                float N = u + bg;
-                                float rD = 1.f / Dn;
-                                float rD2 = rD * rD;
-                                s0.add(g * (N * rD));
-                                s1.add(g * (fmaf(-2.f * N, t, Dn) * rD2));
-                                float q = fmaf(Dn, N + 2.f * g2, -4.f * g2 * N * N);
-                                s2.add(g * (q * rD2));
-                            } else if (a_sc * fabsf(D) + yv >= 5.5f) {
-                                // region II (or I by rounding at its edge): real form, FP32
-                                float rx, ry;
-                                float w = w4_re_grad_12(a_sc * fabsf(D), yv, &rx, &ry);
-                                float v = (float)0.46971863934982566 / alf * w;
-                                float k2 = (float)(0.6931471805599453 / 1.772453850905516027) / (alf * alf);
-                                float dVD = k2 * (D < 0.f ? -rx : rx), dg = k2 * ry;
-                                c0.add(g * v);
-                                c1.add(g * (-(v + D * dVD + gaf * dg) / alf));
-                                c2.add(g * dg);
-                            } else {
-                                // regions III/IV: complex rationals whose derivative cancels in
-                                // FP32; evaluated in FP64 (a narrow band around the centre)
-                                double D64 = __dsub_rn(grid_x(nu_A, step, k), nu);
-                                double V, dVa, dVg;
-                                prof_deriv64<XC_VOIGT_W4>(D64, al, ga, &V, &dVa, &dVg);
-                                double gd = (double)g;
-                                C0 += gd * V;
-                                C1 += gd * dVa;
-                                C2 += gd * dVg;
-                            }
-                        } else if (PROF == XC_DOPPLER) {
-                            float e = expf(-(float)kLn2 * u / (alf * alf));
-                            c0.add(g * e);
-                            c1.add(g * (e * u));
-                        } else {
-                            float r = 1.f / (u + g2);
-                            c0.add(g * r);
-                            c2.add(g * ((u - g2) * r * r));
-                        }
-                    }
-                }
-                const double S0 = s0.value(), S1 = s1.value(), S2 = s2.value();
-                C0 += c0.value();
-                C1 += c1.value();
-                C2 += c2.value();
-                if (PROF == XC_VOIGT_W4) {
-                    double kg = kKappa64 * ga;
-                    SI = kg * S0 + C0;
-                    Sa = kg * S1 * (al / kLn2) + C1;  // dV/dalpha = dV/db * alpha/ln2
-                    Sg = kKappa64 * S2 + C2;
-                } else if (PROF == XC_DOPPLER) {
-                    double pd = 0.46971863934982566 / al;
-                    SI = pd * C0;
-                    Sa = pd * (-C0 / al + 2.0 * kLn2 / (al * al * al) * C1);
-                    Sg = 0.0;
-                } else {
-                    SI = ga / kPi * C0;
-                    Sa = 0.0;
-                    Sg = C2 / kPi;
-                }
+            for (int64_t k = ka + lane; k <= kb; k += 32) {
+                double D = __dsub_rn(grid_x(nu_A, step, k), nu);
+                double V, dVa, dVg;
+                prof_deriv64<PROF>(D, al, ga, &V, &dVa, &dVg);
+                double g = g64[(size_t)c * n_pts + k];
+                SI += g * V;
+                Sa += g * dVa;
+                Sg += g * dVg;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 SI += __shfl_xor_sync(0xffffffffu, SI, o);
@@ -258,10 +178,18 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
             // every lane holds the sums; lane c owns condition c's scalars
             if (lane == c) {
                 const double T = mine.T;
-                accT += I * (SI * mine.dlnI + Sa * al / (2.0 * T) - Sg * (double)(L.n_T[l] + cme.n_shift) * ga / T);
+                accT += I * (SI * mine.dlnI + Sa * al / (2.0 * T) - Sg * mine.ntga / T);
                 accP += I * Sg * mine.dga_dP;
                 accS += I * Sg * mine.dga_ds;
                 accN += I * Sg * ga * mine.lnTr;
+                // each broadener's term gamma_i: d gamma / d(scale of its gamma_0) = gamma_i,
+                // d gamma / d(shift of its n) = gamma_i ln(T_ref/T)
+                for (int i = 0; i < nb; ++i) {
+                    const double gi = cme.gamma_scale * (cme.P / cme.P_ref) * L.bgam[(size_t)i * L.bstride + l] *
+                                      exp((L.bn[(size_t)i * L.bstride + l] + cme.n_shift) * mine.lnTr);
+                    s_broad[warp][lane][2 * i] += I * Sg * gi;
+                    s_broad[warp][lane][2 * i + 1] += I * Sg * gi * mine.lnTr;
+                }
             }
             line_gr += I * Sg * shfl64(mine.dga_dgr, c);
             line_n += I * Sg * ga * shfl64(mine.lnTr, c);
@@ -278,38 +206,46 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
         s_part[warp][lane][3] = accN;
     }
     __syncthreads();
-    if (threadIdx.x < nc * 4) {
-        int c = threadIdx.x >> 2, q = threadIdx.x & 3;
+    for (int i = threadIdx.x; i < nc * NQ; i += blockDim.x) {
+        const int c = i / NQ, q = i % NQ;
         double s = 0.0;
-        for (int w = 0; w < VW; ++w) s += s_part[w][c][q];
-        block_part[((size_t)blockIdx.x * nc + c) * 4 + q] = s;
+        for (int w = 0; w < VW; ++w) s += q < 4 ? s_part[w][c][q] : s_broad[w][c][q - 4];
+        block_part[((size_t)blockIdx.x * nc + c) * NQ + q] = s;
     }
 }
 
-// sum block partials in block order; conditions c0.. of this chunk
-__global__ void k_vjp_finish(const double *block_part, int n_blocks, int nc, int c0, double *dT, double *dP,
-                             double *dS_acc, double *dN_acc) {
-    int c = threadIdx.x;
-    if (c >= nc) return;
-    double s[4] = {0, 0, 0, 0};
-    for (int b = 0; b < n_blocks; ++b)
-        for (int q = 0; q < 4; ++q) s[q] += block_part[((size_t)b * nc + c) * 4 + q];
-    dT[c0 + c] = s[0];
-    dP[c0 + c] = s[1];
-    dS_acc[c0 + c] = s[2];
-    dN_acc[c0 + c] = s[3];
+// sum block partials in block order: quantity q of this chunk's condition c (values
+// [blk][nc][NQ]) -> its output row (rows[c], or c0 + c when rows is null).  acc holds per
+// row: gamma_scale and n_shift sums, then 2 nb per-broadener sums.
+__global__ void k_vjp_finish(const double *block_part, int n_blocks, int nc, int NQ, int c0, const CParam *rows,
+                             double *dT, double *dP, double *acc) {
+    for (int i = threadIdx.x; i < nc * NQ; i += blockDim.x) {
+        const int c = i / NQ, q = i % NQ;
+        double s = 0.0;
+        for (int b = 0; b < n_blocks; ++b) s += block_part[((size_t)b * nc + c) * NQ + q];
+        const int r = rows ? rows[c].row : c0 + c;
+        if (q == 0) dT[r] = s;
+        else if (q == 1) dP[r] = s;
+        else acc[(size_t)r * (NQ - 2) + (q - 2)] = s;
+    }
 }
 
-// global scalars: sum over conditions in order
-__global__ void k_vjp_scalars(const double *dS_acc, const double *dN_acc, int nc, double *ds, double *dn) {
-    if (threadIdx.x != 0) return;
-    double a = 0.0, b = 0.0;
-    for (int c = 0; c < nc; ++c) {
-        a += dS_acc[c];
-        b += dN_acc[c];
+// global scalars and per-broadener sums: sums over conditions in order
+__global__ void k_vjp_scalars(const double *acc, int nc, int nb, double *ds, double *dn, double *dg0b,
+                              double *dnb) {
+    const int q = threadIdx.x, W = 2 + 2 * nb;
+    if (q >= W) return;
+    double a = 0.0;
+    for (int c = 0; c < nc; ++c) a += acc[(size_t)c * W + q];
+    if (q == 0) {
+        if (ds) *ds = a;
+    } else if (q == 1) {
+        if (dn) *dn = a;
+    } else if (((q - 2) & 1) == 0) {
+        if (dg0b) dg0b[(q - 2) / 2] = a;
+    } else if (dnb) {
+        dnb[(q - 2) / 2] = a;
     }
-    if (ds) *ds = a;
-    if (dn) *dn = b;
 }
 
 __global__ void k_to_f32(const double *in, float *out, size_t n) {
@@ -317,14 +253,389 @@ __global__ void k_to_f32(const double *in, float *out, size_t n) {
         out[i] = (float)in[i];
 }
 
-typedef void (*VjpFn)(LinesDev, size_t, const CondDev *, int, double, double, int64_t, double, double,
-                      const double *, const float *, double *, double *, double *, int);
+// ---------------------------------------------------------------------------
+// FP32 adjoint
+// ---------------------------------------------------------------------------
+// polynomial coefficient tables (ascending powers), derived at compile time from the
+// published w4 coefficients of regions III and IV
+template <int N>
+struct Pc {
+    double c[N];
+};
+template <int NA, int NB>
+constexpr Pc<NA + NB - 1> pmul(const Pc<NA> &a, const Pc<NB> &b) {
+    Pc<NA + NB - 1> r{};
+    for (int i = 0; i < NA; ++i)
+        for (int j = 0; j < NB; ++j) r.c[i + j] += a.c[i] * b.c[j];
+    return r;
+}
+// a_i (k0 + k1 i): k0 = 1, k1 = 1 gives p + x p'; k0 = 0, k1 = 1 gives x p'
+template <int N>
+constexpr Pc<N> pidx(const Pc<N> &a, double k0, double k1) {
+    Pc<N> r{};
+    for (int i = 0; i < N; ++i) r.c[i] = a.c[i] * (k0 + k1 * i);
+    return r;
+}
+template <int N>
+constexpr Pc<N> psub(const Pc<N> &a, const Pc<N> &b) {
+    Pc<N> r{};
+    for (int i = 0; i < N; ++i) r.c[i] = a.c[i] - b.c[i];
+    return r;
+}
+// region III: F = N3(t)/D3(t), t = y - i x
+__device__ constexpr Pc<5> kN3{{16.4955, 20.20933, 11.96482, 3.778987, 0.5642236}};
+__device__ constexpr Pc<6> kD3{{16.4955, 38.82363, 39.27121, 21.69274, 6.699398, 1.0}};
+// d(tF)/dt = [D3 (N3 + t N3') - N3 (t D3')] / D3^2 (the t^9 coefficient cancels exactly)
+__device__ constexpr Pc<10> kG3 = psub(pmul(kD3, pidx(kN3, 1.0, 1.0)), pmul(kN3, pidx(kD3, 0.0, 1.0)));
+// region IV: F = e^u - t N4(m)/D4(m), u = t^2, m = -u (plain Horner in m)
+__device__ constexpr Pc<7> kN4{{36183.31, 3321.9905, 1540.787, 219.0313, 35.76683, 1.320522, 0.56419}};
+__device__ constexpr Pc<8> kD4{{32066.6, 24322.84, 9022.228, 2186.181, 364.2191, 61.57037, 1.841439, 1.0}};
+// d(u r)/du = S4(m)/D4^2 with S4 = D4 (N4 + m N4_m) - N4 (m D4_m) (m^13 cancels exactly), and
+// d(t r)/dt = r + 2 u r_u = T4(m)/D4^2 with T4 = D4 (N4 + 2 m N4_m) - N4 (2 m D4_m)
+__device__ constexpr Pc<14> kS4 = psub(pmul(kD4, pidx(kN4, 1.0, 1.0)), pmul(kN4, pidx(kD4, 0.0, 1.0)));
+__device__ constexpr Pc<14> kT4 = psub(pmul(kD4, pidx(kN4, 1.0, 2.0)), pmul(kN4, pidx(kD4, 0.0, 2.0)));
 
-static VjpFn pick(int prof, bool f64) {
+template <int N>
+__device__ __forceinline__ Cx<float> horner_f(const Pc<N> &p, Cx<float> t, int top = N - 1) {
+    Cx<float> r = cx<float>((float)p.c[top], 0.f);
+#pragma unroll
+    for (int i = N - 2; i >= 0; --i)
+        if (i < top) r = (float)p.c[i] + r * t;
+    return r;
+}
+// derivative of the polynomial: sum i c_i t^(i-1)
+template <int N>
+__device__ __forceinline__ Cx<float> dhorner_f(const Pc<N> &p, Cx<float> t) {
+    Cx<float> r = cx<float>((float)((N - 1) * p.c[N - 1]), 0.f);
+#pragma unroll
+    for (int i = N - 2; i >= 1; --i) r = (float)(i * p.c[i]) + r * t;
+    return r;
+}
+
+// Re F, Re F' and Re(F + t F') of w4 in regions II-IV at x >= 0, y (t = y - i x), FP32
+__device__ __noinline__ float3 w4_band_f32(float x, float y) {
+    constexpr double a = 1.410474, b = 0.5641896;
+    const Cx<float> t = cx<float>(y, -x);
+    const Cx<float> u = t * t;
+    Cx<float> F, Fp, G;
+    if (x + y >= 5.5f) {
+        // region II: F = t (a + b u)/(3/4 + 3u + u^2)
+        const Cx<float> D = 0.75f + u * (3.f + u);
+        const Cx<float> iD = cdiv(cx<float>(1.f, 0.f), D);
+        const Cx<float> iD2 = iD * iD;
+        F = (t * ((float)a + (float)b * u)) * iD;
+        Fp = ((float)(0.75 * a) + u * ((float)(2.25 * b - 3 * a) + u * ((float)(3 * b - 3 * a) + (float)(-b) * u))) * iD2;
+        G = (2.f * t) * (((float)(0.75 * a) + u * ((float)(1.5 * b) + (float)(3 * b - a) * u)) * iD2);
+    } else if (y >= 0.195f * x - 0.176f) {
+        const Cx<float> N = horner_f(kN3, t), D = horner_f(kD3, t);
+        const Cx<float> iD = cdiv(cx<float>(1.f, 0.f), D);
+        const Cx<float> iD2 = iD * iD;
+        F = N * iD;
+        Fp = (dhorner_f(kN3, t) * D - N * dhorner_f(kD3, t)) * iD2;
+        G = horner_f(kG3, t, 8) * iD2;
+    } else {
+        const Cx<float> m = cx<float>(-u.re, -u.im);
+        const Cx<float> N = horner_f(kN4, m), D = horner_f(kD4, m);
+        const Cx<float> iD = cdiv(cx<float>(1.f, 0.f), D);
+        const Cx<float> iD2 = iD * iD;
+        float sn, cs;
+        sincosf(u.im, &sn, &cs);
+        const float eu = expf(u.re);
+        const Cx<float> e = cx<float>(eu * cs, eu * sn);
+        F = e - t * (N * iD);
+        Fp = (2.f * t) * e - horner_f(kT4, m) * iD2;
+        G = e * (1.f + 2.f * u) - (2.f * t) * (horner_f(kS4, m, 12) * iD2);
+    }
+    return make_float3(F.re, Fp.re, G.re);
+}
+
+// compensated pair (hi + lo) and its exact-error addition (TwoSum), for warp reductions
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bp = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+    return F2{s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+__device__ __forceinline__ F2 f2_warp_sum(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F2 w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = f2_add(v, w);
+    }
+    return v;
+}
+
+struct Vjp32Params {
+    LinesDev L;
+    size_t n;
+    const int *n_abs, *ka_abs, *kb_abs;   // per line (fixed cut)
+    const float *f_frac;
+    const CParam *cp;                     // this launch's conditions (width order), rows = caller index
+    const CondDev *conds;                 // all conditions, caller order
+    int nc;                               // conditions in this launch (<= 32)
+    double nu_A, step, cutoff, width_mult;
+    int64_t n_pts;
+    const float *g32;                     // dL/dsigma, [caller row][n_pts]
+    double *block_part;                   // [block][nc][4 + 2 nb]
+    double *d_gref_line, *d_n_line;       // per line (sorted order), nullable
+    int accumulate;                       // add to the per-line outputs (later condition chunks)
+};
+
+// MIX: the Lorentz widths come from the handle's mixture of broadeners (per broadener
+// and line rho_i gamma_0,i and n_i): gamma = gamma_scale P/P_ref sum_i rho_i gamma_0,i
+// (T_ref/T)^(n_i + n_shift), and the adjoint also sums, per broadener, the gradients of a
+// scale on its gamma_0 values (d gamma = gamma_i) and of a shift of its n values
+// (d gamma = gamma_i ln(T_ref/T))
+template <int PROF, bool MIX>
+__global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
+    __shared__ double s_part[VW][VMAXC][4];
+    __shared__ double s_broad[VW][VMAXC][MIX ? 2 * VMAXB : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nc = p.nc;
+    const int nb = MIX ? p.L.n_broad : 0, NQ = 4 + 2 * nb;
+    if (MIX)
+        for (int q = 0; q < 2 * nb; ++q) s_broad[warp][lane][q] = 0.0;
+    const float inv_h = (float)(1.0 / p.step);
+    // this lane's condition: FP32 constants, and FP64 accumulators of its four scalars
+    const bool mine = lane < nc;
+    const CParam cc = p.cp[mine ? lane : 0];
+    const CondDev cd = p.conds[cc.row];
+    const float invT = (float)(1.0 / cd.T);
+    const float dQQ = (float)(cd.dQdT / cd.Q);
+    const float lnTr = (float)log(cd.T_ref / cd.T);
+    const float fP = (float)(cd.gamma_scale / cd.P_ref);     // d(gamma_scale P/P_ref)/dP
+    const float fS = (float)(cd.P / cd.P_ref);               // d(gamma_scale P/P_ref)/d(gamma_scale)
+    double accT = 0.0, accP = 0.0, accS = 0.0, accN = 0.0;
+    for (size_t l = (size_t)blockIdx.x * VW + warp; l < p.n; l += (size_t)gridDim.x * VW) {
+        const float nu = (float)p.L.nu[l];
+        const float E = p.L.elower[l];
+        const float gA = (float)p.L.g_up[l] * p.L.A[l];
+        const float gref = p.L.gamma_ref[l], nT = p.L.n_T[l];
+        // lane c: intensity (scaled as the forward kernels scale it), widths in grid steps,
+        // d ln I / dT = c2 E''/T^2 - (c2 nu/T^2)/(exp(c2 nu/T) - 1) - Q'/Q
+        // gq: gamma/h per unit of gamma_scale P/P_ref; ngh: sum of (n + n_shift) gamma/h over
+        // the width's terms (-T/h dgamma/dT); gi: the mixture's terms (per unit of gamma_scale P/P_ref)
+        float Is = 0.f, ah = 1.f, gh = 0.f, tn = 0.f, dlnI = 0.f, gq = 0.f, ngh = 0.f;
+        float gi[MIX ? VMAXB : 1];
+        if (mine) {
+            const float z = fmaf(E, cc.kT_hi, E * cc.kT_lo);
+            const float xs = cc.c2T * nu;
+            Is = cc.pref * gA * rcp_approx(nu * nu) * exp2_neg(z) * (-expm1f(-xs));
+            if (MIX) {
+                ah = __fmul_rn(cc.acoef * nu, inv_h);
+                float nq = 0.f;
+#pragma unroll
+                for (int i = 0; i < VMAXB; ++i) {
+                    gi[i] = 0.f;
+                    if (i < nb) {
+                        const float ni = (float)p.L.bn[(size_t)i * p.L.bstride + l] + cc.nshift;
+                        gi[i] = (float)p.L.bgam[(size_t)i * p.L.bstride + l] * ex2_approx(ni * cc.log2Tr) * inv_h;
+                        gq += gi[i];
+                        nq = fmaf(ni, gi[i], nq);
+                    }
+                }
+                gh = cc.pscale * gq;
+                ngh = cc.pscale * nq;
+            } else {
+                line_widths(nu, gref, nT, cc, inv_h, &ah, &gh);
+                tn = ex2_approx((nT + cc.nshift) * cc.log2Tr);
+                gq = gref * tn * inv_h;
+                ngh = gh * (nT + cc.nshift);
+            }
+            dlnI = cc.c2T * E * invT - xs * invT / expm1f(xs) - dQQ;
+        }
+        const int na = p.n_abs[l];
+        const float ff = p.f_frac[l];
+        int ka = p.ka_abs[l], kb = p.kb_abs[l];
+        float SIm = 0.f, Sam = 0.f, Sgm = 0.f;   // lane c: its condition's three sums
+        for (int c = 0; c < nc; ++c) {
+            const float a_h = __shfl_sync(0xffffffffu, ah, c), g_h = __shfl_sync(0xffffffffu, gh, c);
+            if (p.width_mult > 0.0) {
+                // per-(line, condition) cut min(cutoff, width_mult max(alpha, gamma)), FP64 as in
+                // the forward kernels' geometry
+                int64_t k0 = 1, k1 = 0;
+                if (lane == c) {
+                    const double nud = p.L.nu[l];
+                    const double al = alpha_coef(cd.T, cd.mass_da) * nud;
+                    const double ga = cd.gamma_scale * (double)gref * exp(((double)nT + cd.n_shift) *
+                                                                          log(cd.T_ref / cd.T)) * (cd.P / cd.P_ref);
+                    line_k_range(nud, fmin(p.width_mult * fmax(al, ga), p.cutoff), p.nu_A, p.step, p.n_pts, &k0, &k1);
+                }
+                ka = __shfl_sync(0xffffffffu, (int)k0, c);
+                kb = __shfl_sync(0xffffffffu, (int)k1, c);
+            }
+            const float *gc = p.g32 + (size_t)__shfl_sync(0xffffffffu, cc.row, c) * (size_t)p.n_pts;
+            KahanF K0, K1, K2, B0, B1, B2;
+            if (PROF == XC_VOIGT_W4) {
+                const float asc = kSqrtLn2f * rcp_approx(a_h);   // x = asc |delta|
+                const float y = asc * g_h;
+                const float bb = a_h * a_h * (float)(0.5 / 0.6931471805599453), g2 = g_h * g_h;
+                const float C = bb + g2, g4 = 4.f * g2;
+                const float thr = (15.f - y) * rcp_approx(asc);
+                const float thr2 = y < 15.f ? thr * thr : -1.f;   // region I iff u >= thr2
+                for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
+                    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k8 + 32 * j;
+                        if (k <= kb) {
+                            const float d = (float)(k - na) - ff;
+                            const float u = d * d;
+                            const float gk = gc[k];
+                            if (u >= thr2) {
+                                const float t = C - u;
+                                const float Dn = fmaf(t, t, g4 * u);
+                                const float rD = rcp_approx(Dn);
+                                const float w = (u + C) * rD;
+                                q0 = fmaf(gk, w, q0);
+                                q1 = fmaf(gk, rD * fmaf(-2.f * t, w, 1.f), q1);
+                                q2 = fmaf(gk, u * w * rD, q2);
+                            } else {
+                                const float3 r = w4_band_f32(asc * fabsf(d), y);
+                                B0.add(gk * r.x);
+                                B1.add(gk * r.z);   // Re(F + t F')
+                                B2.add(gk * r.y);   // Re F'
+                            }
+                        }
+                    }
+                    K0.add(q0);
+                    K1.add(q1);
+                    K2.add(q2);
+                }
+                const F2 s0 = f2_warp_sum(F2{K0.s, -K0.c}), s1 = f2_warp_sum(F2{K1.s, -K1.c});
+                const F2 s2 = f2_warp_sum(F2{K2.s, -K2.c});
+                const F2 b0 = f2_warp_sum(F2{B0.s, -B0.c}), b1 = f2_warp_sum(F2{B1.s, -B1.c});
+                const F2 b2 = f2_warp_sum(F2{B2.s, -B2.c});
+                if (lane == c) {
+                    const float S0 = s0.hi + s0.lo, S1 = s1.hi + s1.lo, S2 = s2.hi + s2.lo;
+                    const float ia = rcp_approx(a_h);
+                    const float kd = kSqrtLn2OverPi * ia;                        // sqrt(ln2/pi)/a
+                    const float kg = (float)(0.6931471805599453 / 1.772453850905516027) * ia * ia;
+                    SIm = kKappa * g_h * S0 + kd * (b0.hi + b0.lo);
+                    Sam = kKappa * g_h * (a_h * (float)(1.0 / 0.6931471805599453)) * S1 - kd * ia * (b1.hi + b1.lo);
+                    Sgm = kKappa * (S0 + 2.f * g2 * (S1 - 4.f * S2)) + kg * (b2.hi + b2.lo);
+                }
+            } else if (PROF == XC_DOPPLER) {
+                // V = sqrt(ln2/pi)/a 2^(-u/a^2): sums of g 2^(-u/a^2) and g u 2^(-u/a^2)
+                const float ia2 = rcp_approx(a_h * a_h);
+                for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
+                    float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k8 + 32 * j;
+                        if (k <= kb) {
+                            const float d = (float)(k - na) - ff;
+                            const float u = d * d;
+                            const float e = ex2_approx(-u * ia2) * gc[k];
+                            q0 += e;
+                            q1 = fmaf(e, u, q1);
+                        }
+                    }
+                    K0.add(q0);
+                    K1.add(q1);
+                }
+                const F2 s0 = f2_warp_sum(F2{K0.s, -K0.c}), s1 = f2_warp_sum(F2{K1.s, -K1.c});
+                if (lane == c) {
+                    const float ia = rcp_approx(a_h);
+                    const float pd = kSqrtLn2OverPi * ia;
+                    const float S0 = s0.hi + s0.lo, S1 = s1.hi + s1.lo;
+                    SIm = pd * S0;
+                    Sam = pd * (-S0 * ia + (float)(2.0 * 0.6931471805599453) * ia2 * ia * S1);
+                    Sgm = 0.f;
+                }
+            } else {
+                // Lorentz: V = (1/pi) g/(u + g^2), dV/dg = (1/pi)(u - g^2)/(u + g^2)^2
+                const float g2 = g_h * g_h;
+                for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
+                    float q0 = 0.f, q2 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k8 + 32 * j;
+                        if (k <= kb) {
+                            const float d = (float)(k - na) - ff;
+                            const float u = d * d;
+                            const float r = rcp_approx(u + g2);
+                            const float gr = gc[k] * r;
+                            q0 += gr;
+                            q2 = fmaf(gr, (u - g2) * r, q2);
+                        }
+                    }
+                    K0.add(q0);
+                    K2.add(q2);
+                }
+                const F2 s0 = f2_warp_sum(F2{K0.s, -K0.c}), s2 = f2_warp_sum(F2{K2.s, -K2.c});
+                if (lane == c) {
+                    SIm = g_h * (float)(1.0 / kPi) * (s0.hi + s0.lo);
+                    Sam = 0.f;
+                    Sgm = (float)(1.0 / kPi) * (s2.hi + s2.lo);
+                }
+            }
+        }
+        // lane c: this line's contributions to its condition (grid-unit sums: sum g V = SI/h,
+        // sum g dV/dalpha = Sa/h^2, sum g dV/dgamma = Sg/h^2; alpha = a h, gamma = g h)
+        double lg = 0.0, ln = 0.0;
+        if (mine) {
+            const float IS = Is * Sgm;
+            accT += (double)(Is * (SIm * dlnI + Sam * ah * (0.5f * invT) - Sgm * ngh * invT));
+            accP += (double)(IS * fP * gq);
+            accS += (double)(IS * fS * gq);
+            accN += (double)(IS * gh * lnTr);
+            if (MIX) {
+#pragma unroll
+                for (int i = 0; i < VMAXB; ++i)
+                    if (i < nb) {
+                        const float t = IS * cc.pscale * gi[i];
+                        s_broad[warp][lane][2 * i] += (double)t;
+                        s_broad[warp][lane][2 * i + 1] += (double)(t * lnTr);
+                    }
+            } else {
+                lg = (double)(IS * cc.pscale * tn) * cc.inv_scale;            // x 1/h^2 below
+                ln = (double)(IS * gh * lnTr) * cc.inv_scale;                 // x 1/h below
+            }
+        }
+        if (!MIX && (p.d_gref_line || p.d_n_line)) {
+            for (int o = 1; o < nc; o <<= 1) {
+                lg += __shfl_xor_sync(0xffffffffu, lg, o);
+                ln += __shfl_xor_sync(0xffffffffu, ln, o);
+            }
+            if (lane == 0) {
+                const double ih = 1.0 / p.step;
+                lg *= ih * ih;
+                ln *= ih;
+                if (p.d_gref_line) p.d_gref_line[l] = p.accumulate ? p.d_gref_line[l] + lg : lg;
+                if (p.d_n_line) p.d_n_line[l] = p.accumulate ? p.d_n_line[l] + ln : ln;
+            }
+        }
+    }
+    const double sc = cc.inv_scale / p.step;   // the intensity scale and the common 1/h
+    if (mine) {
+        s_part[warp][lane][0] = accT * sc;
+        s_part[warp][lane][1] = accP * sc;
+        s_part[warp][lane][2] = accS * sc;
+        s_part[warp][lane][3] = accN * sc;
+        if (MIX)
+            for (int q = 0; q < 2 * nb; ++q) s_broad[warp][lane][q] *= sc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * NQ; i += blockDim.x) {
+        const int c = i / NQ, q = i % NQ;
+        double sum = 0.0;
+        for (int w = 0; w < VW; ++w) sum += q < 4 ? s_part[w][c][q] : s_broad[w][c][MIX ? q - 4 : 0];
+        p.block_part[((size_t)blockIdx.x * nc + c) * NQ + q] = sum;
+    }
+}
+
+typedef void (*VjpFn)(LinesDev, size_t, const CondDev *, int, double, double, int64_t, double, double,
+                      const double *, double *, double *, double *, int);
+
+static VjpFn pick(int prof) {
     switch (prof) {
-    case XC_DOPPLER: return f64 ? k_vjp_lines<XC_DOPPLER, true> : k_vjp_lines<XC_DOPPLER, false>;
-    case XC_LORENTZ: return f64 ? k_vjp_lines<XC_LORENTZ, true> : k_vjp_lines<XC_LORENTZ, false>;
-    default: return f64 ? k_vjp_lines<XC_VOIGT_W4, true> : k_vjp_lines<XC_VOIGT_W4, false>;
+    case XC_DOPPLER: return k_vjp_lines<XC_DOPPLER>;
+    case XC_LORENTZ: return k_vjp_lines<XC_LORENTZ>;
+    default: return k_vjp_lines<XC_VOIGT_W4>;
     }
 }
 
@@ -353,13 +664,18 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + VW - 1) / VW, (size_t)nsm * 8));
     // scratch: [grad sigma in device memory][f32 copy][block partials][per-cond acc][outputs]
+    //          FP32 path also: [per-line geometry n, f, ka, kb][line statistics][condition constants]
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     size_t o_g = host ? carve((size_t)nc * N * 8) : 0;
     size_t o_g32 = f64 ? 0 : carve((size_t)nc * N * 4);
-    size_t o_bp = carve((size_t)blocks * VMAXC * 4 * 8);
-    size_t o_acc = carve((size_t)nc * 2 * 8);
-    size_t o_out = host ? carve((size_t)(2 * nc + 2) * 8 + 2 * n * 8) : 0;
+    const int nb = a.L.n_broad, NQ = 4 + 2 * nb;
+    size_t o_bp = carve((size_t)blocks * VMAXC * NQ * 8);
+    size_t o_acc = carve((size_t)nc * (NQ - 2) * 8);
+    size_t o_out = host ? carve((size_t)(2 * nc + 2 + 2 * nb) * 8 + 2 * n * 8) : 0;
+    size_t o_geo = f64 ? 0 : carve(n * 16);
+    size_t o_gs = f64 ? 0 : carve(sizeof(GeomStats));
+    size_t o_cp = f64 ? 0 : carve((size_t)nc * sizeof(CParam));
     VJ_TRY(st->vjp_buf.ensure(off + 256));
     char *base = st->vjp_buf.as<char>();
     const double *g64 = a.grad_sigma;
@@ -369,17 +685,20 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
     }
     float *g32 = f64 ? nullptr : (float *)(base + o_g32);
     double *bp = (double *)(base + o_bp);
-    double *dS = (double *)(base + o_acc), *dN = dS + nc;
+    double *acc = (double *)(base + o_acc);   // per condition row: scale, n-shift, per-broadener sums
     double *dT = a.dT, *dP = a.dP, *ds = a.d_gamma_scale, *dn = a.d_n_shift;
     double *dgl = a.d_gamma_ref_line, *dnl = a.d_n_line;
+    double *dg0b = a.d_gamma0_broad, *dnb = a.d_n_broad;
     if (host) {
         double *o = (double *)(base + o_out);
         dT = o;
         dP = o + nc;
         ds = a.d_gamma_scale ? o + 2 * nc : nullptr;
         dn = a.d_n_shift ? o + 2 * nc + 1 : nullptr;
-        dgl = a.d_gamma_ref_line ? o + 2 * nc + 2 : nullptr;
-        dnl = a.d_n_line ? o + 2 * nc + 2 + n : nullptr;
+        dg0b = a.d_gamma0_broad ? o + 2 * nc + 2 : nullptr;
+        dnb = a.d_n_broad ? o + 2 * nc + 2 + nb : nullptr;
+        dgl = a.d_gamma_ref_line ? o + 2 * nc + 2 + 2 * nb : nullptr;
+        dnl = a.d_n_line ? o + 2 * nc + 2 + 2 * nb + n : nullptr;
     }
     if (a.timing) cudaEventRecord(a.ev_begin, s);
     if (nc == 0 || n == 0) {
@@ -389,21 +708,75 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
         }
         if (ds) VJ_TRY(cudaMemsetAsync(ds, 0, 8, s));
         if (dn) VJ_TRY(cudaMemsetAsync(dn, 0, 8, s));
+        if (dg0b && nb) VJ_TRY(cudaMemsetAsync(dg0b, 0, nb * 8, s));
+        if (dnb && nb) VJ_TRY(cudaMemsetAsync(dnb, 0, nb * 8, s));
+        if (dgl && n) VJ_TRY(cudaMemsetAsync(dgl, 0, n * 8, s));
+        if (dnl && n) VJ_TRY(cudaMemsetAsync(dnl, 0, n * 8, s));
+    } else if (f64) {
+        for (int c0 = 0; c0 < nc; c0 += VMAXC) {
+            int cc = std::min(VMAXC, nc - c0);
+            VjpFn fn = pick(a.opts.profile);
+            fn<<<blocks, VT, 0, s>>>(a.L, n, a.conds_dev + c0, cc, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
+                                     a.opts.width_mult, g64 + (size_t)c0 * N, bp, dgl, dnl, c0 > 0 ? 1 : 0);
+            k_vjp_finish<<<1, 128, 0, s>>>(bp, blocks, cc, NQ, c0, nullptr, dT, dP, acc);
+            *launches += 2;
+        }
+        k_vjp_scalars<<<1, 32, 0, s>>>(acc, nc, nb, ds, dn, dg0b, dnb);
+        ++*launches;
+        VJ_TRY(cudaGetLastError());
     } else {
-        if (!f64 && N) {
+        // FP32: the forward FP32 kernels' line geometry and condition constants, then the
+        // adjoint per chunk of <= 32 conditions (in order of profile width)
+        int *n_abs = (int *)(base + o_geo), *ka = n_abs + n, *kb = ka + n;
+        float *ffr = (float *)(kb + n);
+        GeomStats *gs = (GeomStats *)(base + o_gs);
+        CParam *cp = (CParam *)(base + o_cp);
+        if (N) {
             k_to_f32<<<nsm * 4, 256, 0, s>>>(g64, g32, (size_t)nc * N);
             ++*launches;
         }
+        VJ_TRY(launch_fp32_setup(a.L, n, a.conds_dev, nc, a.grid, a.opts.cutoff, n_abs, ffr, ka, kb, gs, cp, s));
+        *launches += 2;
         for (int c0 = 0; c0 < nc; c0 += VMAXC) {
-            int cc = std::min(VMAXC, nc - c0);
-            VjpFn fn = pick(a.opts.profile, f64);
-            fn<<<blocks, VT, 0, s>>>(a.L, n, a.conds_dev + c0, cc, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
-                                     a.opts.width_mult, g64 ? g64 + (size_t)c0 * N : nullptr,
-                                     g32 ? g32 + (size_t)c0 * N : nullptr, bp, dgl, dnl, c0 > 0 ? 1 : 0);
-            k_vjp_finish<<<1, 32, 0, s>>>(bp, blocks, cc, c0, dT, dP, dS, dN);
+            Vjp32Params vp;
+            vp.L = a.L;
+            vp.n = n;
+            vp.n_abs = n_abs;
+            vp.ka_abs = ka;
+            vp.kb_abs = kb;
+            vp.f_frac = ffr;
+            vp.cp = cp + c0;
+            vp.conds = a.conds_dev;
+            vp.nc = std::min(VMAXC, nc - c0);
+            vp.nu_A = a.grid.nu_A;
+            vp.step = a.grid.step;
+            vp.cutoff = a.opts.cutoff;
+            vp.width_mult = a.opts.width_mult;
+            vp.n_pts = a.grid.n;
+            vp.g32 = g32;
+            vp.block_part = bp;
+            vp.d_gref_line = dgl;
+            vp.d_n_line = dnl;
+            vp.accumulate = c0 > 0 ? 1 : 0;
+            const bool mix = nb > 0;
+            switch (a.opts.profile) {
+            case XC_DOPPLER:
+                if (mix) k_vjp32<XC_DOPPLER, true><<<blocks, VT, 0, s>>>(vp);
+                else k_vjp32<XC_DOPPLER, false><<<blocks, VT, 0, s>>>(vp);
+                break;
+            case XC_LORENTZ:
+                if (mix) k_vjp32<XC_LORENTZ, true><<<blocks, VT, 0, s>>>(vp);
+                else k_vjp32<XC_LORENTZ, false><<<blocks, VT, 0, s>>>(vp);
+                break;
+            default:
+                if (mix) k_vjp32<XC_VOIGT_W4, true><<<blocks, VT, 0, s>>>(vp);
+                else k_vjp32<XC_VOIGT_W4, false><<<blocks, VT, 0, s>>>(vp);
+                break;
+            }
+            k_vjp_finish<<<1, 128, 0, s>>>(bp, blocks, vp.nc, NQ, 0, cp + c0, dT, dP, acc);
             *launches += 2;
         }
-        k_vjp_scalars<<<1, 32, 0, s>>>(dS, dN, nc, ds, dn);
+        k_vjp_scalars<<<1, 32, 0, s>>>(acc, nc, nb, ds, dn, dg0b, dnb);
         ++*launches;
         VJ_TRY(cudaGetLastError());
     }
@@ -415,6 +788,8 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
         }
         if (a.d_gamma_scale) VJ_TRY(cudaMemcpyAsync(a.d_gamma_scale, ds, 8, cudaMemcpyDeviceToHost, s));
         if (a.d_n_shift) VJ_TRY(cudaMemcpyAsync(a.d_n_shift, dn, 8, cudaMemcpyDeviceToHost, s));
+        if (a.d_gamma0_broad && nb) VJ_TRY(cudaMemcpyAsync(a.d_gamma0_broad, dg0b, nb * 8, cudaMemcpyDeviceToHost, s));
+        if (a.d_n_broad && nb) VJ_TRY(cudaMemcpyAsync(a.d_n_broad, dnb, nb * 8, cudaMemcpyDeviceToHost, s));
         if (a.d_gamma_ref_line && n) VJ_TRY(cudaMemcpyAsync(a.d_gamma_ref_line, dgl, n * 8, cudaMemcpyDeviceToHost, s));
         if (a.d_n_line && n) VJ_TRY(cudaMemcpyAsync(a.d_n_line, dnl, n * 8, cudaMemcpyDeviceToHost, s));
         VJ_TRY(cudaStreamSynchronize(s));

@@ -141,3 +141,54 @@ def test_c5_seeded_subset_against_oracle(xc, oracle_lib):
         assert mr < tol and band < (1e-5 if prec == "fp32" else 1e-10)
     print(f"C5 1e6-line subset: FP32 max rel {res['fp32'][0]:.3g} band {res['fp32'][1]:.3g}; "
           f"FP64 max rel {res['fp64'][0]:.3g} band {res['fp64'][1]:.3g}")
+
+
+def test_c5_full_size(xc, oracle_lib):
+    """Mixed precision at maximum size: the whole 1e9-line list (nu in (0, 20000], 2000 K,
+    1 bar, 2 000 001 points, cut 25 cm^-1), generated on the device by the seeded
+    generator (about 28 GB), loaded and sorted by the library (about 52 GB more), and its
+    FP32 cross section checked against the FP64 oracle at sampled grid points.  The
+    oracle sees every line within the cut of each sampled point: their record numbers are
+    found from the generator's wavenumbers on the device and the records regenerated on
+    the host.  Tolerance 2e-4 relative."""
+    W = xs.WORKLOADS["C5"]
+    n = W.n_lines
+    free0 = torch.cuda.mem_get_info()[0]
+    if free0 < 140e9:
+        pytest.skip(f"needs about 140 GB of free device memory ({free0 / 1e9:.0f} GB free)")
+    dl = xs.gen_lines_torch(W.seed, 0, n, W.nu_lo, W.nu_hi, device="cuda:0")
+    E, g = xs.gen_states(W.seed, W.n_states)
+    c = xs.conditions_for(W)[0]
+    eng = xc.Engine(0)
+    eng.load_lines(dl)
+    eng.set_states(E, g)
+    nu = dl["nu"]
+    for k in [k for k in dl if k != "nu"]:
+        del dl[k]
+    torch.cuda.empty_cache()
+    grid = xc.make_grid(W.grid_lo, W.step, W.n_points)
+    cond = xc.make_condition(c["T"], c["P"], mass_da=W.mass_da)
+    sig = torch.empty((1, W.n_points), dtype=torch.float64, device="cuda:0")
+    eng.cross_section_batched([cond], grid, xc.make_opts("voigt_w4", "fp32", W.cutoff), sig)
+    s32 = sig[0].cpu().numpy()
+    evals = eng.count_evals([cond], grid, xc.make_opts("voigt_w4", "fp32", W.cutoff))
+    assert 0.99 * n * 5001 < evals <= n * 5001
+    eng.close()
+    assert np.all(s32 >= 0) and np.all(np.isfinite(s32))
+    # the lines within the cut of the sampled points, by record number
+    ks = _sample_points(W.n_points, 5, m=8)
+    idx = []
+    for k in ks:
+        x = W.grid_lo + k * W.step
+        sel = torch.nonzero((nu >= x - W.cutoff - 0.01) & (nu <= x + W.cutoff + 0.01)).flatten()
+        idx.append(sel.cpu().numpy())
+    del nu
+    torch.cuda.empty_cache()
+    idx = np.unique(np.concatenate(idx))
+    S = xs.gen_lines_at(W.seed, idx, W.nu_lo, W.nu_hi)
+    o = np.argsort(S["nu"], kind="stable")
+    S = {key: v[o] for key, v in S.items()}
+    err = _check(oracle_lib, S, E, g, W, c, s32, ks, "voigt_w4", 2e-4)
+    print(f"C5 full size (1e9 lines, {evals:.4g} evals): FP32 worst sampled relative error {err:.3g} "
+          f"({len(idx)} lines near {len(ks)} points)")
+    assert err < 2e-4

@@ -506,9 +506,10 @@ def test_broadener_mixture(eng, xc, oracle_lib):
     for prec, tol in (("fp64", TOL64), ("fp32", TOL32)):
         got = eng.cross_section(conds[5], grid, xc.make_opts("voigt_w4", prec, 25.0, 200.0))
         assert metrics(got, r)[0] < tol, prec
-    # the adjoint refuses a mixture; an empty mixture returns to the lines' own widths
+    # under a mixture the adjoint has no per-line gradients of the line list's widths (EINVAL);
+    # an empty mixture returns to the lines' own widths
     with pytest.raises(xc.XcError):
-        eng.cross_section_vjp(conds[:1], grid, xc.make_opts("voigt_w4", "fp64", cut), np.ones((1, n)))
+        eng.cross_section_vjp(conds[:1], grid, xc.make_opts("voigt_w4", "fp64", cut), np.ones((1, n)), per_line=True)
     eng.set_broadening([])
     plain = eng.cross_section(conds[0], grid, xc.make_opts("voigt_w4", "fp64", cut))
     r0 = oracle_sigma(oracle_lib, L, E, g, TP[0][0], TP[0][1], nu_A, step, n, "voigt_w4", cut)

@@ -80,6 +80,61 @@ def test_vjp_matches_oracle_gradient(eng, xc, oracle_lib, profile, precision):
         assert v < tol, (k, v)
 
 
+W_LINES_C4 = xs.WORKLOADS["C4"].n_lines
+
+
+@pytest.mark.parametrize("profile", ["voigt_w4", "lorentz", "doppler"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vjp_broadener_mixture_matches_oracle(eng, xc, oracle_lib, profile, precision):
+    """The adjoint under a mixture of .broad broadeners (an a0 table, an a1 table and a
+    constant; Secs. "Broadening parameters", "Mixtures of broadeners"): dT, dP, the global
+    scalars and the per-broadener gradients (a factor on each broadener's gamma_0 values,
+    a shift of its n values) against the oracle's, and the same scalars through the
+    plain entry point.  Positive weights for FP32 as in the test above.  Tolerance
+    1e-8 (FP64) and 1e-4 (FP32) relative."""
+    L = xs.gen_lines(205, 0, 2000, 1000.0, 1015.0)
+    E, g = xs.gen_states(205, 1000)
+    j_up = (L["g_up"].astype(np.int32) - 1) // 2
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    S = eng.get_lines()
+    perm = eng.get_permutation()
+    a0 = {j: (0.09 - 0.0011 * j, 0.75 - 0.004 * j) for j in range(0, 60, 2)}
+    a1 = {(j, j + 1): (0.05 + 0.0007 * j, 0.6) for j in range(0, 60, 3)}
+    spec = [("a0", 0.5, 0.07, 0.5, a0), ("a1", 0.3, 0.03, 0.7, a1), ("constant", 0.2, 0.04, 0.65, None)]
+    eng.set_broadening([xc.make_broadener(*sp) for sp in spec], j_up=j_up)
+    ob = [oracle_lib.make_broadener(*sp) for sp in spec]
+    nu_A, step, n, cut = 995.0, 0.01, 2501, 2.0
+    TP = [(800.0, 0.1), (1600.0, 1.0), (2400.0, 0.3)]
+    rng = np.random.default_rng(7)
+    gs = rng.standard_normal((len(TP), n)) if precision == "fp64" else 0.5 + rng.random((len(TP), n))
+    conds = [xc.make_condition(T, P, gamma_scale=1.0, n_shift=0.01) for T, P in TP]
+    opts = xc.make_opts(profile, precision, cut)
+    try:
+        r = eng.cross_section_vjp_broadening(conds, xc.make_grid(nu_A, step, n), opts, gs, len(spec))
+        r2 = eng.cross_section_vjp(conds, xc.make_grid(nu_A, step, n), opts, gs, per_line=False)
+    finally:
+        eng.set_broadening([])
+    oc = []
+    for T, P in TP:
+        Q, dQ = oracle_lib.partition_function(E, g, T)
+        oc.append(oracle_lib.make_condition(T, P, Q, dQ, gamma_scale=1.0, n_shift=0.01))
+    ref = oracle_lib.cross_section_vjp_broad(S, j_up[perm], ob, oc, nu_A, step, n, oracle_lib.make_opts(profile, cut),
+                                             gs)
+    tol = 1e-8 if precision == "fp64" else 1e-4
+    errs = {"dT": _rel(r["dT"], ref["dT"])}
+    if profile != "doppler":
+        errs.update(dP=_rel(r["dP"], ref["dP"]), ds=_rel(r["d_gamma_scale"], [ref["d_gamma_scale"]]),
+                    dn=_rel(r["d_n_shift"], [ref["d_n_shift"]]),
+                    dg0=_rel(r["d_gamma0_broad"], ref["d_gamma0_broad"]),
+                    dnb=_rel(r["d_n_broad"], ref["d_n_broad"]))
+        errs["plain entry"] = max(_rel(r2["dT"], r["dT"]), _rel(r2["dP"], r["dP"]),
+                                  _rel(r2["d_gamma_scale"], r["d_gamma_scale"]))
+    print("mixture", profile, precision, {k: f"{v:.2g}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < tol, (k, v)
+
+
 def _c4_problem(xc, eng, n_lines, seed_off=0):
     W = xs.WORKLOADS["C4"]
     L = xs.gen_lines(W.seed + seed_off, 0, n_lines, W.nu_lo, W.nu_hi)
@@ -133,6 +188,49 @@ def test_vjp_c4_against_central_differences(eng, xc):
     for r in (r64, r32):
         assert float(r["d_gamma_scale"][0]) == pytest.approx(fds, rel=1e-4, abs=0)
         assert float(r["d_n_shift"][0]) == pytest.approx(fdn, rel=1e-4, abs=0)
+
+
+def test_vjp_c4_full_size_against_central_differences(eng, xc):
+    """The differentiation workload at its full size: 1e7 lines (C1 generator and grid,
+    200001 points, cut 25 cm^-1), T in {800, 1600} K x P in {0.1, 1} bar, the loss
+    sum (sigma - sigma_target)^2 with the target from T x 1.03 and gamma_ref x 1.05.
+    The FP32 adjoint is compared with central differences (h = 1e-4 relative) of the
+    FP64 forward: dL/dT_c and dL/dP_c for the two extreme conditions (only sigma_c
+    depends on them, so each difference needs that condition's forward alone), and the
+    global dL/d(gamma_scale) and dL/d(n_shift).  Tolerance 1e-4 relative."""
+    W, L, E, g, grid, TP = _c4_problem(xc, eng, W_LINES_C4)
+    o64 = xc.make_opts("voigt_w4", "fp64", 25.0)
+    o32 = xc.make_opts("voigt_w4", "fp32", 25.0)
+    dev = "cuda:0"
+    nc = len(TP)
+    tgt = torch.zeros((nc, grid.n), dtype=torch.float64, device=dev)
+    eng.cross_section_batched([xc.make_condition(T * 1.03, P, gamma_scale=1.05) for T, P in TP], grid, o64, tgt)
+    s0 = torch.zeros_like(tgt)
+    eng.cross_section_batched([xc.make_condition(T, P) for T, P in TP], grid, o64, s0)
+    gsig = 2.0 * (s0 - tgt)
+    r32 = eng.cross_section_vjp([xc.make_condition(T, P) for T, P in TP], grid, o32, gsig, per_line=False)
+    one = torch.zeros((1, grid.n), dtype=torch.float64, device=dev)
+
+    def loss_c(c, T, P, s=1.0, dn=0.0):   # condition c's part of the loss
+        eng.cross_section_batched([xc.make_condition(T, P, gamma_scale=s, n_shift=dn)], grid, o64, one)
+        return float(((one[0] - tgt[c]) ** 2).sum())
+
+    h = 1e-4
+    report = {}
+    for c in (0, nc - 1):
+        T, P = TP[c]
+        fdT = (loss_c(c, T * (1 + h), P) - loss_c(c, T * (1 - h), P)) / (2 * h * T)
+        fdP = (loss_c(c, T, P * (1 + h)) - loss_c(c, T, P * (1 - h))) / (2 * h * P)
+        report[f"dT{c}"] = (float(r32["dT"][c]), fdT)
+        report[f"dP{c}"] = (float(r32["dP"][c]), fdP)
+    fds = sum(loss_c(c, T, P, s=1 + h) - loss_c(c, T, P, s=1 - h) for c, (T, P) in enumerate(TP)) / (2 * h)
+    fdn = sum(loss_c(c, T, P, dn=h) - loss_c(c, T, P, dn=-h) for c, (T, P) in enumerate(TP)) / (2 * h)
+    report["d_gamma_scale"] = (float(r32["d_gamma_scale"][0]), fds)
+    report["d_n_shift"] = (float(r32["d_n_shift"][0]), fdn)
+    print("C4 full size, FP32 adjoint vs central differences:",
+          {k: f"{abs(a - b) / abs(b):.2g}" for k, (a, b) in report.items()})
+    for k, (a, b) in report.items():
+        assert a == pytest.approx(b, rel=1e-4, abs=0), (k, a, b)
 
 
 def test_vjp_c4_subset_against_oracle(eng, xc, oracle_lib):
