@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 form on a subset")
     ap.add_argument("--profile", default=None, help="override the workload's line profile")
     ap.add_argument("--no-extras", action="store_true", help="skip the C1/C2/C4 secondary timings")
+    ap.add_argument("--step", default="forward", choices=["forward", "adjoint"],
+                    help="adjoint: time the FP32 adjoint of the workload (a seeded dL/dsigma) as the step instead "
+                         "of load + cross sections (for profiling the adjoint kernel)")
     return ap.parse_args()
 
 
@@ -385,6 +388,28 @@ def c5_measurement(xc, torch, dev):
     return out
 
 
+def run_adjoint_step(args, eng, dlines, conds, grid, opts, torch, dev, W, n):
+    """The FP32 adjoint as the timed step (lines resident and sorted; a seeded dL/dsigma):
+    one JSON line with its evals/s, for profiling the adjoint kernel."""
+    eng.load_lines(dlines)
+    gs = torch.from_numpy(np.random.default_rng(9).standard_normal((len(conds), W.n_points))).to(dev)
+    evals = eng.count_evals(conds, grid, opts)
+    for _ in range(args.warmup):
+        eng.cross_section_vjp(conds, grid, opts, gs, per_line=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        eng.cross_section_vjp(conds, grid, opts, gs, per_line=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "adjoint (VJP) line x gridpoint evals/s, FP32", "value": evals / (ms / 1e3),
+                      "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": f"{W.name}: {n} lines, {len(conds)} conditions, {W.n_points} points, "
+                                             f"adjoint with per-line outputs"}}), flush=True)
+
+
 def run_xc(args, dist, rank, world, local):
     import torch
     import paper_1801_09803_gb300 as xc
@@ -411,6 +436,10 @@ def run_xc(args, dist, rank, world, local):
     def step_device():
         eng.load_lines(dlines)
         eng.cross_section_batched(conds, grid, opts, sigma)
+
+    if args.step == "adjoint":
+        run_adjoint_step(args, eng, dlines, conds, grid, opts, torch, dev, W, n)
+        return
 
     # algorithmic work: pairs (line, grid point) inside the cut, summed over conditions
     eng.load_lines(dlines)

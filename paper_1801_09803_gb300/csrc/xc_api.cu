@@ -862,8 +862,9 @@ static xc_status vjp_common(xc_handle *h, const xc_condition *conds, size_t n_co
     xc_status st = check_handle(h);
     if (st) return st;
     if ((st = check_grid(grid)) || (st = check_opts(opts)) || (st = check_conds(conds, n_cond, h))) return st;
-    if (opts->profile != XC_DOPPLER && opts->profile != XC_LORENTZ && opts->profile != XC_VOIGT_W4) {
-        set_error("the adjoint supports Doppler, Lorentz and Voigt-w4 profiles");
+    if (opts->profile != XC_DOPPLER && opts->profile != XC_LORENTZ && opts->profile != XC_VOIGT_W4 &&
+        opts->profile != XC_VOIGT_GH_BINNED) {
+        set_error("the adjoint supports Doppler, Lorentz, Voigt-w4 and binned Gauss-Hermite profiles");
         return XC_EUNSUPPORTED;
     }
     if (opts->quantity != XC_ABSORPTION || opts->threshold != XC_THRESHOLD_NONE) {
@@ -902,6 +903,11 @@ static xc_status vjp_common(xc_handle *h, const xc_condition *conds, size_t n_co
     a.d_n_line = d_n_line;
     a.d_gamma0_broad = d_gamma0_broad;
     a.d_n_broad = d_n_broad;
+    if (opts->profile == XC_VOIGT_GH_BINNED) {
+        if ((st = ensure_gh(h, opts->n_gh, s))) return st;
+        a.ghx = h->gh.as<double>();
+        a.ghw = a.ghx + 64;
+    }
     a.timing = h->timing;
     a.ev_begin = h->ev[2 * ST_VJP];
     a.ev_end = h->ev[2 * ST_VJP + 1];

@@ -98,6 +98,7 @@ struct VjpArgs {
     double *dT = nullptr, *dP = nullptr, *d_gamma_scale = nullptr, *d_n_shift = nullptr;
     double *d_gamma_ref_line = nullptr, *d_n_line = nullptr;
     double *d_gamma0_broad = nullptr, *d_n_broad = nullptr;   // per broadener of a mixture (nullable)
+    const double *ghx = nullptr, *ghw = nullptr;               // Gauss-Hermite nodes (binned GH), device
     bool timing = false;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
 };

@@ -137,12 +137,37 @@ __device__ inline void prof_deriv64(double D, double al, double ga, double *V, d
     }
 }
 
+// Bin average of the Gauss-Hermite Voigt, Eq. (e:sigma:quad), over [D - h/2, D + h/2] and its
+// derivatives.  Per node j, s+- = D +- h/2 - alpha x_j/sqrt(ln2), Q+- = s+-^2 + gamma^2:
+//   atan(s+/gamma) - atan(s-/gamma) = atan2(gamma h, gamma^2 + s+ s-),
+//   d/dgamma = -s+/Q+ + s-/Q- = h (s+ s- - gamma^2)/(Q+ Q-),
+//   d/dalpha = (x_j/sqrt(ln2)) gamma (1/Q- - 1/Q+) = (x_j/sqrt(ln2)) gamma h (s+ + s-)/(Q+ Q-),
+// the right-hand forms free of the cancellation of the differences in the far wings.
+__device__ inline void gh_binned_deriv64(double D, double h, double al, double ga, const double *x, const double *w,
+                                         int n, double *V, double *dVa, double *dVg) {
+    double v = 0.0, da = 0.0, dg = 0.0;
+    const double g2 = ga * ga;
+    for (int j = 0; j < n; ++j) {
+        const double xs = x[j] / kSqrtLn2;
+        const double sp = D + 0.5 * h - al * xs, sm = sp - h;
+        const double iQ = 1.0 / ((sp * sp + g2) * (sm * sm + g2));
+        v += w[j] * atan2(ga * h, g2 + sp * sm);
+        dg += w[j] * h * (sp * sm - g2) * iQ;
+        da += w[j] * xs * ga * h * (sp + sm) * iQ;
+    }
+    const double k = 1.0 / (kPi * kSqrtPi * h);
+    *V = v * k;
+    *dVa = da * k;
+    *dVg = dg * k;
+}
+
 template <int PROF>
 __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const CondDev *__restrict__ conds, int nc,
                                                   double nu_A, double step, int64_t n_pts, double cutoff,
                                                   double width_mult, const double *__restrict__ g64,
                                                   double *block_part /*[blk][nc][4 + 2 nb]*/, double *d_gref_line,
-                                                  double *d_n_line, int accumulate) {
+                                                  double *d_n_line, int accumulate, const double *ghx,
+                                                  const double *ghw, int ngh) {
     __shared__ double s_part[VW][VMAXC][4];
     __shared__ double s_broad[VW][VMAXC][2 * VMAXB];   // mixture: per broadener, scale and n-shift sums
     const int nb = L.n_broad, NQ = 4 + 2 * nb;
@@ -164,7 +189,10 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
             for (int64_t k = ka + lane; k <= kb; k += 32) {
                 double D = __dsub_rn(grid_x(nu_A, step, k), nu);
                 double V, dVa, dVg;
-                prof_deriv64<PROF>(D, al, ga, &V, &dVa, &dVg);
+                if (PROF == XC_VOIGT_GH_BINNED)
+                    gh_binned_deriv64(D, step, al, ga, ghx, ghw, ngh, &V, &dVa, &dVg);
+                else
+                    prof_deriv64<PROF>(D, al, ga, &V, &dVa, &dVg);
                 double g = g64[(size_t)c * n_pts + k];
                 SI += g * V;
                 Sa += g * dVa;
@@ -382,6 +410,8 @@ struct Vjp32Params {
     double *block_part;                   // [block][nc][4 + 2 nb]
     double *d_gref_line, *d_n_line;       // per line (sorted order), nullable
     int accumulate;                       // add to the per-line outputs (later condition chunks)
+    const double *ghx, *ghw;              // Gauss-Hermite nodes and weights (binned GH), device
+    int ngh;
 };
 
 // MIX: the Lorentz widths come from the handle's mixture of broadeners (per broadener
@@ -393,7 +423,16 @@ template <int PROF, bool MIX>
 __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
     __shared__ double s_part[VW][VMAXC][4];
     __shared__ double s_broad[VW][VMAXC][MIX ? 2 * VMAXB : 1];
+    __shared__ float s_gx[PROF == XC_VOIGT_GH_BINNED ? 64 : 1], s_gw[PROF == XC_VOIGT_GH_BINNED ? 64 : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (PROF == XC_VOIGT_GH_BINNED) {
+        // the node shifts x_j / sqrt(ln2) (in units of the Doppler width) and the weights
+        for (int j = threadIdx.x; j < p.ngh; j += blockDim.x) {
+            s_gx[j] = (float)(p.ghx[j] / kSqrtLn2);
+            s_gw[j] = (float)p.ghw[j];
+        }
+        __syncthreads();
+    }
     const int nc = p.nc;
     const int nb = MIX ? p.L.n_broad : 0, NQ = 4 + 2 * nb;
     if (MIX)
@@ -518,6 +557,47 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                     Sam = kKappa * g_h * (a_h * (float)(1.0 / 0.6931471805599453)) * S1 - kd * ia * (b1.hi + b1.lo);
                     Sgm = kKappa * (S0 + 2.f * g2 * (S1 - 4.f * S2)) + kg * (b2.hi + b2.lo);
                 }
+            } else if (PROF == XC_VOIGT_GH_BINNED) {
+                // bin average of the Gauss-Hermite Voigt (Eq. e:sigma:quad), grid units (bin width 1):
+                // per node j, s+ = delta + 1/2 - a x_j/sqrt(ln2), s- = s+ - 1, Q+- = s+-^2 + g^2,
+                //   V = pi^(-3/2) sum_j w_j atan2(g, g^2 + s+ s-),
+                //   dV/dg = pi^(-3/2) sum_j w_j (s+ s- - g^2)/(Q+ Q-),
+                //   dV/da = pi^(-3/2) sum_j w_j (x_j/sqrt(ln2)) g (s+ + s-)/(Q+ Q-)
+                const float g2 = g_h * g_h;
+                const int ngh = p.ngh;
+                for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
+                    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll 2
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k8 + 32 * j;
+                        if (k <= kb) {
+                            const float d = (float)(k - na) - ff + 0.5f;
+                            float v = 0.f, da = 0.f, dg = 0.f;
+                            for (int m = 0; m < ngh; ++m) {
+                                const float sp = fmaf(-a_h, s_gx[m], d), sm = sp - 1.f;
+                                const float iQ = rcp_approx(fmaf(sp, sp, g2) * fmaf(sm, sm, g2));
+                                v = fmaf(s_gw[m], atan2f(g_h, fmaf(sp, sm, g2)), v);
+                                dg = fmaf(s_gw[m], fmaf(sp, sm, -g2) * iQ, dg);
+                                da = fmaf(s_gw[m] * s_gx[m], (sp + sm) * iQ, da);
+                            }
+                            const float gk = gc[k];
+                            q0 = fmaf(gk, v, q0);
+                            q1 = fmaf(gk, da, q1);
+                            q2 = fmaf(gk, dg, q2);
+                        }
+                    }
+                    K0.add(q0);
+                    K1.add(q1);
+                    K2.add(q2);
+                }
+                const F2 s0 = f2_warp_sum(F2{K0.s, -K0.c}), s1 = f2_warp_sum(F2{K1.s, -K1.c});
+                const F2 s2 = f2_warp_sum(F2{K2.s, -K2.c});
+                if (lane == c) {
+                    constexpr float kpi = (float)(1.0 / (3.141592653589793 * 1.772453850905516));   // pi^(-3/2)
+                    SIm = kpi * (s0.hi + s0.lo);
+                    Sam = kpi * g_h * (s1.hi + s1.lo);
+                    Sgm = kpi * (s2.hi + s2.lo);
+                }
             } else if (PROF == XC_DOPPLER) {
                 // V = sqrt(ln2/pi)/a 2^(-u/a^2): sums of g 2^(-u/a^2) and g u 2^(-u/a^2)
                 const float ia2 = rcp_approx(a_h * a_h);
@@ -629,12 +709,13 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
 }
 
 typedef void (*VjpFn)(LinesDev, size_t, const CondDev *, int, double, double, int64_t, double, double,
-                      const double *, double *, double *, double *, int);
+                      const double *, double *, double *, double *, int, const double *, const double *, int);
 
 static VjpFn pick(int prof) {
     switch (prof) {
     case XC_DOPPLER: return k_vjp_lines<XC_DOPPLER>;
     case XC_LORENTZ: return k_vjp_lines<XC_LORENTZ>;
+    case XC_VOIGT_GH_BINNED: return k_vjp_lines<XC_VOIGT_GH_BINNED>;
     default: return k_vjp_lines<XC_VOIGT_W4>;
     }
 }
@@ -717,7 +798,8 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
             int cc = std::min(VMAXC, nc - c0);
             VjpFn fn = pick(a.opts.profile);
             fn<<<blocks, VT, 0, s>>>(a.L, n, a.conds_dev + c0, cc, a.grid.nu_A, a.grid.step, a.grid.n, a.opts.cutoff,
-                                     a.opts.width_mult, g64 + (size_t)c0 * N, bp, dgl, dnl, c0 > 0 ? 1 : 0);
+                                     a.opts.width_mult, g64 + (size_t)c0 * N, bp, dgl, dnl, c0 > 0 ? 1 : 0, a.ghx,
+                                     a.ghw, a.opts.n_gh);
             k_vjp_finish<<<1, 128, 0, s>>>(bp, blocks, cc, NQ, c0, nullptr, dT, dP, acc);
             *launches += 2;
         }
@@ -758,6 +840,9 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
             vp.d_gref_line = dgl;
             vp.d_n_line = dnl;
             vp.accumulate = c0 > 0 ? 1 : 0;
+            vp.ghx = a.ghx;
+            vp.ghw = a.ghw;
+            vp.ngh = a.opts.n_gh;
             const bool mix = nb > 0;
             switch (a.opts.profile) {
             case XC_DOPPLER:
@@ -767,6 +852,10 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
             case XC_LORENTZ:
                 if (mix) k_vjp32<XC_LORENTZ, true><<<blocks, VT, 0, s>>>(vp);
                 else k_vjp32<XC_LORENTZ, false><<<blocks, VT, 0, s>>>(vp);
+                break;
+            case XC_VOIGT_GH_BINNED:
+                if (mix) k_vjp32<XC_VOIGT_GH_BINNED, true><<<blocks, VT, 0, s>>>(vp);
+                else k_vjp32<XC_VOIGT_GH_BINNED, false><<<blocks, VT, 0, s>>>(vp);
                 break;
             default:
                 if (mix) k_vjp32<XC_VOIGT_W4, true><<<blocks, VT, 0, s>>>(vp);

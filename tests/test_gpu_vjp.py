@@ -40,7 +40,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
 
 
-@pytest.mark.parametrize("profile", ["voigt_w4", "doppler", "lorentz"])
+@pytest.mark.parametrize("profile", ["voigt_w4", "doppler", "lorentz", "voigt_gh_binned"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_vjp_matches_oracle_gradient(eng, xc, oracle_lib, profile, precision):
     L = xs.gen_lines(201, 0, 3000, 1000.0, 1020.0)
@@ -83,7 +83,7 @@ def test_vjp_matches_oracle_gradient(eng, xc, oracle_lib, profile, precision):
 W_LINES_C4 = xs.WORKLOADS["C4"].n_lines
 
 
-@pytest.mark.parametrize("profile", ["voigt_w4", "lorentz", "doppler"])
+@pytest.mark.parametrize("profile", ["voigt_w4", "lorentz", "doppler", "voigt_gh_binned"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_vjp_broadener_mixture_matches_oracle(eng, xc, oracle_lib, profile, precision):
     """The adjoint under a mixture of .broad broadeners (an a0 table, an a1 table and a
