@@ -635,8 +635,10 @@ __device__ __forceinline__ void w4_series_pair(f32x2 (&acc)[R / 2][CG], int c, c
     }
 }
 
-template <int PROF, int R, int CG, bool EXT = true>
-__global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherParams p) {
+// TCN: compiled for the near pairs of the tensor-core sweep only (p.tc_far set): the code
+// of the other modes is left out, which frees registers for more resident warps
+template <int PROF, int R, int CG, bool EXT = true, bool TCN = false>
+__global__ void __launch_bounds__(GT, (TCN ? (CG >= 16 ? 2 : 3) : (CG >= 16 ? 1 : 2))) k_gather_f32(GatherParams p) {
     constexpr unsigned kAllConds = CG >= 32 ? 0xffffffffu : ((1u << CG) - 1u);
     using Lay = SmemLayout<PROF, R, CG>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                     float4 S = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
                     if (cc < p.n_cond) {
                         line_consts<PROF, EXT>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
-                                          &t2, &S, p.tc_far != 0);
+                                          &t2, &S, TCN || p.tc_far != 0);
                     } else {  // padding condition: contributes exactly 0
                         if (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV) A = make_float4(1.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
             // ---- evaluate: classify lines for this warp's span, then accumulate
             for (int ib = 0; ib < cnt; ib += 32) {
                 int i = ib + lane;
-                if (PROF == XC_VOIGT_W4 && p.tc_far) {
+                if (PROF == XC_VOIGT_W4 && (TCN || p.tc_far)) {
                     // The far-wing kernel took every (line, condition) with span_far on this
                     // 128-point span; the rest here, region I only: pairs of lines that cover
                     // the span with no centre-zone point (packed, shared reciprocal), the
@@ -1078,12 +1080,12 @@ __global__ void __launch_bounds__(GT, (CG >= 16 ? 1 : 2)) k_gather_f32(GatherPar
                 }
             }
             if (++chunk == FOLD_CHUNKS) {
-                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !p.tc_far);
+                fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !TCN && !p.tc_far);
                 first_fold = false;
                 chunk = 0;
             }
         }
-        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !p.tc_far);
+        fold_acc<R, CG>(acc, ji, kw, grp, p, sScale, sRow, first_fold && !TCN && !p.tc_far);
     }
 }
 
@@ -1718,10 +1720,14 @@ struct Variant {
     GatherFn fn;
     size_t smem;
     bool ext;   // honours the per-(line, condition) options (see line_consts)
+    bool tcn;   // the near-pair kernel of the tensor-core sweep (and nothing else)
 };
 
-#define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, true>, SmemLayout<P, R, CG>::total, true}
-#define XC_VARIANT_PLAIN(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, false>, SmemLayout<P, R, CG>::total, false}
+#define XC_VARIANT(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, true>, SmemLayout<P, R, CG>::total, true, false}
+#define XC_VARIANT_PLAIN(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, false>, SmemLayout<P, R, CG>::total, false, false}
+#define XC_VARIANT_TCN(P, R, CG) {P, R, CG, k_gather_f32<P, R, CG, true, true>, SmemLayout<P, R, CG>::total, true, true}
+#define XC_VARIANT_PLAIN_TCN(P, R, CG) \
+    {P, R, CG, k_gather_f32<P, R, CG, false, true>, SmemLayout<P, R, CG>::total, false, true}
 static const Variant kVariants[] = {
     // Voigt w4: the plain hot kernels, and the shapes that carry the per-(line, condition) options
     XC_VARIANT_PLAIN(XC_VOIGT_W4, 4, 16), XC_VARIANT_PLAIN(XC_VOIGT_W4, 2, 32), XC_VARIANT_PLAIN(XC_VOIGT_W4, 4, 8),
@@ -1729,6 +1735,9 @@ static const Variant kVariants[] = {
     XC_VARIANT_PLAIN(XC_VOIGT_W4, 8, 1),
     XC_VARIANT(XC_VOIGT_W4, 4, 16), XC_VARIANT(XC_VOIGT_W4, 4, 8), XC_VARIANT(XC_VOIGT_W4, 8, 4),
     XC_VARIANT(XC_VOIGT_W4, 8, 1),
+    // the near pairs of the tensor-core sweep (128-point spans: R = 4)
+    XC_VARIANT_PLAIN_TCN(XC_VOIGT_W4, 4, 16), XC_VARIANT_PLAIN_TCN(XC_VOIGT_W4, 4, 8),
+    XC_VARIANT_TCN(XC_VOIGT_W4, 4, 16), XC_VARIANT_TCN(XC_VOIGT_W4, 4, 8),
     XC_VARIANT(XC_LORENTZ, 4, 16),  XC_VARIANT(XC_LORENTZ, 8, 8),   XC_VARIANT(XC_LORENTZ, 8, 4),
     XC_VARIANT(XC_LORENTZ, 8, 1),
     XC_VARIANT(XC_DOPPLER, 4, 16),  XC_VARIANT(XC_DOPPLER, 8, 4),   XC_VARIANT(XC_DOPPLER, 8, 1),
@@ -2176,7 +2185,7 @@ xc_status autotune(BatchedState *st, const BatchedArgs &a, int nc, TileCfg *out,
                 if (v.CG > 1 && v.CG > 2 * nc) continue;          // no more than half the group padded
                 if (v.CG < std::min(nc, 8)) continue;              // enough conditions share each staged line
             }
-            if (tc && v.R != 4) continue;  // spans of 128 points = the far-wing kernel's blocks
+            if (v.tcn != tc) continue;     // with the far wings on the tensor cores: the near-pair kernels
             if (st->force_R > 0 && (v.R != st->force_R || v.CG != st->force_CG)) continue;
             cands.push_back(i);
         }
@@ -2569,11 +2578,11 @@ extern "C" xc_status xc_cross_section_batched_static(const xc_lines *lines, size
     const Variant *v = nullptr;
     int want_cg = nc >= 16 ? 16 : (nc >= 8 ? 8 : (nc >= 4 ? 4 : 1));
     for (int i = 0; i < kNumVariants && !v; ++i)
-        if (kVariants[i].profile == opts->profile && kVariants[i].CG == want_cg &&
+        if (kVariants[i].profile == opts->profile && kVariants[i].CG == want_cg && !kVariants[i].tcn &&
             (kVariants[i].profile != XC_VOIGT_W4 || !kVariants[i].ext))   // no per-(line, condition) options here
             v = &kVariants[i];
     for (int i = 0; i < kNumVariants && !v; ++i)  // profiles compiled with fewer group sizes
-        if (kVariants[i].profile == opts->profile && kVariants[i].CG <= want_cg) v = &kVariants[i];
+        if (kVariants[i].profile == opts->profile && kVariants[i].CG <= want_cg && !kVariants[i].tcn) v = &kVariants[i];
     if (!v) { set_error("no kernel variant for this profile"); return XC_EUNSUPPORTED; }
     xc_status st = configure_variant(v, dev);
     if (st) return st;
