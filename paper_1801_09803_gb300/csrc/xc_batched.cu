@@ -492,6 +492,13 @@ __device__ __noinline__ float w4_value_f32(float delta, const float4 &B) {
     return B.z * w.re;
 }
 
+// Re w in w4's region I from (x, y): 0.5641896 y (0.5 + X + Y) / ((X + Y - 0.5)^2 + 2Y)
+__device__ __forceinline__ float w4_region1_re(float x, float y) {
+    float X = x * x, Y = y * y;
+    float t = X + Y - 0.5f;
+    return 0.5641896f * y * (0.5f + X + Y) * rcp_approx(fmaf(t, t, 2.f * Y));
+}
+
 template <int PROF>
 __device__ __forceinline__ float contrib_single(float u, float delta, const float4 &A, const float4 &B,
                                                 const float *s_x, const float *s_w, int ngh) {
@@ -512,8 +519,14 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
         }
         return A.z * s;
     } else if (PROF == XC_VOIGT_VV) {
-        // Eq. (e:fast-v): the line's own Voigt in the exact zone, the reference wing beyond it
-        return fabsf(delta) <= A.w ? w4_value_f32(delta, B) : w4_value_f32(delta, make_float4(A.x, A.y, A.z, 0.f));
+        // Eq. (e:fast-v): the line's own Voigt in the exact zone, the reference wing beyond it.
+        // Both are w4 Voigts; where |x| + y >= 15 (the whole reference wing, whose Doppler
+        // width alpha/nu is tiny, and most of the exact zone) w4 is its region-I rational,
+        // evaluated in real form; the full w4 only for the few points nearer the centre
+        const bool wing = fabsf(delta) > A.w;
+        const float a = wing ? A.x : B.x, y = wing ? A.y : B.y, P = wing ? A.z : B.z;
+        const float x = a * fabsf(delta);
+        return x + y >= 15.f ? P * w4_region1_re(x, y) : w4_value_f32(delta, make_float4(a, y, P, 0.f));
     } else if (PROF == XC_DOPPLER_BINNED) {
         // erf(x+) - erf(x-) on the side |delta| of the (symmetric) profile, as
         // erfc(x-) - erfc(x+): no difference of two numbers near 1 in the wings
@@ -1560,13 +1573,6 @@ __device__ __forceinline__ float w4_region34_re(float x, float y) {
                         m * (364.2191f + m * (61.57037f + m * (1.841439f + m))))));
     const Cx<float> r = cdiv(N, D);
     return expf(u.re) * cosf(u.im) - (t.re * r.re - t.im * r.im);
-}
-
-// Re w in w4's region I from (x, y): 0.5641896 y (0.5 + X + Y) / ((X + Y - 0.5)^2 + 2Y)
-__device__ __forceinline__ float w4_region1_re(float x, float y) {
-    float X = x * x, Y = y * y;
-    float t = X + Y - 0.5f;
-    return 0.5641896f * y * (0.5f + X + Y) * rcp_approx(fmaf(t, t, 2.f * Y));
 }
 
 __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {

@@ -516,10 +516,6 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                 const float thr = (15.f - y) * rcp_approx(asc);
                 const float thr2 = y < 15.f ? thr * thr : -1.f;   // region I iff u >= thr2
                 for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
-                    // the block's dL/dsigma values first, all in flight together
-                    float gv[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) gv[j] = k8 + 32 * j <= kb ? __ldg(gc + k8 + 32 * j) : 0.f;
                     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -527,7 +523,7 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                         if (k <= kb) {
                             const float d = (float)(k - na) - ff;
                             const float u = d * d;
-                            const float gk = gv[j];
+                            const float gk = gc[k];
                             if (u >= thr2) {
                                 const float t = C - u;
                                 const float Dn = fmaf(t, t, g4 * u);
@@ -606,9 +602,6 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                 // V = sqrt(ln2/pi)/a 2^(-u/a^2): sums of g 2^(-u/a^2) and g u 2^(-u/a^2)
                 const float ia2 = rcp_approx(a_h * a_h);
                 for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
-                    float gv[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) gv[j] = k8 + 32 * j <= kb ? __ldg(gc + k8 + 32 * j) : 0.f;
                     float q0 = 0.f, q1 = 0.f;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -616,7 +609,7 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                         if (k <= kb) {
                             const float d = (float)(k - na) - ff;
                             const float u = d * d;
-                            const float e = ex2_approx(-u * ia2) * gv[j];
+                            const float e = ex2_approx(-u * ia2) * gc[k];
                             q0 += e;
                             q1 = fmaf(e, u, q1);
                         }
@@ -637,9 +630,6 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                 // Lorentz: V = (1/pi) g/(u + g^2), dV/dg = (1/pi)(u - g^2)/(u + g^2)^2
                 const float g2 = g_h * g_h;
                 for (int k8 = ka + lane; k8 <= kb; k8 += 32 * 8) {
-                    float gv[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) gv[j] = k8 + 32 * j <= kb ? __ldg(gc + k8 + 32 * j) : 0.f;
                     float q0 = 0.f, q2 = 0.f;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -648,7 +638,7 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                             const float d = (float)(k - na) - ff;
                             const float u = d * d;
                             const float r = rcp_approx(u + g2);
-                            const float gr = gv[j] * r;
+                            const float gr = gc[k] * r;
                             q0 += gr;
                             q2 = fmaf(gr, (u - g2) * r, q2);
                         }
