@@ -19,10 +19,9 @@
 // covers all but a few points next to each line centre.  Two lines that cover
 // the whole warp span with no region II-IV point are summed over one shared
 // reciprocal:  q1/D1 + q2/D2 = (q1 D2 + q2 D1) / (D1 D2).  Lines that straddle
-// the span edge of their cut, or whose region II-IV points (for some condition)
-// reach the span, take a masked single-line path that evaluates region I and
-// region II (in real form) at those points; regions III and IV (|x| + y < 5.5)
-// are left to the centre-zone kernel.
+// the span edge of their cut, or whose centre zone (region II-IV for some
+// condition) reaches the span, take a masked single-line path that evaluates
+// region I there; the centre zones are left to the centre-zone kernel.
 //
 // Accumulation: FP32 in registers over FOLD_CHUNKS chunks of lines, then folded
 // into the FP64 output, which each thread owns exclusively (no atomics, fixed
@@ -424,10 +423,9 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         float C = b + g2;
         float P = I * kKappa * gh * inv_h;
         *A = make_float4(2.f * (g2 - b), C * C, P, P * C);
-        // a, y and the region-I threshold decide how a point is evaluated (region I as the
-        // rational, region II in real form by the main kernel, |x| + y < 5.5 by the
-        // centre-zone kernel: w4_t34); the far radius which points the tensor-core kernel
-        // takes (see w4_zone)
+        // a, y and the region-I threshold decide which kernel evaluates a point (the
+        // main kernel: |x| + y >= 15; the centre-zone kernel: the rest); the far radius
+        // which points the tensor-core kernel takes (see w4_zone)
         const W4Zone z = w4_zone(ah, gh);
         float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
         *B = make_float4(z.a, z.y, Pv, z.t2);
@@ -501,27 +499,14 @@ __device__ __forceinline__ float w4_region1_re(float x, float y) {
     return 0.5641896f * y * (0.5f + X + Y) * rcp_approx(fmaf(t, t, 2.f * Y));
 }
 
-// The w4 region-III/IV zone of a (line, condition): the points with u < t34 (u = delta^2
-// in grid steps), i.e. |x| + y < 5.5, from the a = sqrt(ln2)/a_h and y every kernel keeps
-// (explicitly rounded: the near-pair / main kernels and the centre-zone kernel split the
-// points by this same value); t34 < 0 when y >= 5.5 (no such zone)
-__device__ __forceinline__ float w4_t34(float a, float y) {
-    const float thr = __fmul_rn(__fsub_rn(5.5f, y), rcp_approx(a));
-    return y < 5.5f ? __fmul_rn(thr, thr) : -1.f;
-}
-
 template <int PROF>
 __device__ __forceinline__ float contrib_single(float u, float delta, const float4 &A, const float4 &B,
                                                 const float *s_x, const float *s_w, int ngh) {
     if (PROF == XC_VOIGT_W4) {
-        // region I (u >= t2) as the rational; region II (u >= t34, |x| + y >= 5.5) in real
-        // form, Pv Re w; points with |x| + y < 5.5 belong to the centre-zone kernel
+        // region I only; points with |x| + y < 15 belong to the centre-zone kernel
         float D = fmaf(u, u + A.x, A.y);
         float q = fmaf(A.z, u, A.w);
-        if (u >= B.w) return q * rcp_approx(D);
-        if (u < w4_t34(B.x, B.y)) return 0.f;
-        const float x = B.x * fabsf(delta);
-        return B.z * (x + B.y >= 15.f ? w4_region1_re(x, B.y) : w4_region2_re(x, B.y));
+        return u >= B.w ? q * rcp_approx(D) : 0.f;
     } else if (PROF == XC_LORENTZ) {
         return A.y * rcp_approx(u + A.x);
     } else if (PROF == XC_DOPPLER) {
@@ -1541,17 +1526,17 @@ __global__ void k_far_count(const float4 *__restrict__ geo, const float4 *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Centre-zone kernel (Voigt w4): the points with |x| + y < 5.5 (w4 regions III and
-// IV), which the other kernels skip (they evaluate region I as the rational and region
-// II in its real two-Lorentzian-pair form).  Gather form again: a CTA owns CORE_T
-// consecutive grid points (one per thread) and a group of conditions, walks the lines
-// whose centre zone can reach its window (|nu - x| < 6.65 alpha_max, a range of the
-// sorted list), and for each of its points sums, in line order, Re w by region (III/IV
-// as complex w4; II or I only for rounding cases at the zone's edge).  It runs after
-// the other kernels and adds its FP32 sums into the FP64 output each thread owns, so
-// the result stays deterministic.  Which kernel evaluates a (line, point, condition) is
-// decided by the same tests u < t2 (region I) and u < t34 (w4_t34) on bit-identical
-// values, so every contribution is counted exactly once.
+// Centre-zone kernel (Voigt w4): the points with |x| + y < 15, which the main
+// kernel skips.  Gather form again: a CTA owns CORE_T consecutive grid points
+// (one per thread) and a group of conditions, walks the lines whose centre zone
+// can reach its window (|nu - x| < 18.02 alpha_max, a range of the sorted list),
+// and for each of its points sums, in line order, Re w by region: I (rounding
+// cases at the boundary), II (real two-Lorentzian-pair form) or III/IV (complex
+// w4).  It runs after the main kernel and adds its FP32 sums into the FP64
+// output each thread owns (every CORE_FLUSH chunks), so the result stays
+// deterministic.  Which kernel evaluates a (line, point, condition) is decided by
+// the same test u < thr^2 on bit-identical values, so every contribution is
+// counted exactly once.
 // ---------------------------------------------------------------------------
 constexpr int CORE_T = 256;
 constexpr int CORE_CG = 32;
@@ -1654,11 +1639,9 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
             int cc = grp * CORE_CG + c;
             float t2 = -1.f;
             float4 A, S, B = make_float4(0.f, 0.f, 0.f, -1.f);
-            if (i < cnt && cc < p.n_cond) {
+            if (i < cnt && cc < p.n_cond)
                 line_consts<XC_VOIGT_W4>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
                                          &t2, &S);
-                t2 = w4_t34(B.x, B.y);   // this kernel's zone: |x| + y < 5.5 (regions III and IV)
-            }
             if (i < cnt) sB[i][c] = B;
             // one line per warp (CORE_CG == 32 lanes = conditions): bitonic sort of the
             // thresholds, largest first, so the point loop can stop at the first
@@ -1726,7 +1709,7 @@ __global__ void __launch_bounds__(CORE_T) k_core_w4_f32(CoreParams p) {
     flush();
 }
 
-// window -> line range for the centre zone: |nu - x| < K nu with K = 6.65 alpha_max/nu
+// window -> line range for the centre zone: |nu - x| < K nu with K = 18.02 alpha_max/nu
 __global__ void k_core_ranges(const double *__restrict__ nu, int64_t n, double nu_A, double step, int64_t n_pts,
                               double K, int n_win, unsigned *lo, unsigned *hi) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2035,12 +2018,11 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main1, s, cudaEventRecordExternal));
     *launches += 1;
     if (a.opts.profile == XC_VOIGT_W4 && max_lines == 0) {
-        // centre zone: |x| + y < 5.5 (w4 regions III and IV), |nu - x| < 5.5 alpha / sqrt(ln2)
-        // = 6.606 alpha <= K nu
+        // centre zone: |x| + y < 15, |nu - x| < 18.02 alpha <= K nu
         double amax = 0.0;
         for (int c = 0; c < nc; ++c)
             amax = std::max(amax, alpha_coef(a.conds_host[c0 + c].T, a.conds_host[c0 + c].mass_da));
-        const double K = 6.65 * amax;
+        const double K = 18.05 * amax;
         k_core_ranges<<<(pl.n_win_core + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step,
                                                                    a.grid.n, K, pl.n_win_core, pl.core_lo,
                                                                    pl.core_hi);
