@@ -312,6 +312,22 @@ def secondary_measurements(xc, torch, dev):
                                                                          ("_beta" if kw.get("vv_beta") else ""))
             res[f"{prof}_{prec}{tag}"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
         if name == "C2":
+            # the plain FP64 form of binned GH (20 atan2 per evaluation at the FP64 rate: about 40 s
+            # over the whole grid) on the 1000 cm^-1 slice 5000..6000 with every line loaded (the
+            # same line density), for the FP32 / FP64 ratio in evals/s
+            o = xc.make_opts("voigt_gh_binned", "fp64", W.cutoff, W.cutoff_width_mult, W.n_gh)
+            sg = xc.make_grid(W.grid_lo + 500000 * W.step, W.step, 100001)
+            s1 = torch.empty((len(conds), sg.n), dtype=torch.float64, device=dev)
+            ev = eng.count_evals(conds, sg, o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            eng.cross_section_batched(conds, sg, o, s1)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res["voigt_gh_binned_fp64_slice_5000_6000"] = {"ms": ms, "evals": ev, "evals_per_s": ev / (ms / 1e3)}
+            res["voigt_gh_binned_fp32_over_fp64"] = res["voigt_gh_binned_fp32"]["evals_per_s"] / (ev / (ms / 1e3))
+            del s1
             # Lorentz widths from a two-broadener mixture (an a0 table by J'' and a constant)
             a0 = {j: (0.09 - 0.001 * j, 0.75 - 0.004 * j) for j in range(0, 80)}
             eng.set_broadening([xc.make_broadener("a0", 0.8, 0.07, 0.5, a0),

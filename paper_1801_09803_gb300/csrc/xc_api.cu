@@ -17,6 +17,8 @@
 #include "xc_internal.cuh"
 #include "xc_batched.cuh"
 
+#include <unistd.h>
+
 #ifndef XC_VERSION_STRING
 #define XC_VERSION_STRING "xc 0.1 (sm_103a)"
 #endif
@@ -24,6 +26,19 @@
 namespace xc {
 
 static thread_local std::string g_last_error;
+
+void warm_host_pages(const void *p, size_t bytes) {
+    if (!p || bytes < ((size_t)1 << 20)) return;
+    static const size_t page = [] {
+        const long v = sysconf(_SC_PAGESIZE);
+        return v > 0 ? (size_t)v : (size_t)4096;
+    }();
+    const volatile unsigned char *c = static_cast<const volatile unsigned char *>(p);
+    unsigned acc = 0;
+    for (size_t o = 0; o < bytes; o += page) acc += c[o];
+    acc += c[bytes - 1];
+    (void)acc;
+}
 
 void set_error(const char *fmt, ...) {
     char buf[1024];
@@ -454,6 +469,9 @@ xc_status xc_load_lines(xc_handle *h, const xc_lines *L, size_t n, unsigned flag
         float *e = (float *)take(n * 4), *a = (float *)take(n * 4), *gr = (float *)take(n * 4),
               *nt = (float *)take(n * 4);
         int16_t *g = (int16_t *)take(n * 2), *j = (int16_t *)take(n * 2);
+        const void *src[7] = {L->nu, L->elower, L->A, L->gamma_ref, L->n_T, L->g_up, L->j_lo};
+        const size_t sz[7] = {n * 8, n * 4, n * 4, n * 4, n * 4, n * 2, n * 2};
+        for (int f = 0; f < 7; ++f) warm_host_pages(src[f], sz[f]);
         stage_begin(h, ST_FINISH, s);
         XC_TRY(cudaMemcpyAsync(nu, L->nu, n * 8, cudaMemcpyHostToDevice, s));
         XC_TRY(cudaMemcpyAsync(e, L->elower, n * 4, cudaMemcpyHostToDevice, s));
@@ -823,6 +841,7 @@ xc_status xc_cross_section_batched(xc_handle *h, const xc_condition *conds, size
         used[ST_PARAMS] = true;  // whole sweep; per-kernel times are read below
     }
     if (mem == XC_MEM_HOST) {
+        warm_host_pages(sigma_out, total * sizeof(double));
         stage_begin(h, ST_FINISH, s);
         XC_TRY(cudaMemcpyAsync(sigma_out, sig, total * sizeof(double), cudaMemcpyDeviceToHost, s));
         stage_end(h, ST_FINISH, s);

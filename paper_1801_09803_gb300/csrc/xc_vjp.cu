@@ -761,6 +761,7 @@ xc_status vjp_run(BatchedState *st, const VjpArgs &a, int64_t *launches) {
     char *base = st->vjp_buf.as<char>();
     const double *g64 = a.grad_sigma;
     if (host && nc && N) {
+        warm_host_pages(a.grad_sigma, (size_t)nc * N * 8);
         VJ_TRY(cudaMemcpyAsync(base + o_g, a.grad_sigma, (size_t)nc * N * 8, cudaMemcpyHostToDevice, s));
         g64 = (const double *)(base + o_g);
     }
