@@ -339,6 +339,8 @@ __global__ void k_nodes_to_float(const double *x, const double *w, int n, float 
 // ---------------------------------------------------------------------------
 // per-(line, condition) constants, by profile
 //   W4 : A = {E', F', P', P'C'}   B = {a, y, Pv, thr^2}   (grid units)
+//   VV : A = reference wing {E', F', P', P'C'} (or {a, -1, P, y} where it is not region I
+//        throughout)   B = {a, y, Pv, exact-zone half-width}
 //   LOR: A = {G', P', 0, 0}
 //   DOP: A = {qd, Pd, 0, 0}
 //   GHS: A = {sh, G', P, 0}
@@ -440,9 +442,9 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
     } else if (PROF == XC_VOIGT_GH_SAMPLED) {
         *A = make_float4(ah / kSqrtLn2f, fmaxf(gh * gh, 1e-30f), I * kPiM32 * gh * inv_h, 0.f);
     } else if (PROF == XC_VOIGT_VV) {
-        // B: the line's own w4 Voigt (a, y, Pv); A: the reference wing -- the Voigt of a line at
-        // 1 cm^-1, Doppler HWHM alpha / nu: a_ref = a nu, y_ref = a_ref g, amplitude Pv nu, times
-        // beta (Eq. e:beta) when asked -- and the exact zone's half-width in grid steps
+        // B: the line's own w4 Voigt (a, y, Pv) and the exact zone's half-width in grid steps;
+        // A: the reference wing -- the Voigt of a line at 1 cm^-1, Doppler HWHM alpha / nu:
+        // a_ref = a nu, y_ref = a_ref g, amplitude Pv nu, times beta (Eq. e:beta) when asked
         const float a = kSqrtLn2f * rcp_approx(ah), y = a * gh;
         const float Pv = I * kSqrtLn2OverPi * rcp_approx(al);
         const float ar = a * nu, yr = ar * gh;
@@ -452,8 +454,17 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
             const float rw = w4_value_f32(sp, make_float4(ar, yr, 1.f, 0.f));
             Pw = rw > 0.f ? w4_value_f32(sp, make_float4(a, y, Pv, 0.f)) / rw : 0.f;
         }
-        *A = make_float4(ar, yr, Pw, sp);
-        *B = make_float4(a, y, Pv, 0.f);
+        if (ar * (sp + gh) >= 15.f) {
+            // beyond the exact zone the reference Voigt is in w4's region I everywhere
+            // (x_ref + y_ref > a_ref (sp + g) >= 15): its rational in u = delta^2, as the
+            // Voigt w4 constants A (with b_ref = 1 / (2 a_ref^2), C = b_ref + g^2)
+            const float br = 0.5f * rcp_approx(ar * ar), g2 = gh * gh, Cr = br + g2;
+            const float Pr = Pw * 0.5641896f * gh * rcp_approx(ar);
+            *A = make_float4(2.f * (g2 - br), Cr * Cr, Pr, Pr * Cr);
+        } else {
+            *A = make_float4(ar, -1.f, Pw, yr);   // flagged by A.y < 0: the complex w4 where needed
+        }
+        *B = make_float4(a, y, Pv, sp);
     } else if (PROF == XC_DOPPLER_BINNED) {
         // Eq. (eqn:sig_ij) in grid steps: x+- = (sqrt(ln2)/ah) (delta +- 1/2), I/(2h)
         *A = make_float4(kSqrtLn2f * rcp_approx(ah), 0.5f * I * inv_h, 0.f, 0.f);
@@ -520,13 +531,18 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
         return A.z * s;
     } else if (PROF == XC_VOIGT_VV) {
         // Eq. (e:fast-v): the line's own Voigt in the exact zone, the reference wing beyond it.
-        // Both are w4 Voigts; where |x| + y >= 15 (the whole reference wing, whose Doppler
-        // width alpha/nu is tiny, and most of the exact zone) w4 is its region-I rational,
-        // evaluated in real form; the full w4 only for the few points nearer the centre
-        const bool wing = fabsf(delta) > A.w;
-        const float a = wing ? A.x : B.x, y = wing ? A.y : B.y, P = wing ? A.z : B.z;
-        const float x = a * fabsf(delta);
-        return x + y >= 15.f ? P * w4_region1_re(x, y) : w4_value_f32(delta, make_float4(a, y, P, 0.f));
+        // Both are w4 Voigts.  The reference wing (most of the points) is region I throughout
+        // for almost every line: its rational in u with the line's constants, as Voigt w4's
+        // main kernel evaluates it; in the exact zone w4 is its region-I rational in real
+        // form where |x| + y >= 15 and the full w4 only for the few points nearer the centre
+        const float ad = fabsf(delta);
+        if (ad > B.w) {
+            if (A.y >= 0.f) return fmaf(A.z, u, A.w) * rcp_approx(fmaf(u, u + A.x, A.y));
+            const float x = A.x * ad;
+            return x + A.w >= 15.f ? A.z * w4_region1_re(x, A.w) : w4_value_f32(delta, make_float4(A.x, A.w, A.z, 0.f));
+        }
+        const float x = B.x * ad;
+        return x + B.y >= 15.f ? B.z * w4_region1_re(x, B.y) : w4_value_f32(delta, make_float4(B.x, B.y, B.z, 0.f));
     } else if (PROF == XC_DOPPLER_BINNED) {
         // erf(x+) - erf(x-) on the side |delta| of the (symmetric) profile, as
         // erfc(x-) - erfc(x+): no difference of two numbers near 1 in the wings
@@ -751,7 +767,7 @@ __global__ void __launch_bounds__(GT, (TCN ? (CG >= 16 ? 2 : 3) : (CG >= 16 ? 1 
                         line_consts<PROF, EXT>(p.L, (size_t)lo + ci + (size_t)i * nch, p.cp[cc], p.h, p.inv_h, &A, &B,
                                           &t2, &S, TCN || p.tc_far != 0);
                     } else {  // padding condition: contributes exactly 0
-                        if (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV) A = make_float4(1.f, 1.f, 0.f, 0.f);
+                        if (PROF == XC_VOIGT_W4 || PROF == XC_VOIGT_VV) A = make_float4(1.f, 1.f, 0.f, 0.f);   // 0 / (u^2 + u + 1)
                         else if (PROF == XC_VOIGT_GH_SAMPLED) A = make_float4(0.f, 1.f, 0.f, 0.f);
                         else if (PROF == XC_VOIGT_GH_BINNED) A = make_float4(0.f, 1.f, 1.f, 0.f);
                         else A = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -1903,6 +1919,18 @@ xc_status make_plan(BatchedState *st, const BatchedArgs &a, const Variant *v, in
 
 int tc_grid_size(int n_tiles);
 
+// A timing event inside the sweep: while the sweep is captured into a graph it must be an
+// external event node (a plain record would become an internal dependency); on a stream
+// that is not capturing (the per-condition sweeps of a width-limited cut) the external
+// flag is refused, and a plain record is the same thing.
+static cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
 // enqueue the whole sweep for conditions [c0, c0 + nc) on the stream
 xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid, int max_lines, int64_t *launches,
                   bool per_cond_cut) {
@@ -1981,7 +2009,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
     gp.tc_far = pl.tc ? 1 : 0;
     gp.sigma = a.sigma + (size_t)c0 * (size_t)a.grid.n;
     const bool ev = a.timing && a.ev_main0 && max_lines == 0;
-    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main0, s, cudaEventRecordExternal));
+    if (ev) BT_TRY(record_timing_event(a.ev_main0, s));
     if (pl.tc && max_lines == 0) {
         // far wings on the tensor cores: first writer of every output of the sweep
         k_win_ranges32<<<(pl.n_blk + 127) / 128, 128, 0, s>>>(a.L.nu, (int64_t)n, a.grid.nu_A, a.grid.step, a.grid.n,
@@ -2011,11 +2039,11 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
             k_far_tc<true><<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
         else
             k_far_tc<false><<<tc_grid_size(pl.n_tc_tiles), TC_T, TC_SMEM, s>>>(tp);
-        if (ev && a.ev_tc1) BT_TRY(cudaEventRecordWithFlags(a.ev_tc1, s, cudaEventRecordExternal));
+        if (ev && a.ev_tc1) BT_TRY(record_timing_event(a.ev_tc1, s));
         *launches += 2;
     }
     pl.v->fn<<<grid, GT, pl.v->smem, s>>>(gp);
-    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_main1, s, cudaEventRecordExternal));
+    if (ev) BT_TRY(record_timing_event(a.ev_main1, s));
     *launches += 1;
     if (a.opts.profile == XC_VOIGT_W4 && max_lines == 0) {
         // centre zone: |x| + y < 15, |nu - x| < 18.02 alpha <= K nu
@@ -2044,7 +2072,7 @@ xc_status enqueue(const BatchedArgs &a, const Plan &pl, int c0, int nc, int grid
         k_core_w4_f32<<<cg, CORE_T, 0, s>>>(cp);
         *launches += 2;
     }
-    if (ev) BT_TRY(cudaEventRecordWithFlags(a.ev_core1, s, cudaEventRecordExternal));
+    if (ev) BT_TRY(record_timing_event(a.ev_core1, s));
     BT_TRY(cudaGetLastError());
     return XC_OK;
 }

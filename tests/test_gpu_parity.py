@@ -353,6 +353,16 @@ def test_width_limited_cut(eng, xc, oracle_lib, profile):
         mr, band = metrics(got, ref)
         print(f"width-limited {profile} {precision}: {mr:.3g} {band:.3g}")
         assert mr < tol[0] and band < tol[1]
+    # the batched FP32 form with per-kernel timing on: its per-condition sweeps run on the
+    # stream directly (not captured in a graph), where the timing events are plain records
+    eng.set_timing(True)
+    try:
+        got = eng.cross_section_batched([xc.make_condition(1500.0, 1.0)], grid,
+                                        xc.make_opts(profile, "fp32", 25.0, 500.0))
+    finally:
+        eng.set_timing(False)
+    mr, band = metrics(got[0], ref)
+    assert mr < TOL32 and band < TOL32_BAND, (mr, band)
 
 
 @pytest.mark.parametrize("profile", ["doppler_binned", "lorentz_binned"])
