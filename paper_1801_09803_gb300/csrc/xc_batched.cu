@@ -550,12 +550,12 @@ __device__ __forceinline__ float contrib_single(float u, float delta, const floa
         return A.y * (erfcf(A.x * (t - 0.5f)) - erfcf(A.x * (t + 0.5f)));
     } else if (PROF == XC_LORENTZ_BINNED) {
         // atan(y+) - atan(y-) = atan2(y+ - y-, 1 + y+ y-), both arguments scaled by gh^2 > 0
-        return A.z * atan2f(A.x, u + A.y);
+        return A.z * atan2_ypos(A.x, u + A.y);
     } else {
         float s = 0.f;
         for (int j = 0; j < ngh; ++j) {
             float e = fmaf(-A.x, s_x[j], delta);
-            s = fmaf(s_w[j], atan2f(A.y, fmaf(e, e, A.z)), s);
+            s = fmaf(s_w[j], atan2_ypos(A.y, fmaf(e, e, A.z)), s);
         }
         return A.w * s;
     }

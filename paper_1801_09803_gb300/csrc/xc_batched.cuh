@@ -46,6 +46,35 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return r;
 }
 
+// atan2(y, x) for y >= 0 (in [0, pi]), the arctangent of the binned Lorentzian and of the
+// binned Gauss-Hermite Voigt (Eqs. eqn:sig_lor-2, e:sigma:quad), whose first argument is
+// gamma >= 0.  t = min(|x|, y) / max(|x|, y) in [0, 1]; atan(t) = t q(t^2) with q the
+// degree-8 polynomial interpolating atan(sqrt(s)) / sqrt(s) at the 9 Chebyshev nodes of
+// s in [0, 1] (derived here in FP64, relative error 1.8e-8); then atan2 = pi/2 - atan(t)
+// where y > |x| and pi minus that where x < 0.  In FP32 with the approximate reciprocal
+// the result is within a few units in the last place of atan2 (2e-7 relative over
+// y in [1e-6, 1e3], |x| in [1e-6, 1e7]); about 20 instructions against ~50 for the
+// general library function.  atan2(0, 0) = 0.
+__device__ __forceinline__ float atan2_ypos(float y, float x) {
+    const float ax = fabsf(x);
+    const float mx = fmaxf(ax, y), mn = fminf(ax, y);
+    const float t = mx > 0.f ? mn * rcp_approx(mx) : 0.f;
+    const float s = t * t;
+    float q = 2.766283504e-03f;
+    q = fmaf(q, s, -1.573124913e-02f);
+    q = fmaf(q, s, 4.213762360e-02f);
+    q = fmaf(q, s, -7.456854827e-02f);
+    q = fmaf(q, s, 1.061837064e-01f);
+    q = fmaf(q, s, -1.419779779e-01f);
+    q = fmaf(q, s, 1.999187203e-01f);
+    q = fmaf(q, s, -3.333303671e-01f);
+    q = fmaf(q, s, 9.999999818e-01f);
+    float p = q * t;
+    if (y > ax) p = 1.5707963267948966f - p;
+    if (x < 0.f) p = 3.141592653589793f - p;
+    return p;
+}
+
 // 2^(-z) for z >= 0 with the argument split into integer and fraction
 __device__ __forceinline__ float exp2_neg(float z) {
     float zi = rintf(z);

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                             for (int m = 0; m < ngh; ++m) {
                                 const float sp = fmaf(-a_h, s_gx[m], d), sm = sp - 1.f;
                                 const float iQ = rcp_approx(fmaf(sp, sp, g2) * fmaf(sm, sm, g2));
-                                v = fmaf(s_gw[m], atan2f(g_h, fmaf(sp, sm, g2)), v);
+                                v = fmaf(s_gw[m], atan2_ypos(g_h, fmaf(sp, sm, g2)), v);
                                 dg = fmaf(s_gw[m], fmaf(sp, sm, -g2) * iQ, dg);
                                 da = fmaf(s_gw[m] * s_gx[m], (sp + sm) * iQ, da);
                             }
