@@ -457,7 +457,9 @@ __device__ __forceinline__ void line_consts(const LinesDev &L, size_t l, const C
         if (ar * (sp + gh) >= 15.f) {
             // beyond the exact zone the reference Voigt is in w4's region I everywhere
             // (x_ref + y_ref > a_ref (sp + g) >= 15): its rational in u = delta^2, as the
-            // Voigt w4 constants A (with b_ref = 1 / (2 a_ref^2), C = b_ref + g^2)
+            // Voigt w4 constants A (with b_ref = 1 / (2 a_ref^2), C = b_ref + g^2).
+            // a_ref = sqrt(ln 2) h / (alpha / nu) does not depend on nu (thousands for common
+            // steps), so only a split and a Lorentz width both far below a grid step fail it
             const float br = 0.5f * rcp_approx(ar * ar), g2 = gh * gh, Cr = br + g2;
             const float Pr = Pw * 0.5641896f * gh * rcp_approx(ar);
             *A = make_float4(2.f * (g2 - br), Cr * Cr, Pr, Pr * Cr);

@@ -561,6 +561,34 @@ def test_vectorized_voigt(eng, xc, oracle_lib, beta, norm):
     assert worst[0] < TOL32 and worst[1] < TOL32_BAND
 
 
+def test_vectorized_voigt_reference_wing_outside_region_one(eng, xc, oracle_lib):
+    """The FP32 kernel evaluates the reference wing as a region-I rational in u only when
+    a_ref (split + g) >= 15 in grid steps (a_ref = sqrt(ln 2) h / (alpha / nu), about 3e4
+    here); a split far below the grid step and a Lorentz width near zero (P = 1e-4 bar) take
+    the other branch (the w4 Voigt in x, y) for every line.  Against the oracle, FP32.
+    With the exact zone far below a grid step the band is carried by the one or two grid
+    points a few 1e-4 steps from a line centre, where the reference Voigt has |x| + y < 15
+    and the complex w4 is evaluated in FP32 (8e-5 relative at the one such point of this
+    list); so the band is held to the pointwise bound here, not to the band bound."""
+    L = xs.gen_lines(114, 0, 1000, 3000.0, 3020.0)
+    E, g = xs.gen_states(114, 1000)
+    eng.load_lines(L)
+    eng.set_states(E, g)
+    nu_A, step, n, cut = 2995.0, 0.05, 601, 5.0
+    TP = [(300.0, 1e-4), (1500.0, 1e-4), (3000.0, 2e-4)]
+    kw = dict(vv_split=1e-5, vv_beta=True, vv_norm=False)
+    grid = xc.make_grid(nu_A, step, n)
+    got = eng.cross_section_batched([xc.make_condition(T, P) for T, P in TP], grid,
+                                    xc.make_opts("voigt_vv", "fp32", cut, **kw))
+    for j, (T, P) in enumerate(TP):
+        Q, dQ = oracle_lib.partition_function(E, g, T)
+        c = oracle_lib.make_condition(T, P, Q, dQ)
+        ref = oracle_lib.cross_section(L, c, nu_A, step, n, oracle_lib.make_opts("voigt_vv", cut, **kw),
+                                       nthreads=NTHREADS)
+        mr, band = metrics(got[j], ref)
+        assert mr < TOL32 and band < TOL32, (j, mr, band)
+
+
 def test_c1_full_size(eng, xc, oracle_lib):
     """The single-condition FP64 workload at full size: 1e5 lines, 200001 points."""
     W = xs.WORKLOADS["C1"]
