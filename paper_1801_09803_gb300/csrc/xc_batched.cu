@@ -1156,8 +1156,10 @@ constexpr int TC_T = TC_M * TC_BLK;       // threads per CTA: one per point
 constexpr int TC_N = 32;                  // conditions per tile = MMA N
 constexpr int TC_L = 8;                   // lines per chunk
 constexpr int TC_J = 4;                   // series terms
-constexpr int TC_ACOLS = 6 * TC_L;        // A columns per chunk: r hi, r lo, r^2 hi, r^2 lo, r^3, r^4
-constexpr int TC_BT = 6;                  // B tiles (K = 8 each): p0 hi, p0 lo, p1 hi, p1 lo, p2, p3
+constexpr int TC_ACOLS = 5 * TC_L;        // A columns per chunk: r hi, r lo, r^2, r^3, r^4
+constexpr int TC_ASTRIDE = 48;            // TMEM columns between the two A buffers
+constexpr int TC_BT = 5;                  // B tiles (K = 8 each): p0 hi, p0 lo, p1, p2, p3
+constexpr int TC_MMAS = 6;                // MMAs per chunk and block
 constexpr int TC_FOLD = 16;               // chunks per tensor-memory accumulation period
 constexpr uint32_t TC_COLS = 128 * TC_BLK;// TMEM columns: per block D 32 + 2 buffers x 48
 constexpr int TC_BTILE = TC_N * TC_L;     // one B tile: 8 K x 32 N = 256 floats (1 KB)
@@ -1165,6 +1167,7 @@ constexpr size_t TC_SMEM_B = (size_t)TC_BLK * 2 * TC_BT * TC_BTILE * sizeof(floa
 constexpr size_t TC_SMEM_ACC = (size_t)2 * TC_N * TC_T * sizeof(float);           // compensated FP32 sums
 constexpr size_t TC_SMEM = 100 * 1024;    // B + sums + barriers; sized so that 2 CTAs (2 x 256 TMEM
                                           // columns) and never 3 share an SM
+static_assert(TC_N + 2 * TC_ASTRIDE <= 128 && TC_ACOLS <= TC_ASTRIDE, "far-wing kernel tensor-memory columns");
 static_assert(TC_SMEM_B + TC_SMEM_ACC + 128 + 4 * TC_L * 16 + 2 * TC_L * 4 + 12 <= TC_SMEM, "far-wing kernel shared memory");
 
 // a chunk line with a cut covering the whole super-block [t0, t0 + TC_T) and its centre
@@ -1233,7 +1236,7 @@ __device__ __forceinline__ float4 tc_series_consts(const float4 &ph, float nT, c
 template <bool EXT>
 __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *sB = reinterpret_cast<float *>(smem);                           // [blk][buf][hi, lo][768]
+    float *sB = reinterpret_cast<float *>(smem);                           // [blk][buf][tile][256]
     float *sSum = reinterpret_cast<float *>(smem + TC_SMEM_B);             // [c][point]
     float *sCmp = sSum + TC_N * TC_T;                                       // Kahan compensation
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_SMEM_B + TC_SMEM_ACC);  // [blk][buf]
@@ -1361,8 +1364,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                         p3 = 0.f;
                     }
                 }
-                const float p0h = tc::tf32_trunc(S.x), p1h = tc::tf32_trunc(S.y);
-                const float p0l = S.x - p0h, p1l = S.y - p1h, p2h = S.z;
+                // p0 as hi + lo; p1 rounded to the nearest TF32 value (where the series is
+                // used its term is at most 3.6 % of p0's, so one unbiased TF32 rounding of each
+                // factor stays below 4e-5 of the sum)
+                const float p0h = tc::tf32_trunc(S.x);
+                const float p0l = S.x - p0h, p1r = tc::tf32_round(S.y), p2h = S.z;
 #pragma unroll
                 for (int hb = 0; hb < TC_BLK; ++hb) {
                     // span_far in float: na and the block ends are exact integers below 2^24,
@@ -1372,15 +1378,15 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                     float *bt = sB + (size_t)(hb * 2 + b) * TC_BT * TC_BTILE + bix;
                     bt[0 * TC_BTILE] = far ? p0h : 0.f;
                     bt[1 * TC_BTILE] = far ? p0l : 0.f;
-                    bt[2 * TC_BTILE] = far ? p1h : 0.f;
-                    bt[3 * TC_BTILE] = far ? p1l : 0.f;
-                    bt[4 * TC_BTILE] = far ? p2h : 0.f;
-                    bt[5 * TC_BTILE] = far ? p3 : 0.f;
+                    bt[2 * TC_BTILE] = far ? p1r : 0.f;
+                    bt[3 * TC_BTILE] = far ? p2h : 0.f;
+                    bt[4 * TC_BTILE] = far ? p3 : 0.f;
                 }
             }
-            // ---- A: r^(j+1) of this thread's point for the chunk's lines, split hi + lo
+            // ---- A: r^(j+1) of this thread's point for the chunk's lines (r split hi + lo,
+            // r^2 rounded to the nearest TF32 value)
             {
-                float av[TC_ACOLS];   // [r hi | r lo | r^2 hi | r^2 lo | r^3 | r^4], TC_L lines each
+                float av[TC_ACOLS];   // [r hi | r lo | r^2 | r^3 | r^4], TC_L lines each
 #pragma unroll
                 for (int l8 = 0; l8 < TC_L; ++l8) {
                     float r;
@@ -1395,22 +1401,26 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
                         r = (l0 + l8 < nl && kf >= g.z && kf <= g.w) ? rcp_approx(fmaxf(d * d, 1.f)) : 0.f;
                     }
                     const float r2 = r * r;
-                    const float rh = tc::tf32_trunc(r), r2h = tc::tf32_trunc(r2);
+                    const float rh = tc::tf32_trunc(r);
                     av[l8] = rh;
                     av[TC_L + l8] = r - rh;
-                    av[2 * TC_L + l8] = r2h;
-                    av[3 * TC_L + l8] = r2 - r2h;
-                    av[4 * TC_L + l8] = r2 * r;    // the MMA reads r^3, r^4, p2, p3 as TF32
-                    av[5 * TC_L + l8] = r2 * r2;
+                    av[2 * TC_L + l8] = tc::tf32_round(r2);
+                    av[3 * TC_L + l8] = r2 * r;    // the MMA reads r^3, r^4, p2, p3 as TF32
+                    av[4 * TC_L + l8] = r2 * r2;
                 }
-                const uint32_t ta = t_lane + 32u + (uint32_t)b * TC_ACOLS;
+                const uint32_t ta = t_lane + 32u + (uint32_t)b * TC_ASTRIDE;
+                static_assert(TC_ACOLS == 2 * 16 + 8, "A stores: two 16-column and one 8-column store");
                 float v16[16];
 #pragma unroll
-                for (int q = 0; q < TC_ACOLS / 16; ++q) {
+                for (int q = 0; q < 2; ++q) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v16[i] = av[16 * q + i];
                     tc::tmem_st16(ta + 16u * q, v16);
                 }
+                float v8[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v8[i] = av[32 + i];
+                tc::tmem_st8(ta + 32u, v8);
                 tc::tmem_st_wait();
             }
             if (warp == 0 && ci + 1 < nch) {
@@ -1435,19 +1445,18 @@ __global__ void __launch_bounds__(TC_T, 2) k_far_tc(TcParams p) {
             }
             if (issuer) {
                 tc::fence_after_sync();
-                const uint32_t a0 = tblk + 32u + (uint32_t)b * TC_ACOLS;
+                const uint32_t a0 = tblk + 32u + (uint32_t)b * TC_ASTRIDE;
                 // descriptors differ only in the start address field (bits 0-13, 16-byte units):
                 // tile t of buffer b at + (b * TC_BT + t) KB
                 const uint64_t d0 = desc_b0 + (uint64_t)(b * TC_BT * (TC_BTILE * 4 / 16));
                 constexpr uint64_t kT = TC_BTILE * 4 / 16;
+                static_assert(TC_MMAS == 6, "the issue sequence below");
                 tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 0 * kT, kIdesc, in_fold > 0 ? 1u : 0u);  // rhi p0hi
                 tc::mma_tf32_ts(tblk, a0 + 0u * TC_L, d0 + 1 * kT, kIdesc, 1u);                    // rhi p0lo
                 tc::mma_tf32_ts(tblk, a0 + 1u * TC_L, d0 + 0 * kT, kIdesc, 1u);                    // rlo p0hi
-                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r2hi p1hi
-                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 3 * kT, kIdesc, 1u);                    // r2hi p1lo
-                tc::mma_tf32_ts(tblk, a0 + 3u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r2lo p1hi
-                tc::mma_tf32_ts(tblk, a0 + 4u * TC_L, d0 + 4 * kT, kIdesc, 1u);                    // r^3 p2
-                tc::mma_tf32_ts(tblk, a0 + 5u * TC_L, d0 + 5 * kT, kIdesc, 1u);                    // r^4 p3
+                tc::mma_tf32_ts(tblk, a0 + 2u * TC_L, d0 + 2 * kT, kIdesc, 1u);                    // r^2 p1
+                tc::mma_tf32_ts(tblk, a0 + 3u * TC_L, d0 + 3 * kT, kIdesc, 1u);                    // r^3 p2
+                tc::mma_tf32_ts(tblk, a0 + 4u * TC_L, d0 + 4 * kT, kIdesc, 1u);                    // r^4 p3
                 tc::mma_commit(&mbar[blkh * 2 + b]);
             }
             ++uses[b];
@@ -2413,8 +2422,8 @@ int64_t batched_tc_mma_count(BatchedState *st) {
     }
     int64_t chunks = 0;
     for (int i = 0; i < st->tc_n_blk; ++i) chunks += (int64_t)((hi[i] - lo[i] + TC_L - 1) / TC_L);
-    // per chunk and 128-point block: 8 MMAs (M = 128, N = 32, K = 8)
-    return chunks * st->tc_groups * TC_BLK * 8;
+    // per chunk and 128-point block: TC_MMAS MMAs (M = 128, N = 32, K = 8)
+    return chunks * st->tc_groups * TC_BLK * TC_MMAS;
 }
 
 xc_status batched_count_far(BatchedState *st, const BatchedArgs &a, int64_t *count) {
