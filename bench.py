@@ -43,8 +43,8 @@ TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes of one k_far_tc launch from one ncu capture on the C3 generator at 1e6
 # lines (profiles/k_far_tc_c3_1e6lines_32cond.md): reads grow with the line count,
 # writes are the 32-condition output; scaled to the bench's line count.
-TC_DRAM_READ_PER_LINE = 37.46e6 / 1e6
-TC_DRAM_WRITE_1M_PTS_32C = 197.69e6
+TC_DRAM_READ_PER_LINE = 37.05e6 / 1e6
+TC_DRAM_WRITE_1M_PTS_32C = 197.52e6
 
 
 def parse():

@@ -92,6 +92,26 @@ def test_c3_batched_full_size(xc, oracle_lib):
         worst = max(worst, _check(oracle_lib, S, E, g, W, conds_py[c], s1[c], ks, "voigt_w4", 2e-4))
     print(f"C3 full size, FP32 batched: worst sampled relative error {worst:.3g}")
     assert worst < 2e-4
+    # a whole slice of the grid, 4000..4010 cm^-1 (1001 points), for every condition: every
+    # point and the integrated band, against the oracle over every line within the cut of it
+    # (about 6e5 lines, each reaching up to the whole slice: the far wings of most of them on
+    # the tensor cores, summed over ~1e4 MMAs per point)
+    k0, m = 400_000, 1001
+    x0, x1 = W.grid_lo + k0 * W.step, W.grid_lo + (k0 + m - 1) * W.step
+    a, b = np.searchsorted(S["nu"], [x0 - W.cutoff - 0.01, x1 + W.cutoff + 0.01])
+    S2 = {k: v[a:b] for k, v in S.items()}
+    op = oracle_lib.make_opts("voigt_w4", W.cutoff)
+    mr_all = band_all = 0.0
+    for c in range(32):
+        Q, dQ = oracle_lib.partition_function(E, g, conds_py[c]["T"])
+        oc = oracle_lib.make_condition(conds_py[c]["T"], conds_py[c]["P"], Q, dQ, mass_da=W.mass_da)
+        ref = oracle_lib.cross_section(S2, oc, x0, W.step, m, op, nthreads=NTHREADS)
+        got = s1[c][k0:k0 + m]
+        assert np.all(ref > 0)
+        mr_all = max(mr_all, float(np.max(np.abs(got - ref) / ref)))
+        band_all = max(band_all, float(abs(got.sum() - ref.sum()) / ref.sum()))
+    print(f"C3 slice {x0:g}..{x1:g} ({b - a} lines, 32 conditions): max rel {mr_all:.3g}, band {band_all:.3g}")
+    assert mr_all < 2e-4 and band_all < 1e-5
 
 
 @pytest.mark.parametrize("profile", ["voigt_w4", "voigt_gh_binned"])
