@@ -244,7 +244,7 @@ __global__ void k_line_geom(LinesDev L, size_t n, double nu_A, double step, int6
         n_abs[l] = (int)flc;
         f_frac[l] = (float)(d - fl);
         int64_t ka, kb;
-        line_k_range(nu, cut, nu_A, step, n_pts, &ka, &kb);
+        line_k_range(nu, cut, nu_A, step, inv_h, n_pts, &ka, &kb);
         if (kb < ka) { ka = 1; kb = 0; }
         ka_abs[l] = (int)i64min(i64max(ka, -1), (int64_t)0x7fffffff);
         kb_abs[l] = (int)i64min(i64max(kb, -1), (int64_t)0x7fffffff);

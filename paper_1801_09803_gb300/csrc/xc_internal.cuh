@@ -126,10 +126,13 @@ __device__ inline double grid_x(double nu_A, double step, int64_t k) {
 
 // Inclusive k-range of grid points with |x_k - nu| <= cut, using the same
 // rounding as grid_x; empty range gives ka > kb.
-__device__ inline void line_k_range(double nu, double cut, double nu_A, double step, int64_t n,
+// inv_step = 1 / step, computed once by the caller: the first estimates only need to be
+// close (the loops below settle them on the exact predicate), and an FP64 division per
+// call costs more than the rest of the function on a GPU with a low FP64 rate
+__device__ inline void line_k_range(double nu, double cut, double nu_A, double step, double inv_step, int64_t n,
                                     int64_t *ka_out, int64_t *kb_out) {
-    double fa = ceil((nu - cut - nu_A) / step);
-    double fb = floor((nu + cut - nu_A) / step);
+    double fa = ceil((nu - cut - nu_A) * inv_step);
+    double fb = floor((nu + cut - nu_A) * inv_step);
     fa = fmax(fa, -1.0);
     fb = fmin(fb, (double)n);
     int64_t ka, kb;

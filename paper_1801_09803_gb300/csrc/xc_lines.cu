@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(256) k_count_evals(LinesDev L, size_t n, const
                                                      double cutoff, double width_mult,
                                                      unsigned long long *count) {
     unsigned long long local = 0;
+    const double inv_step = 1.0 / step;
     for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (size_t)gridDim.x * blockDim.x) {
         double nu = L.nu[l];
         for (int c = 0; c < n_cond; ++c) {
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(256) k_count_evals(LinesDev L, size_t n, const
                 cut = fmin(width_mult * fmax(al, ga), cutoff);
             }
             int64_t ka, kb;
-            line_k_range(nu, cut, nu_A, step, n_pts, &ka, &kb);
+            line_k_range(nu, cut, nu_A, step, inv_step, n_pts, &ka, &kb);
             if (kb >= ka) local += (unsigned long long)(kb - ka + 1);
         }
     }

@@ -8,8 +8,9 @@
 //
 // Per pass: (1) per-tile digit histograms, (2) digit totals and exclusive scan
 // into per-(digit, tile) output offsets, (3) a stable scatter where each warp
-// ranks its keys with __match_any_sync and warps are ordered through shared
-// counters.  A tile is 256 threads x 16 rounds = 4096 keys.
+// ranks its keys with __match_any_sync, warps are ordered through shared
+// counters, and each half-tile is ordered by digit in shared memory before it is
+// written out.  A tile is 256 threads x 16 rounds = 4096 keys.
 #include <stdio.h>
 
 #include "xc_internal.cuh"
@@ -120,59 +121,167 @@ __global__ void k_rs_row_scan(uint32_t *hist, uint32_t n_tiles, const uint32_t *
     }
 }
 
+// Stable scatter of one tile, in two halves of RS_HALF keys.  Each half is ranked in
+// shared memory first (digit counts, their exclusive scan, then per round the warp ranks of
+// __match_any_sync and the counts of earlier warps, as a stable sort by digit), and then
+// written out in that order: consecutive threads write consecutive positions of a digit's
+// run, instead of every key going to its own scattered address.  The global position of a
+// key is the tile's offset for its digit plus its stable rank among the tile's keys of that
+// digit, so the output is that of a stable LSD pass.
+constexpr int RS_HALF_ROUNDS = RS_ROUNDS / 2;
+constexpr int RS_HALF = RS_THREADS * RS_HALF_ROUNDS;
+static_assert(RS_THREADS == 256, "one thread per digit value in the per-digit tables");
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin, uint64_t *kout,
                                                            uint32_t *vout, size_t n, int shift,
                                                            const uint32_t *__restrict__ offs, uint32_t n_tiles) {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wc[RS_THREADS / 32][256];
+    __shared__ uint64_t skey[RS_HALF];
+    __shared__ uint32_t sval[RS_HALF];
+    __shared__ uint32_t wc[RS_THREADS / 32][256];   // per round: keys of each digit per warp
+    __shared__ uint32_t grun[256];                  // next global position per digit
+    __shared__ uint32_t sstart[256];                // first local position per digit (this half)
+    __shared__ uint32_t slrun[256];                 // next local position per digit
+    __shared__ uint32_t scnt[256];                  // keys per digit (this half)
+    __shared__ uint32_t swt[RS_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    run[tid] = offs[(size_t)tid * n_tiles + blockIdx.x];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    grun[tid] = offs[(size_t)tid * n_tiles + blockIdx.x];
+    scnt[tid] = 0;
 #pragma unroll
     for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][tid] = 0;
-    __syncthreads();
-    const size_t base = (size_t)blockIdx.x * RS_TILE;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        size_t i = base + (size_t)r * RS_THREADS + tid;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        uint32_t val = valid ? vin[i] : 0u;
-        uint32_t d = valid ? (uint32_t)((key >> shift) & 255) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt_mask);
-        int leader = 31 - __clz(peers);
-        if (valid && lane == leader) wc[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = run[d] + rank;
-            for (int w = 0; w < warp; ++w) pos += wc[w][d];
-            kout[pos] = key;
-            vout[pos] = val;
-        }
-        __syncthreads();
-        uint32_t s = 0;
+    const size_t tbase = (size_t)blockIdx.x * RS_TILE;
+    for (int half = 0; half < 2; ++half) {
+        const size_t base = tbase + (size_t)half * RS_HALF;
+        uint64_t key[RS_HALF_ROUNDS];
+        uint32_t val[RS_HALF_ROUNDS], dig[RS_HALF_ROUNDS];
 #pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; ++w) {
-            s += wc[w][tid];
-            wc[w][tid] = 0;
+        for (int r = 0; r < RS_HALF_ROUNDS; ++r) {
+            const size_t i = base + (size_t)r * RS_THREADS + tid;
+            const bool valid = i < n;
+            key[r] = valid ? kin[i] : 0ull;
+            val[r] = valid ? vin[i] : 0u;
+            dig[r] = valid ? (uint32_t)((key[r] >> shift) & 255) : 256u;
         }
-        run[tid] += s;
+        __syncthreads();   // the previous half's tables are no longer read
+        // digit counts of the half (one shared atomic per distinct digit of a warp)
+#pragma unroll
+        for (int r = 0; r < RS_HALF_ROUNDS; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            if (dig[r] < 256u && lane == 31 - __clz(peers)) atomicAdd(&scnt[dig[r]], (uint32_t)__popc(peers));
+        }
         __syncthreads();
+        // exclusive scan of the counts over the 256 digits
+        {
+            const uint32_t v = scnt[tid];
+            uint32_t inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (lane == 31) swt[warp] = inc;
+            __syncthreads();
+            uint32_t wpre = 0;
+#pragma unroll
+            for (int w = 0; w < RS_THREADS / 32; ++w) wpre += w < warp ? swt[w] : 0u;
+            sstart[tid] = slrun[tid] = wpre + inc - v;
+        }
+        __syncthreads();
+        // stable local ranks, round by round, into shared memory
+#pragma unroll
+        for (int r = 0; r < RS_HALF_ROUNDS; ++r) {
+            const uint32_t d = dig[r];
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && lane == 31 - __clz(peers)) wc[warp][d] = __popc(peers);
+            __syncthreads();
+            if (d < 256u) {
+                uint32_t pos = slrun[d] + __popc(peers & lt_mask);
+                for (int w = 0; w < warp; ++w) pos += wc[w][d];
+                skey[pos] = key[r];
+                sval[pos] = val[r];
+            }
+            __syncthreads();
+            uint32_t add = 0;
+#pragma unroll
+            for (int w = 0; w < RS_THREADS / 32; ++w) {
+                add += wc[w][tid];
+                wc[w][tid] = 0;
+            }
+            slrun[tid] += add;
+            __syncthreads();   // counters reset and advanced before the next round uses them
+        }
+        // write the half out in local order: runs of one digit go to consecutive addresses
+        const uint32_t nvalid = slrun[255];   // every valid key of the half has been placed
+#pragma unroll
+        for (int r = 0; r < RS_HALF_ROUNDS; ++r) {
+            const uint32_t idx = (uint32_t)(r * RS_THREADS + tid);
+            if (idx < nvalid) {
+                const uint64_t k = skey[idx];
+                const uint32_t d = (uint32_t)((k >> shift) & 255);
+                const uint32_t gpos = grun[d] + (idx - sstart[d]);
+                kout[gpos] = k;
+                vout[gpos] = sval[idx];
+            }
+        }
+        __syncthreads();
+        grun[tid] += scnt[tid];
+        scnt[tid] = 0;
     }
 }
 
-__global__ void k_gather_lines(LinesDev L, size_t n, const uint64_t *skeys, const uint32_t *perm, double *nu,
-                               float *elower, float *A, float *gref, float *nT, int16_t *g, int16_t *j) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        uint32_t s = perm[i];
-        nu[i] = val_of_key(skeys[i]);
-        elower[i] = L.elower[s];
-        A[i] = L.A[s];
-        gref[i] = L.gamma_ref[s];
-        nT[i] = L.n_T[s];
-        g[i] = L.g_up[s];
-        j[i] = L.j_lo ? L.j_lo[s] : (int16_t)0;
+// Reorders every field by the sorted permutation.  The reads are random (one sector per
+// field and line), so each thread issues the loads of GL_UNROLL lines before any store to
+// keep more of them in flight.
+constexpr int GL_UNROLL = 4;
+__global__ void k_gather_lines(LinesDev L, size_t n, const uint64_t *__restrict__ skeys,
+                               const uint32_t *__restrict__ perm, double *__restrict__ nu,
+                               float *__restrict__ elower, float *__restrict__ A, float *__restrict__ gref,
+                               float *__restrict__ nT, int16_t *__restrict__ g, int16_t *__restrict__ j) {
+    const float *__restrict__ iE = L.elower;
+    const float *__restrict__ iA = L.A;
+    const float *__restrict__ iG = L.gamma_ref;
+    const float *__restrict__ iN = L.n_T;
+    const int16_t *__restrict__ iU = L.g_up;
+    const int16_t *__restrict__ iJ = L.j_lo;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * GL_UNROLL) {
+        uint32_t sidx[GL_UNROLL];
+        float e[GL_UNROLL], a[GL_UNROLL], gr[GL_UNROLL], nt[GL_UNROLL];
+        int16_t gu[GL_UNROLL], jl[GL_UNROLL];
+        uint64_t k[GL_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GL_UNROLL; ++u) {
+            const size_t i = i0 + (size_t)u * stride;
+            sidx[u] = i < n ? perm[i] : 0u;
+            k[u] = i < n ? skeys[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < GL_UNROLL; ++u) {
+            const size_t i = i0 + (size_t)u * stride;
+            if (i < n) {
+                const uint32_t s = sidx[u];
+                e[u] = iE[s];
+                a[u] = iA[s];
+                gr[u] = iG[s];
+                nt[u] = iN[s];
+                gu[u] = iU[s];
+                jl[u] = iJ ? iJ[s] : (int16_t)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GL_UNROLL; ++u) {
+            const size_t i = i0 + (size_t)u * stride;
+            if (i < n) {
+                nu[i] = val_of_key(k[u]);
+                elower[i] = e[u];
+                A[i] = a[u];
+                gref[i] = gr[u];
+                nT[i] = nt[u];
+                g[i] = gu[u];
+                j[i] = jl[u];
+            }
+        }
     }
 }
 

@@ -174,17 +174,18 @@ __global__ void __launch_bounds__(VT) k_vjp_lines(LinesDev L, size_t n, const Co
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double accT = 0.0, accP = 0.0, accS = 0.0, accN = 0.0;  // lane c: condition c
     const CondDev cme = conds[lane < nc ? lane : 0];
+    const double inv_step = 1.0 / step;
     for (int q = 0; q < 2 * nb; ++q) s_broad[warp][lane][q] = 0.0;
     for (size_t l = (size_t)blockIdx.x * VW + warp; l < n; l += (size_t)gridDim.x * VW) {
         const double nu = L.nu[l];
         VjpLineCond mine = line_cond64(L, l, cme);
         double line_gr = 0.0, line_n = 0.0;
         int64_t ka0 = 0, kb0 = -1;
-        if (!(width_mult > 0.0)) line_k_range(nu, cutoff, nu_A, step, n_pts, &ka0, &kb0);
+        if (!(width_mult > 0.0)) line_k_range(nu, cutoff, nu_A, step, inv_step, n_pts, &ka0, &kb0);
         for (int c = 0; c < nc; ++c) {
             const double I = shfl64(mine.I, c), al = shfl64(mine.al, c), ga = shfl64(mine.ga, c);
             int64_t ka = ka0, kb = kb0;
-            if (width_mult > 0.0) line_k_range(nu, fmin(width_mult * fmax(al, ga), cutoff), nu_A, step, n_pts, &ka, &kb);
+            if (width_mult > 0.0) line_k_range(nu, fmin(width_mult * fmax(al, ga), cutoff), nu_A, step, inv_step, n_pts, &ka, &kb);
             double SI = 0.0, Sa = 0.0, Sg = 0.0;
             for (int64_t k = ka + lane; k <= kb; k += 32) {
                 double D = __dsub_rn(grid_x(nu_A, step, k), nu);
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(VT) k_vjp32(Vjp32Params p) {
                     const double al = alpha_coef(cd.T, cd.mass_da) * nud;
                     const double ga = cd.gamma_scale * (double)gref * exp(((double)nT + cd.n_shift) *
                                                                           log(cd.T_ref / cd.T)) * (cd.P / cd.P_ref);
-                    line_k_range(nud, fmin(p.width_mult * fmax(al, ga), p.cutoff), p.nu_A, p.step, p.n_pts, &k0, &k1);
+                    line_k_range(nud, fmin(p.width_mult * fmax(al, ga), p.cutoff), p.nu_A, p.step, 1.0 / p.step, p.n_pts, &k0, &k1);
                 }
                 ka = __shfl_sync(0xffffffffu, (int)k0, c);
                 kb = __shfl_sync(0xffffffffu, (int)k1, c);
