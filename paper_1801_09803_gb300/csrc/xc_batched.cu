@@ -669,7 +669,7 @@ __device__ __forceinline__ void w4_series_pair(f32x2 (&acc)[R / 2][CG], int c, c
 // TCN: compiled for the near pairs of the tensor-core sweep only (p.tc_far set): the code
 // of the other modes is left out, which frees registers for more resident warps
 template <int PROF, int R, int CG, bool EXT = true, bool TCN = false>
-__global__ void __launch_bounds__(GT, (TCN ? (CG >= 16 ? 2 : 3) : (CG >= 16 ? 1 : 2))) k_gather_f32(GatherParams p) {
+__global__ void __launch_bounds__(GT, (TCN ? (CG >= 16 ? 2 : 4) : (CG >= 16 ? 1 : 2))) k_gather_f32(GatherParams p) {
     constexpr unsigned kAllConds = CG >= 32 ? 0xffffffffu : ((1u << CG) - 1u);
     using Lay = SmemLayout<PROF, R, CG>;
     extern __shared__ __align__(16) unsigned char smem[];
