@@ -668,8 +668,19 @@ __device__ __forceinline__ void w4_series_pair(f32x2 (&acc)[R / 2][CG], int c, c
 
 // TCN: compiled for the near pairs of the tensor-core sweep only (p.tc_far set): the code
 // of the other modes is left out, which frees registers for more resident warps
+// CTAs per SM the register allocation is held to: more resident warps hide the latency of
+// these kernels' dependent chains, as long as the allocation does not spill in the point
+// loops (ptxas: the near-pair kernel 84 bytes at 4; the one-condition Voigt w4 shape 6 bytes
+// at 3; the other Voigt w4 shapes and Lorentz at 8 conditions hundreds of bytes at 3, so
+// they keep 2)
+template <int PROF, int CG, bool TCN>
+constexpr int gather_min_ctas() {
+    return TCN ? (CG >= 16 ? 2 : 4)
+               : (CG >= 16 ? 1 : ((PROF == XC_VOIGT_W4 ? CG == 1 : CG <= 4) ? 3 : 2));
+}
+
 template <int PROF, int R, int CG, bool EXT = true, bool TCN = false>
-__global__ void __launch_bounds__(GT, (TCN ? (CG >= 16 ? 2 : 4) : (CG >= 16 ? 1 : 2))) k_gather_f32(GatherParams p) {
+__global__ void __launch_bounds__(GT, (gather_min_ctas<PROF, CG, TCN>())) k_gather_f32(GatherParams p) {
     constexpr unsigned kAllConds = CG >= 32 ? 0xffffffffu : ((1u << CG) - 1u);
     using Lay = SmemLayout<PROF, R, CG>;
     extern __shared__ __align__(16) unsigned char smem[];
